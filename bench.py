@@ -1,0 +1,423 @@
+"""Benchmark of the pDCA hot path on GB300.
+
+One step = one full pDCA solve of the workload from u^0 (outer steps x inner
+fused sweeps with linearisation, fidelity, preconditioner and projection),
+then the final energy / residual reduction and the labels, all through the C
+interface with the graph already resident in HBM.  The metric is algorithmic
+bytes per second (the HBM bytes the path must move, counted once), the
+sweep kernel's share of it is compared with the measured HBM copy bandwidth.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU runs go through torchrun; every rank solves its own replica of the
+workload (independent problems, no collective on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Laplacian-sweep HBM GB/s (% of peak); ms per PDCA solve; p50/p99 under mixed load"
+FALLBACK_HBM_GBS = 6800.0
+PRECOND_NAMES = {0: "damped Jacobi", 1: "perturbed Jacobi", 2: "generalized Richardson"}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------
+# byte model (per unit of work)
+# ---------------------------------------------------------------------------
+
+def sweep_bytes(nnz, n, K, s_idx=4, s_w=4, s_u=4):
+    """Algorithmic HBM bytes of one fused sweep: the index and weight streams,
+    one read of v^s, one read of u^t, one write of v^{s+1}, one tag byte per
+    row; neighbour rows counted once."""
+    return nnz * (s_idx + s_w) + n * (3 * K * s_u + 1)
+
+
+def energy_bytes(nnz, n, K, s_idx=4, s_w=4, s_u=4):
+    """Energy + residual pass: the operator, u^{t+1} and u^t, one tag byte."""
+    return nnz * (s_idx + s_w) + n * (2 * K * s_u + 1)
+
+
+def labels_bytes(n, K, s_u=4):
+    return n * (K * s_u + 4)
+
+
+def solve_bytes(wl):
+    p = wl.params
+    return (p["outer"] * p["inner"] * sweep_bytes(wl.nnz, wl.n, wl.K)
+            + energy_bytes(wl.nnz, wl.n, wl.K) + labels_bytes(wl.n, wl.K))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def sweep_traffic_record():
+    """DRAM bytes per sweep launch from the committed ncu summary, valid only
+    while the kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "sweep_voronoi2048_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_2303_14495_gb300", "csrc", "sweep_kernels.cu")
+    h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    rec = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("kernel_source_sha1") != h:
+        return None
+    try:
+        return float(rec["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"pdca_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas only)
+# ---------------------------------------------------------------------------
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(wl, omp, sweeps):
+    """One outer step with `sweeps` sweeps of the FP64 oracle on the full graph
+    (plus its residual and energy passes); returns (seconds, algorithmic bytes, threads)."""
+    import oracle
+    p = wl.params
+    lam = 2.0 if p["precond"] == 2 else 0.0
+    P = oracle.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, p["eps"], p["eta"],
+                       p["c"], precond=p["precond"], damping=p["damping"] or 0.5, lambda_max=lam, omp=omp)
+    u0 = P.init_u()
+    t0 = time.perf_counter()
+    P.solve(1, sweeps, u0)
+    dt = time.perf_counter() - t0
+    nb = sweeps * sweep_bytes(wl.nnz, wl.n, wl.K) + 2 * energy_bytes(wl.nnz, wl.n, wl.K)
+    return dt, nb, oracle.num_threads(omp)
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def workload_config(wl, extra=None):
+    p = wl.params
+    cfg = {
+        "workload": (f"{wl.name}: {wl.meta.get('kind')} graph, N={wl.n}, nnz={wl.nnz}, K={wl.K}, "
+                     f"{p['outer']} outer x {p['inner']} {PRECOND_NAMES[p['precond']]} sweeps, "
+                     f"eps={p['eps']:g} c={p['c']:g} eta={p['eta']:g}"),
+        "n": wl.n, "nnz": wl.nnz, "K": wl.K, "outer": p["outer"], "inner": p["inner"],
+        "precond": PRECOND_NAMES[p["precond"]],
+        "l2": "inputs larger than L2 (operator + 3 iterates > 129 MB), no flush",
+        "parallelism": "replicas (one independent problem per GPU)",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def run_reference(args, wl, world, rank):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(wl, True, 1)
+    vals = []
+    tot_s, tot_b = 0.0, 0
+    for _ in range(args.steps):
+        dt, nb, thr = oracle_sample(wl, True, 1)
+        tot_s += dt
+        tot_b += nb
+    value = tot_b / tot_s / 1e9
+    ms = 1e3 * tot_s / args.steps
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(wl),
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": thr, "kind": "oracle",
+                         "sample": f"per step: 1 outer step x 1 sweep + residual + energy of {wl.name} "
+                                   f"(FP64 oracle, OpenMP over rows)"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, wl, world, rank, local):
+    import torch
+    from paper_2303_14495_gb300 import binding as B
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    p = wl.params
+    prm = B.params_from_workload(p)
+    t0 = time.perf_counter()
+    prob = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm, device=dev)
+    torch.cuda.synchronize(dev)
+    create_s = time.perf_counter() - t0
+    lay = prob.layout()
+    lam_used, lam_est = prob.lambda_max()
+    lab_dev = torch.empty(wl.n, dtype=torch.int32, device=dev)
+
+    def step():
+        prob.set_u(None)
+        prob.solve(p["outer"], p["inner"])
+        F, rel = prob.energy()
+        prob.labels(lab_dev)
+        return F, rel
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.4)
+    prob.profile(True)
+    launches0 = B.pdca_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        F, rel = step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = B.pdca_kernel_launches() - launches0
+    sweep_ms_tot, sweep_launches = prob.profile_read()
+    prob.profile(False)
+    clocks = clk.stop()
+    barrier(world)
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ms_total, world)
+    ms_step = ms_total / args.steps
+    bytes_step = solve_bytes(wl)
+    value = world * bytes_step * args.steps / (ms_total * 1e-3) / 1e9
+
+    hbm, kind = peaks()
+    sb = sweep_bytes(wl.nnz, wl.n, wl.K)
+    sweep_ms = sweep_ms_tot / max(sweep_launches, 1)
+    achieved = sb / (sweep_ms * 1e-3) / 1e9
+    traffic = sweep_traffic_record()
+
+    # end to end through the C interface from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_rp, h_col, h_w = pin(wl.row_ptr), pin(wl.col), pin(wl.w)
+        h_mask, h_lab = pin(wl.fid_mask), pin(wl.fid_labels)
+        h_out = torch.empty(wl.n, dtype=torch.int32).pin_memory()
+        ws = prob.workspace
+        del prob
+        torch.cuda.synchronize(dev)
+
+        def e2e_step():
+            st, h = B.pdca_create(h_rp, h_col, h_w, wl.n, wl.K, h_mask, h_lab, prm, ws, ws.numel(),
+                                  stream.cuda_stream)
+            assert st == 0, B.STATUS_NAMES[st]
+            assert B.pdca_solve(h, p["outer"], p["inner"]) == 0
+            st, F, rel = B.pdca_energy(h)
+            assert st == 0
+            assert B.pdca_labels(h, h_out) == 0
+            B.pdca_destroy(h)
+
+        e2e_step()
+        n_e2e = max(1, min(args.steps, 5))
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(n_e2e):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - w0
+        ms_e2e = max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3) / n_e2e, world)
+        h2d = wl.row_ptr.nbytes + wl.col.nbytes + wl.w.nbytes + wl.fid_mask.nbytes + wl.fid_labels.nbytes
+        e2e = {"value": world * bytes_step / (ms_e2e * 1e-3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(wl.n * 4 + 64),
+               "ms_per_step": ms_e2e, "steps": n_e2e,
+               "includes": "pdca_create (H2D of the CSR, validation, degrees, reordering, "
+                           "sliced-ELL packing, power method) + solve + energy + labels D2H"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, nb, thr = oracle_sample(wl, False, 2)
+        cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": thr, "kind": "oracle",
+               "sample": f"1 outer step x 2 sweeps + residual + energy of {wl.name} "
+                         f"(FP64 oracle, single thread), {dt:.1f} s"}
+        if not args.no_cpu_allcores:
+            dt2, nb2, thr2 = oracle_sample(wl, True, 2)
+            cpu["allcores"] = {"value": nb2 / dt2 / 1e9, "cores": thr2,
+                               "sample": f"same work, OpenMP over rows, {dt2:.1f} s"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(wl, {"sort_window": lay["sort_window"],
+                                       "sell_entries": lay["sell_entries"],
+                                       "lambda_max_used": lam_used}),
+        "ms_per_solve": ms_step,
+        "pct_of_peak": 100.0 * value / world / hbm,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "kernel": "sweep_kernel<4,*> (fused sweep)",
+                     "bytes_per_launch": sb, "ms_per_launch": sweep_ms,
+                     "launches_timed": sweep_launches, "peak_kind": kind},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "create_ms": create_s * 1e3,
+        "final_energy": F, "final_rel_residual": rel,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="voronoi2048")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-allcores", action="store_true")
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        # the CPU reference runs once, on rank 0; other ranks exit without work
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        world, rank, local = 1, 0, 0
+    else:
+        world, rank, local = dist_setup()
+    from gen import make_workload
+    t0 = time.perf_counter()
+    wl = make_workload(args.workload)
+    log(f"workload {wl.name}: n={wl.n} nnz={wl.nnz} K={wl.K} ({time.perf_counter() - t0:.1f} s)")
+    if args.impl == "reference":
+        run_reference(args, wl, world, rank)
+    else:
+        import __graft_entry__
+        __graft_entry__.build()
+        run_ours(args, wl, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * pdca.h -- C interface of the GB300 (sm_103a) preconditioned DCA solver for
+ * the graph Ginzburg-Landau model (Shen, Sun, Tai, "Preconditioned Algorithm
+ * for Difference of Convex Functions with applications to Graph
+ * Ginzburg-Landau Model").
+ *
+ * Problem (Sec. 2, eq. functional:GL): minimise over u (n x K, row-major)
+ *   F(u) = (eps/2) <u, L u> + (1/(4 eps)) sum_i (u_i^2 - 1)^2
+ *          + (eta/2) sum_i Lambda_i (u_i - y_i)^2
+ * with L the graph Laplacian of a symmetric weight matrix W, normalized
+ * (L_s = I - D^{-1/2} W D^{-1/2}) by default.  Each outer DCA step (eq.
+ * dca:linear:system:ori, Prop. nopre) linearises the double well at u^t,
+ *   b^t = eta Lambda y + c u^t - (u^t^3 - u^t)/eps,
+ * and replaces the solve of T u = b^t, T = eps L + eta Lambda + c I, by a
+ * few diagonal preconditioned sweeps v <- v + G^{-1}(b^t - T v)
+ * (eq. general:diag:pre) with the feasible damped-Jacobi, perturbed-Jacobi
+ * or generalized-Richardson preconditioner of eq. pre:norm:jacob:richard.
+ *
+ * K = 1 is the paper's binary model (labels +-1).  K >= 2 runs the same
+ * scalar update on every column of a +-1 class coding and projects each row
+ * onto the probability simplex (in v = (u+1)/2) after every outer step; the
+ * paper has no multi-class form, this extension follows the same equations
+ * column by column.
+ *
+ * Conventions for every call:
+ *  - Every function returns a pdca_status; no C++ exception crosses it.
+ *  - Pointers documented "host or device" may be either: the library asks
+ *    the CUDA runtime which kind it is and copies accordingly.
+ *  - The library allocates no device memory.  All device state lives in the
+ *    caller's workspace (size from pdca_workspace_size), which the handle
+ *    borrows until pdca_destroy; the caller frees it afterwards.
+ *  - All device work of a handle runs on the stream given to pdca_create.
+ *    Calls that return host values synchronise that stream.  Errors of
+ *    asynchronous kernels surface at the next synchronising call.
+ *  - One handle must not be used from two host threads at once; separate
+ *    handles on separate streams are independent.
+ */
+#ifndef PDCA_H
+#define PDCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Largest number of label columns K supported by the kernels. */
+#define PDCA_MAX_K 16
+
+typedef enum {
+    PDCA_OK = 0,
+    PDCA_ERR_INVALID_ARG = 1,    /* bad size, pointer, parameter or call order        */
+    PDCA_ERR_NOT_SYMMETRIC = 2,  /* w_ij != w_ji or (i,j) stored without (j,i)         */
+    PDCA_ERR_ISOLATED_NODE = 3,  /* d_i = sum_j w_ij is not > 0 (Sec. 2.2 needs d > 0) */
+    PDCA_ERR_INFEASIBLE = 4,     /* preconditioner not feasible (G > T fails)          */
+    PDCA_ERR_NONFINITE = 5,      /* NaN/Inf in the iterate                             */
+    PDCA_ERR_OOM = 6,            /* workspace smaller than pdca_workspace_size         */
+    PDCA_ERR_CUDA = 7,           /* a CUDA runtime call failed                         */
+    PDCA_ERR_TIMEOUT = 8,        /* a bounded device-side wait ran out                 */
+    PDCA_ERR_BAD_GRAPH = 9       /* column out of range, self loop, columns not
+                                    strictly increasing, weight < 0 or not finite,
+                                    mask not 0/1, or prior label out of range           */
+} pdca_status;
+
+/* Laplacian (Sec. 2.2). */
+enum { PDCA_LAP_NORMALIZED = 0, PDCA_LAP_UNNORMALIZED = 1 };
+
+/* Diagonal preconditioner G (Sec. 3.1, eq. pre:norm:jacob:richard), normalized
+ * Laplacian, infinite step size:
+ *   PDCA_JACOBI_DAMPED    g_i = (eps + c + eta Lambda_i) / omega
+ *                         (the paper's G_{Jd,s} = 2 diag(T) is omega = 1/2);
+ *   PDCA_JACOBI_PERTURBED g_i = 2 eps + c + delta0 + eta Lambda_i   (G_{Jp,s});
+ *   PDCA_RICHARDSON       g_i = eps lambda_max + c + delta0 + eta Lambda_i (G_{R,s}). */
+enum { PDCA_JACOBI_DAMPED = 0, PDCA_JACOBI_PERTURBED = 1, PDCA_RICHARDSON = 2 };
+
+/* Arithmetic of the sweeps.  Only PDCA_FP32 is implemented: FP32 storage of
+ * the pre-scaled weights and of u, FP32 accumulation, FP64 reductions. */
+enum { PDCA_FP32 = 0 };
+
+typedef struct {
+    double eps;          /* diffuse interface parameter epsilon > 0                    */
+    double c;            /* convex-split constant c > 0 (eq. dc:functional)           */
+    double eta;          /* fidelity weight eta >= 0 (eq. functional:GL)              */
+    int32_t laplacian;   /* PDCA_LAP_*; only PDCA_LAP_NORMALIZED is implemented       */
+    int32_t precond;     /* PDCA_JACOBI_DAMPED / PDCA_JACOBI_PERTURBED / PDCA_RICHARDSON */
+    double damping;      /* omega in (0,1) for PDCA_JACOBI_DAMPED; feasible for every
+                            graph iff c > eps (2 omega - 1)/(1 - omega)               */
+    double delta0;       /* the small constant delta_0 > 0 of G_Jp and G_R (1e-6)     */
+    double lambda_max;   /* lambda_max(L_s) for PDCA_RICHARDSON; 0 = estimate it with
+                            the power method at create time, then use
+                            min(2, 1.001 * estimate) (2 bounds it, Prop. diagonal:pre) */
+    int32_t power_iters; /* power-method iterations (150 in the paper's experiments)   */
+    int32_t precision;   /* PDCA_FP32                                                  */
+    int32_t sort_window; /* rows are reordered by degree inside windows of this many
+                            rows (a power of two in [32, 8192]); 0 = choose the
+                            smallest window with at most 10% slice padding              */
+    int32_t reserved_;
+} pdca_params;
+
+typedef struct pdca_problem pdca_problem;
+
+/* Fill *p with the defaults: eps = 1, c = 3, eta = 1, normalized Laplacian,
+ * perturbed Jacobi, omega = 0.5, delta0 = 1e-6, lambda_max = 0 (estimate),
+ * 150 power iterations, FP32, automatic sort window. */
+void pdca_default_params(pdca_params *p);
+
+/* Device workspace, in bytes, that pdca_create needs for this graph.
+ * row_ptr: n+1 CSR row offsets (host or device), row_ptr[0] = 0, non-decreasing.
+ * k: label columns (1..PDCA_MAX_K).  p: parameters (NULL = defaults).
+ * Errors: PDCA_ERR_INVALID_ARG for n < 1, k out of range, a bad row_ptr or
+ * a sort window that is not a power of two in [32, 8192]. */
+pdca_status pdca_workspace_size(const int64_t *row_ptr, int32_t n, int32_t k,
+                                const pdca_params *p, size_t *bytes);
+
+/* Build a problem (Sec. 2.2 and 3.1): validate the graph, compute the degrees
+ * d_i and the pre-scaled weights w_ij / sqrt(d_i d_j), reorder rows by degree
+ * within sort windows, pack the sliced-ELL operator, set u^0 and, for
+ * Richardson with lambda_max = 0, run the power method.
+ *   row_ptr  n+1 int64 CSR offsets            (host or device; read during the call)
+ *   col      nnz int32 columns, strictly increasing within each row, no i == j
+ *   w        nnz float32 weights, finite and >= 0, symmetric: w_ij == w_ji exactly
+ *   fid_mask n uint8 Lambda_i in {0,1}
+ *   labels   n int32 prior class per node, read only where fid_mask = 1:
+ *            K = 1: class 0 -> y = -1, class 1 -> y = +1;  K >= 2: class in [0, K)
+ *   p        parameters (NULL = defaults)
+ *   workspace, ws_bytes  caller-owned device memory, 256-byte aligned
+ *   stream   cudaStream_t as void* (NULL = legacy default stream)
+ *   out      receives the handle (NULL on error)
+ * u^0: labelled rows start at their prior y_i; unlabelled rows at 0 (K = 1)
+ * or at the simplex centre 2/K - 1 (K >= 2).
+ * Errors: INVALID_ARG, OOM (workspace too small), BAD_GRAPH, NOT_SYMMETRIC,
+ * ISOLATED_NODE, INFEASIBLE, CUDA. */
+pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float *w,
+                        int32_t n, int32_t k, const uint8_t *fid_mask, const int32_t *labels,
+                        const pdca_params *p, void *workspace, size_t ws_bytes,
+                        void *stream, pdca_problem **out);
+
+/* Replace the iterate: u (n x K row-major float32, host or device), or NULL
+ * to restore u^0.  Clears the record of the last outer step. */
+pdca_status pdca_set_u(pdca_problem *h, const float *u);
+
+/* One outer pDCA step (Prop. nopre) with `inner_sweeps` >= 1 preconditioned
+ * sweeps; for K >= 2 the last sweep also projects each row onto the simplex.
+ * Asynchronous. */
+pdca_status pdca_step(pdca_problem *h, int32_t inner_sweeps);
+
+/* `outer_iters` >= 0 outer steps of `inner_sweeps` sweeps each.
+ * damping > 0 replaces omega for PDCA_JACOBI_DAMPED (re-checked for
+ * feasibility; INFEASIBLE otherwise); pass 0 to keep the current value.
+ * energy_trace / residual_trace: NULL, or host or device arrays of
+ * outer_iters doubles receiving F(u^{t+1}) and ||b^t - T u^{t+1}|| / ||b^t||
+ * after every step (this adds one reduction pass per step and synchronises
+ * at the end).  Without traces the call is asynchronous. */
+pdca_status pdca_solve(pdca_problem *h, int32_t outer_iters, int32_t inner_sweeps,
+                       double damping, double *energy_trace, double *residual_trace);
+
+/* F(u) of the current iterate (FP64 accumulation) and, if rel_residual is
+ * not NULL, the relative residual ||b^t - T u^{t+1}||_2 / ||b^t||_2 of the
+ * last outer step (NaN if no step was taken since create / set_u).
+ * Returns NONFINITE if u holds NaN/Inf.  Synchronises. */
+pdca_status pdca_energy(pdca_problem *h, double *F, double *rel_residual);
+
+/* Copy the iterate to u_out (n x K float32, original node order, host or device). */
+pdca_status pdca_get_u(pdca_problem *h, float *u_out);
+
+/* Labels of the current iterate into labels_out (n int32, host or device):
+ * K = 1: 1 if u_i >= 0 else 0;  K >= 2: argmax_k u_ik, lowest k on ties. */
+pdca_status pdca_labels(pdca_problem *h, int32_t *labels_out);
+
+/* The lambda_max in use by the Richardson preconditioner (the power-method
+ * estimate raised by 0.1% and capped at 2, or the value given), and the raw
+ * estimate (0 if none was computed). */
+pdca_status pdca_lambda_max(pdca_problem *h, double *lambda_used, double *lambda_estimate);
+
+/* Layout facts of a created problem: padded sliced-ELL entries, number of
+ * 32-row slices, sort window.  Any pointer may be NULL. */
+pdca_status pdca_layout(pdca_problem *h, int64_t *sell_entries, int64_t *n_slices,
+                        int32_t *sort_window);
+
+/* Kernel timing for measurement: enable (1) / disable (0) CUDA-event timing
+ * of every sweep launch of this handle; read returns the summed sweep time
+ * in milliseconds and the number of timed launches since the last read, and
+ * resets both (synchronises). */
+pdca_status pdca_profile_enable(pdca_problem *h, int32_t on);
+pdca_status pdca_profile_read(pdca_problem *h, double *sweep_ms, int64_t *sweep_launches);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t pdca_kernel_launches(void);
+
+/* Release the handle's host-side state (the workspace stays the caller's).
+ * Synchronises the handle's stream first.  NULL is ignored. */
+void pdca_destroy(pdca_problem *h);
+
+/* Static description of a status code. */
+const char *pdca_status_string(pdca_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDCA_H */

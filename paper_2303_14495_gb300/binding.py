@@ -1,0 +1,311 @@
+"""Thin Python binding of ``libpdca.so`` (argument marshalling only).
+
+The functions ``pdca_*`` mirror the C interface of ``include/pdca.h`` one to
+one.  ``Problem`` bundles them with a device workspace allocated by PyTorch
+(PyTorch owns every byte of device memory; the library allocates none).
+Every computation runs in the library's CUDA kernels; there is no CPU path.
+If the library has not been built, ``lib()`` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpdca.so")
+
+PDCA_MAX_K = 16
+
+PDCA_OK = 0
+STATUS_NAMES = {
+    0: "PDCA_OK", 1: "PDCA_ERR_INVALID_ARG", 2: "PDCA_ERR_NOT_SYMMETRIC",
+    3: "PDCA_ERR_ISOLATED_NODE", 4: "PDCA_ERR_INFEASIBLE", 5: "PDCA_ERR_NONFINITE",
+    6: "PDCA_ERR_OOM", 7: "PDCA_ERR_CUDA", 8: "PDCA_ERR_TIMEOUT", 9: "PDCA_ERR_BAD_GRAPH",
+}
+PDCA_LAP_NORMALIZED, PDCA_LAP_UNNORMALIZED = 0, 1
+PDCA_JACOBI_DAMPED, PDCA_JACOBI_PERTURBED, PDCA_RICHARDSON = 0, 1, 2
+PDCA_FP32 = 0
+
+# every symbol include/pdca.h declares
+EXPORTS = [
+    "pdca_default_params", "pdca_workspace_size", "pdca_create", "pdca_set_u", "pdca_step",
+    "pdca_solve", "pdca_energy", "pdca_get_u", "pdca_labels", "pdca_lambda_max", "pdca_layout",
+    "pdca_profile_enable", "pdca_profile_read", "pdca_kernel_launches", "pdca_destroy",
+    "pdca_status_string",
+]
+
+
+class PdcaError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}")
+
+
+class pdca_params(C.Structure):
+    _fields_ = [
+        ("eps", C.c_double), ("c", C.c_double), ("eta", C.c_double),
+        ("laplacian", C.c_int32), ("precond", C.c_int32),
+        ("damping", C.c_double), ("delta0", C.c_double), ("lambda_max", C.c_double),
+        ("power_iters", C.c_int32), ("precision", C.c_int32),
+        ("sort_window", C.c_int32), ("reserved_", C.c_int32),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load the built CUDA library (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = C.CDLL(LIB_PATH)
+            vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+            P = C.POINTER(pdca_params)
+            sig = {
+                "pdca_default_params": (None, [P]),
+                "pdca_workspace_size": (C.c_int, [vp, i32, i32, P, C.POINTER(C.c_size_t)]),
+                "pdca_create": (C.c_int, [vp, vp, vp, i32, i32, vp, vp, P, vp, C.c_size_t, vp,
+                                          C.POINTER(vp)]),
+                "pdca_set_u": (C.c_int, [vp, vp]),
+                "pdca_step": (C.c_int, [vp, i32]),
+                "pdca_solve": (C.c_int, [vp, i32, i32, dbl, vp, vp]),
+                "pdca_energy": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(dbl)]),
+                "pdca_get_u": (C.c_int, [vp, vp]),
+                "pdca_labels": (C.c_int, [vp, vp]),
+                "pdca_lambda_max": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(dbl)]),
+                "pdca_layout": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
+                "pdca_profile_enable": (C.c_int, [vp, i32]),
+                "pdca_profile_read": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i64)]),
+                "pdca_kernel_launches": (u64, []),
+                "pdca_destroy": (None, [vp]),
+                "pdca_status_string": (C.c_char_p, [C.c_int]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _check(status: int, what: str):
+    if status != PDCA_OK:
+        raise PdcaError(status, what)
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a numpy array or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, C.c_void_p):
+        return a.value
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def make_params(eps=1.0, c=3.0, eta=1.0, precond=PDCA_JACOBI_PERTURBED, damping=0.5, delta0=1e-6,
+                lambda_max=0.0, power_iters=150, laplacian=PDCA_LAP_NORMALIZED,
+                precision=PDCA_FP32, sort_window=0) -> pdca_params:
+    p = pdca_params()
+    lib().pdca_default_params(C.byref(p))
+    p.eps, p.c, p.eta = float(eps), float(c), float(eta)
+    p.precond, p.damping, p.delta0 = int(precond), float(damping), float(delta0)
+    p.lambda_max, p.power_iters = float(lambda_max), int(power_iters)
+    p.laplacian, p.precision, p.sort_window = int(laplacian), int(precision), int(sort_window)
+    return p
+
+
+# ---- one-to-one wrappers of the C entry points ------------------------------
+
+def pdca_default_params() -> pdca_params:
+    p = pdca_params()
+    lib().pdca_default_params(C.byref(p))
+    return p
+
+
+def pdca_workspace_size(row_ptr, n: int, k: int, params: Optional[pdca_params] = None) -> int:
+    out = C.c_size_t(0)
+    st = lib().pdca_workspace_size(_ptr(row_ptr), int(n), int(k),
+                                   C.byref(params) if params is not None else None, C.byref(out))
+    _check(st, "pdca_workspace_size")
+    return int(out.value)
+
+
+def pdca_create(row_ptr, col, w, n, k, fid_mask, labels, params, workspace, ws_bytes, stream=0):
+    h = C.c_void_p()
+    st = lib().pdca_create(_ptr(row_ptr), _ptr(col), _ptr(w), int(n), int(k), _ptr(fid_mask),
+                           _ptr(labels), C.byref(params) if params is not None else None,
+                           _ptr(workspace), int(ws_bytes), C.c_void_p(int(stream)), C.byref(h))
+    return st, h
+
+
+def pdca_set_u(h, u=None) -> int:
+    return lib().pdca_set_u(h, _ptr(u))
+
+
+def pdca_step(h, inner: int) -> int:
+    return lib().pdca_step(h, int(inner))
+
+
+def pdca_solve(h, outer: int, inner: int, damping: float = 0.0, energy_trace=None,
+               residual_trace=None) -> int:
+    return lib().pdca_solve(h, int(outer), int(inner), float(damping), _ptr(energy_trace),
+                            _ptr(residual_trace))
+
+
+def pdca_energy(h):
+    F, r = C.c_double(0.0), C.c_double(0.0)
+    st = lib().pdca_energy(h, C.byref(F), C.byref(r))
+    return st, F.value, r.value
+
+
+def pdca_get_u(h, out) -> int:
+    return lib().pdca_get_u(h, _ptr(out))
+
+
+def pdca_labels(h, out) -> int:
+    return lib().pdca_labels(h, _ptr(out))
+
+
+def pdca_lambda_max(h):
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    st = lib().pdca_lambda_max(h, C.byref(a), C.byref(b))
+    return st, a.value, b.value
+
+
+def pdca_layout(h):
+    e, s, w = C.c_int64(0), C.c_int64(0), C.c_int32(0)
+    st = lib().pdca_layout(h, C.byref(e), C.byref(s), C.byref(w))
+    return st, e.value, s.value, w.value
+
+
+def pdca_profile_enable(h, on: bool) -> int:
+    return lib().pdca_profile_enable(h, 1 if on else 0)
+
+
+def pdca_profile_read(h):
+    ms, cnt = C.c_double(0.0), C.c_int64(0)
+    st = lib().pdca_profile_read(h, C.byref(ms), C.byref(cnt))
+    return st, ms.value, cnt.value
+
+
+def pdca_kernel_launches() -> int:
+    return int(lib().pdca_kernel_launches())
+
+
+def pdca_destroy(h) -> None:
+    lib().pdca_destroy(h)
+
+
+def pdca_status_string(st: int) -> str:
+    return lib().pdca_status_string(int(st)).decode()
+
+
+# ---- convenience object -----------------------------------------------------
+
+class Problem:
+    """A created pDCA problem with a PyTorch-owned device workspace.
+
+    Graph and fidelity arrays may be numpy arrays or torch tensors (host or
+    CUDA).  ``stream``: a ``torch.cuda.Stream`` (default: the current one).
+    """
+
+    def __init__(self, row_ptr, col, w, K, fid_mask, fid_labels, params: pdca_params,
+                 device="cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.n = int(row_ptr.shape[0] - 1)
+        self.K = int(K)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._keep = (row_ptr, col, w, fid_mask, fid_labels)
+        self.ws_bytes = pdca_workspace_size(row_ptr, self.n, self.K, params)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        st, h = pdca_create(row_ptr, col, w, self.n, self.K, fid_mask, fid_labels, params,
+                            self.workspace, self.ws_bytes, self.stream.cuda_stream)
+        _check(st, "pdca_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            pdca_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_u(self, u=None):
+        _check(pdca_set_u(self.h, u), "pdca_set_u")
+
+    def step(self, inner: int):
+        _check(pdca_step(self.h, inner), "pdca_step")
+
+    def solve(self, outer: int, inner: int, damping: float = 0.0, trace: bool = False):
+        if trace:
+            e = np.zeros(max(outer, 1), np.float64)
+            r = np.zeros(max(outer, 1), np.float64)
+            _check(pdca_solve(self.h, outer, inner, damping, e, r), "pdca_solve")
+            return e[:outer], r[:outer]
+        _check(pdca_solve(self.h, outer, inner, damping), "pdca_solve")
+        return None
+
+    def energy(self):
+        st, F, r = pdca_energy(self.h)
+        _check(st, "pdca_energy")
+        return F, r
+
+    def get_u(self, out=None):
+        if out is None:
+            shape = (self.n,) if self.K == 1 else (self.n, self.K)
+            out = np.empty(shape, np.float32)
+        _check(pdca_get_u(self.h, out), "pdca_get_u")
+        return out
+
+    def labels(self, out=None):
+        if out is None:
+            out = np.empty(self.n, np.int32)
+        _check(pdca_labels(self.h, out), "pdca_labels")
+        return out
+
+    def lambda_max(self):
+        st, used, est = pdca_lambda_max(self.h)
+        _check(st, "pdca_lambda_max")
+        return used, est
+
+    def layout(self):
+        st, e, s, w = pdca_layout(self.h)
+        _check(st, "pdca_layout")
+        return dict(sell_entries=e, n_slices=s, sort_window=w)
+
+    def profile(self, on: bool):
+        _check(pdca_profile_enable(self.h, on), "pdca_profile_enable")
+
+    def profile_read(self):
+        st, ms, cnt = pdca_profile_read(self.h)
+        _check(st, "pdca_profile_read")
+        return ms, cnt
+
+
+def params_from_workload(p: dict, **over) -> pdca_params:
+    """pdca_params from a workload's parameter dict."""
+    kw = dict(eps=p["eps"], c=p["c"], eta=p["eta"], precond=p["precond"],
+              damping=p.get("damping", 0.5) or 0.5, delta0=p.get("delta0", 1e-6),
+              power_iters=p.get("power_iters", 150))
+    kw.update(over)
+    return make_params(**kw)

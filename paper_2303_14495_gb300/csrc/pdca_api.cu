@@ -1,0 +1,621 @@
+// Host side of the C interface declared in include/pdca.h: argument checks,
+// the workspace layout, problem creation and the outer pDCA loop.
+#include "pdca_internal.cuh"
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace pdca;
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+constexpr size_t kAlign = 256;
+constexpr int kTraceCap = 1024;   // outer steps per trace chunk
+constexpr double kPadTarget = 1.10;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Everything about the device layout that depends only on the sizes and the
+// row lengths; computed on the host from row_ptr.
+struct Layout {
+    int32_t n = 0, K = 0, n_pad = 0, n_slices = 0, sigma = 0;
+    int64_t nnz = 0, sell_entries = 0;
+    std::vector<int64_t> slice_off;  // n_slices + 1
+    size_t o_col, o_w, o_slice, o_rowinfo, o_perm, o_iperm, o_u[3], o_part, o_red, o_scal, o_trace;
+    size_t o_srp, o_scol, o_sw, o_sdeg, o_smask, o_slab, o_status;
+    size_t persistent = 0, total = 0;
+};
+
+// Slice widths for one sort window: the degrees of the window sorted
+// descending; a slice's width is the degree at its first position.
+void window_widths(const int64_t *rp, int64_t base, int64_t end, std::vector<int32_t> &scratch,
+                   std::vector<int64_t> &widths) {
+    scratch.resize((size_t)(end - base));
+    for (int64_t i = base; i < end; ++i) scratch[(size_t)(i - base)] = (int32_t)(rp[i + 1] - rp[i]);
+    std::sort(scratch.begin(), scratch.end(), std::greater<int32_t>());
+    for (int64_t p = 0; p < end - base; p += kSliceRows) widths[(size_t)((base + p) / kSliceRows)] = scratch[(size_t)p];
+}
+
+int64_t sell_entries_for(const int64_t *rp, int32_t n, int32_t sigma, std::vector<int64_t> &widths) {
+    const int32_t n_slices = (n + kSliceRows - 1) / kSliceRows;
+    widths.assign((size_t)n_slices, 0);
+    std::vector<int32_t> scratch;
+    for (int64_t base = 0; base < n; base += sigma) window_widths(rp, base, std::min<int64_t>(n, base + sigma), scratch, widths);
+    int64_t tot = 0;
+    for (int64_t w : widths) tot += w * kSliceRows;
+    return tot;
+}
+
+pdca_status check_params(const pdca_params &p) {
+    auto fin = [](double x) { return std::isfinite(x); };
+    if (!(fin(p.eps) && p.eps > 0) || !(fin(p.c) && p.c > 0) || !(fin(p.eta) && p.eta >= 0))
+        return PDCA_ERR_INVALID_ARG;
+    if (p.laplacian != PDCA_LAP_NORMALIZED) return PDCA_ERR_INVALID_ARG;
+    if (p.precision != PDCA_FP32) return PDCA_ERR_INVALID_ARG;
+    if (p.precond < PDCA_JACOBI_DAMPED || p.precond > PDCA_RICHARDSON) return PDCA_ERR_INVALID_ARG;
+    if (!(fin(p.delta0) && p.delta0 >= 0) || !(fin(p.lambda_max) && p.lambda_max >= 0))
+        return PDCA_ERR_INVALID_ARG;
+    if (p.power_iters < 0) return PDCA_ERR_INVALID_ARG;
+    if (p.sort_window != 0) {
+        const int s = p.sort_window;
+        if (s < 32 || s > 8192 || (s & (s - 1)) != 0) return PDCA_ERR_INVALID_ARG;
+    }
+    return PDCA_OK;
+}
+
+// Feasibility G > T of the diagonal preconditioners for L_s (Sec. 3.1):
+// damped Jacobi G = diag(T)/omega needs omega in (0,1) and, for omega > 1/2,
+// c > eps (2 omega - 1)/(1 - omega) (the spectrum of L_s lies in [0, 2]);
+// perturbed Jacobi and Richardson need delta0 > 0 (Richardson also a
+// lambda_max that bounds the spectrum, which the caller vouches for).
+pdca_status feasible(const pdca_params &p, double omega, double lambda) {
+    switch (p.precond) {
+    case PDCA_JACOBI_DAMPED:
+        if (!(omega > 0.0 && omega < 1.0)) return PDCA_ERR_INFEASIBLE;
+        if (omega > 0.5 && !(p.c > p.eps * (2.0 * omega - 1.0) / (1.0 - omega))) return PDCA_ERR_INFEASIBLE;
+        return PDCA_OK;
+    case PDCA_JACOBI_PERTURBED:
+        return p.delta0 > 0.0 ? PDCA_OK : PDCA_ERR_INFEASIBLE;
+    default:
+        return (p.delta0 > 0.0 && lambda > 0.0) ? PDCA_OK : PDCA_ERR_INFEASIBLE;
+    }
+}
+
+Coeffs make_coeffs(const pdca_params &p, double omega, double lambda) {
+    double g0, g1;
+    switch (p.precond) {
+    case PDCA_JACOBI_DAMPED:
+        g0 = (p.eps + p.c) / omega;
+        g1 = (p.eps + p.c + p.eta) / omega;
+        break;
+    case PDCA_JACOBI_PERTURBED:
+        g0 = 2.0 * p.eps + p.c + p.delta0;
+        g1 = g0 + p.eta;
+        break;
+    default:
+        g0 = p.eps * lambda + p.c + p.delta0;
+        g1 = g0 + p.eta;
+        break;
+    }
+    Coeffs cf;
+    cf.eps = (float)p.eps;
+    cf.inv_eps = (float)(1.0 / p.eps);
+    cf.c = (float)p.c;
+    cf.eta = (float)p.eta;
+    cf.inv_g0 = (float)(1.0 / g0);
+    cf.inv_g1 = (float)(1.0 / g1);
+    return cf;
+}
+
+// Host copy of row_ptr (copied from the device when it lives there) plus
+// its structural checks.
+pdca_status host_row_ptr(const int64_t *row_ptr, int32_t n, std::vector<int64_t> &keep,
+                         const int64_t **view) {
+    if (!row_ptr || n < 1) return PDCA_ERR_INVALID_ARG;
+    if (is_device_ptr(row_ptr)) {
+        keep.resize((size_t)n + 1);
+        if (cudaMemcpy(keep.data(), row_ptr, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyDefault) != cudaSuccess)
+            return PDCA_ERR_CUDA;
+        *view = keep.data();
+    } else {
+        *view = row_ptr;
+    }
+    const int64_t *rp = *view;
+    if (rp[0] != 0) return PDCA_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < n; ++i) {
+        const int64_t d = rp[i + 1] - rp[i];
+        if (d < 0 || d >= (1 << 24)) return PDCA_ERR_INVALID_ARG;
+    }
+    return PDCA_OK;
+}
+
+pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, int32_t sigma_req, Layout &L) {
+    L.n = n;
+    L.K = K;
+    L.nnz = rp[n];
+    L.n_slices = (n + kSliceRows - 1) / kSliceRows;
+    L.n_pad = L.n_slices * kSliceRows;
+    std::vector<int64_t> widths;
+    if (sigma_req) {
+        L.sigma = sigma_req;
+        L.sell_entries = sell_entries_for(rp, n, L.sigma, widths);
+    } else {
+        // smallest window (from 128 rows up) whose slice padding is <= 10%
+        for (int s = 128;; s <<= 1) {
+            L.sigma = s;
+            L.sell_entries = sell_entries_for(rp, n, s, widths);
+            if (s >= 8192 || (double)L.sell_entries <= kPadTarget * (double)std::max<int64_t>(L.nnz, 1)) break;
+        }
+    }
+    L.slice_off.assign((size_t)L.n_slices + 1, 0);
+    for (int32_t s = 0; s < L.n_slices; ++s) L.slice_off[s + 1] = L.slice_off[s] + widths[s] * kSliceRows;
+
+    const size_t P = (size_t)L.sell_entries, np = (size_t)L.n_pad, nn = (size_t)n;
+    const size_t parts = (size_t)std::max(1, energy_blocks(L.n_slices)) * kRedSlots;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + std::max<size_t>(bytes, 1)); return at; };
+    L.o_col = take(4 * P);
+    L.o_w = take(4 * P);
+    L.o_slice = take(8 * ((size_t)L.n_slices + 1));
+    L.o_rowinfo = take(4 * np);
+    L.o_perm = take(4 * np);
+    L.o_iperm = take(4 * nn);
+    for (int b = 0; b < 3; ++b) L.o_u[b] = take(4 * np * (size_t)K);
+    L.o_part = take(8 * parts);
+    L.o_red = take(sizeof(RedOut));
+    L.o_scal = take(8 * 8);
+    L.o_trace = take(8 * 2 * (size_t)kTraceCap);
+    L.persistent = o;
+    // create-time staging of the CSR input
+    L.o_srp = take(8 * (nn + 1));
+    L.o_scol = take(4 * (size_t)L.nnz);
+    L.o_sw = take(4 * (size_t)L.nnz);
+    L.o_sdeg = take(8 * nn);
+    L.o_smask = take(nn);
+    L.o_slab = take(4 * nn);
+    L.o_status = take(16);
+    L.total = o;
+    return PDCA_OK;
+}
+
+}  // namespace
+
+namespace pdca {
+void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace pdca
+
+struct pdca_problem {
+    Layout L;
+    pdca_params prm;
+    double omega = 0.5;
+    double lambda_used = 0.0, lambda_est = 0.0;
+    Coeffs cf;
+    cudaStream_t stream = nullptr;
+    char *ws = nullptr;
+    int32_t *sell_col = nullptr;
+    float *sell_w = nullptr;
+    int64_t *slice_off = nullptr;
+    uint32_t *rowinfo = nullptr;
+    int32_t *perm = nullptr, *iperm = nullptr;
+    float *U[3] = {nullptr, nullptr, nullptr};
+    double *partials = nullptr;
+    RedOut *red = nullptr;
+    double *scal = nullptr;    // [0] power scale, [1] power lambda
+    double *trace = nullptr;   // [0, cap) energy, [cap, 2 cap) residual
+    int cur = 0, prev = 1;
+    bool has_prev = false;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+
+    SellView view() const {
+        SellView A;
+        A.col = sell_col;
+        A.w = sell_w;
+        A.slice_off = slice_off;
+        A.rowinfo = rowinfo;
+        A.n_slices = L.n_slices;
+        A.n = L.n;
+        return A;
+    }
+    int spare() const { return has_prev ? 3 - cur - prev : (cur + 1) % 3; }
+};
+
+namespace {
+
+pdca_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PDCA_OK : PDCA_ERR_CUDA; }
+
+#define PDCA_TRY(expr)                         \
+    do {                                       \
+        cudaError_t _e = (expr);               \
+        if (_e != cudaSuccess) return PDCA_ERR_CUDA; \
+    } while (0)
+
+pdca_status sweep(pdca_problem *h, bool project, const float *src, const float *ut, float *dst) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (h->prof) {
+        while (h->ev.size() < h->ev_used + 2) {
+            cudaEvent_t e;
+            PDCA_TRY(cudaEventCreate(&e));
+            h->ev.push_back(e);
+        }
+        a = h->ev[h->ev_used];
+        b = h->ev[h->ev_used + 1];
+        h->ev_used += 2;
+        PDCA_TRY(cudaEventRecord(a, h->stream));
+    }
+    PDCA_TRY(launch_sweep(h->L.K, project, h->view(), h->cf, src, ut, dst, h->stream));
+    if (h->prof) PDCA_TRY(cudaEventRecord(b, h->stream));
+    return PDCA_OK;
+}
+
+// One outer step (Prop. nopre): sweeps ping-pong between the two buffers
+// that do not hold u^t; the last one projects rows for K >= 2.
+pdca_status outer_step(pdca_problem *h, int32_t inner) {
+    const int a = (h->cur + 1) % 3, b = (h->cur + 2) % 3;
+    const float *ut = h->U[h->cur];
+    const float *src = ut;
+    int last = h->cur;
+    for (int32_t s = 0; s < inner; ++s) {
+        const int dst = (s % 2 == 0) ? a : b;
+        const bool project = (h->L.K >= 2) && (s == inner - 1);
+        pdca_status st = sweep(h, project, src, ut, h->U[dst]);
+        if (st != PDCA_OK) return st;
+        src = h->U[dst];
+        last = dst;
+    }
+    h->prev = h->cur;
+    h->cur = last;
+    h->has_prev = true;
+    return PDCA_OK;
+}
+
+pdca_status reduce_energy(pdca_problem *h, double *trace_F, double *trace_r) {
+    const SellView A = h->view();
+    PDCA_TRY(launch_energy(h->L.K, A, h->cf, h->U[h->cur], h->has_prev ? h->U[h->prev] : nullptr,
+                           h->partials, h->stream));
+    PDCA_TRY(launch_energy_finalize(h->partials, energy_blocks(A.n_slices), h->prm.eps, h->prm.eta,
+                                    h->has_prev ? 1 : 0, h->red, trace_F, trace_r, h->stream));
+    return PDCA_OK;
+}
+
+pdca_status power_method(pdca_problem *h) {
+    const SellView A = h->view();
+    const int parts = energy_blocks(A.n_slices);
+    float *x = h->U[1], *y = h->U[2];
+    double *scale = h->scal, *lam = h->scal + 1;
+    PDCA_TRY(launch_power_init(A, h->perm, x, h->partials, h->stream));
+    PDCA_TRY(launch_power_finalize(h->partials, parts, scale, lam, h->stream));
+    for (int it = 0; it <= h->prm.power_iters; ++it) {
+        PDCA_TRY(launch_power_spmv(A, x, scale, y, h->partials, h->stream));
+        PDCA_TRY(launch_power_finalize(h->partials, parts, scale, lam, h->stream));
+        std::swap(x, y);
+    }
+    double lam_h = 0.0;
+    PDCA_TRY(cudaMemcpyAsync(&lam_h, lam, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    PDCA_TRY(cudaStreamSynchronize(h->stream));
+    h->lambda_est = lam_h;
+    h->lambda_used = std::min(2.0, 1.001 * lam_h);
+    return PDCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pdca_default_params(pdca_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->eps = 1.0;
+    p->c = 3.0;
+    p->eta = 1.0;
+    p->laplacian = PDCA_LAP_NORMALIZED;
+    p->precond = PDCA_JACOBI_PERTURBED;
+    p->damping = 0.5;
+    p->delta0 = 1e-6;
+    p->lambda_max = 0.0;
+    p->power_iters = 150;
+    p->precision = PDCA_FP32;
+    p->sort_window = 0;
+}
+
+const char *pdca_status_string(pdca_status s) {
+    switch (s) {
+    case PDCA_OK: return "ok";
+    case PDCA_ERR_INVALID_ARG: return "invalid argument";
+    case PDCA_ERR_NOT_SYMMETRIC: return "weight matrix is not symmetric";
+    case PDCA_ERR_ISOLATED_NODE: return "isolated node (degree not > 0)";
+    case PDCA_ERR_INFEASIBLE: return "preconditioner is not feasible (G > T fails)";
+    case PDCA_ERR_NONFINITE: return "non-finite value in the iterate";
+    case PDCA_ERR_OOM: return "workspace too small";
+    case PDCA_ERR_CUDA: return "CUDA runtime error";
+    case PDCA_ERR_TIMEOUT: return "bounded device wait ran out";
+    case PDCA_ERR_BAD_GRAPH: return "malformed graph or fidelity input";
+    }
+    return "unknown status";
+}
+
+uint64_t pdca_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+pdca_status pdca_workspace_size(const int64_t *row_ptr, int32_t n, int32_t k, const pdca_params *p,
+                                size_t *bytes) {
+    if (!bytes || k < 1 || k > PDCA_MAX_K || n < 1) return PDCA_ERR_INVALID_ARG;
+    pdca_params prm;
+    pdca_default_params(&prm);
+    if (p) prm = *p;
+    pdca_status st = check_params(prm);
+    if (st != PDCA_OK) return st;
+    std::vector<int64_t> keep;
+    const int64_t *rp = nullptr;
+    st = host_row_ptr(row_ptr, n, keep, &rp);
+    if (st != PDCA_OK) return st;
+    Layout L;
+    st = compute_layout(rp, n, k, prm.sort_window, L);
+    if (st != PDCA_OK) return st;
+    *bytes = L.total;
+    return PDCA_OK;
+}
+
+pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float *w, int32_t n, int32_t k,
+                        const uint8_t *fid_mask, const int32_t *labels, const pdca_params *p,
+                        void *workspace, size_t ws_bytes, void *stream, pdca_problem **out) {
+    if (!out) return PDCA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (k < 1 || k > PDCA_MAX_K || n < 1 || !fid_mask || !labels || !workspace) return PDCA_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return PDCA_ERR_INVALID_ARG;
+    pdca_params prm;
+    pdca_default_params(&prm);
+    if (p) prm = *p;
+    pdca_status st = check_params(prm);
+    if (st != PDCA_OK) return st;
+    const double omega = prm.damping;
+    if (prm.precond != PDCA_RICHARDSON || prm.lambda_max > 0) {
+        st = feasible(prm, omega, prm.lambda_max);
+        if (st != PDCA_OK) return st;
+    }
+    std::vector<int64_t> keep;
+    const int64_t *rp = nullptr;
+    st = host_row_ptr(row_ptr, n, keep, &rp);
+    if (st != PDCA_OK) return st;
+    const int64_t nnz = rp[n];
+    if (nnz > 0 && (!col || !w)) return PDCA_ERR_INVALID_ARG;
+
+    pdca_problem *h = new (std::nothrow) pdca_problem();
+    if (!h) return PDCA_ERR_INVALID_ARG;
+    st = compute_layout(rp, n, k, prm.sort_window, h->L);
+    if (st != PDCA_OK) { delete h; return st; }
+    if (ws_bytes < h->L.total) { delete h; return PDCA_ERR_OOM; }
+    h->prm = prm;
+    h->omega = omega;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->ws = static_cast<char *>(workspace);
+    const Layout &L = h->L;
+    char *W = h->ws;
+    h->sell_col = reinterpret_cast<int32_t *>(W + L.o_col);
+    h->sell_w = reinterpret_cast<float *>(W + L.o_w);
+    h->slice_off = reinterpret_cast<int64_t *>(W + L.o_slice);
+    h->rowinfo = reinterpret_cast<uint32_t *>(W + L.o_rowinfo);
+    h->perm = reinterpret_cast<int32_t *>(W + L.o_perm);
+    h->iperm = reinterpret_cast<int32_t *>(W + L.o_iperm);
+    for (int b = 0; b < 3; ++b) h->U[b] = reinterpret_cast<float *>(W + L.o_u[b]);
+    h->partials = reinterpret_cast<double *>(W + L.o_part);
+    h->red = reinterpret_cast<RedOut *>(W + L.o_red);
+    h->scal = reinterpret_cast<double *>(W + L.o_scal);
+    h->trace = reinterpret_cast<double *>(W + L.o_trace);
+    int64_t *s_rp = reinterpret_cast<int64_t *>(W + L.o_srp);
+    int32_t *s_col = reinterpret_cast<int32_t *>(W + L.o_scol);
+    float *s_w = reinterpret_cast<float *>(W + L.o_sw);
+    double *s_deg = reinterpret_cast<double *>(W + L.o_sdeg);
+    uint8_t *s_mask = reinterpret_cast<uint8_t *>(W + L.o_smask);
+    int32_t *s_lab = reinterpret_cast<int32_t *>(W + L.o_slab);
+    uint32_t *s_status = reinterpret_cast<uint32_t *>(W + L.o_status);
+    cudaStream_t sm = h->stream;
+
+    auto fail = [&](pdca_status s) { cudaStreamSynchronize(sm); delete h; return s; };
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, sm) : cudaSuccess;
+    };
+    if (cp(s_rp, rp, 8 * ((size_t)n + 1)) != cudaSuccess || cp(s_col, col, 4 * (size_t)nnz) != cudaSuccess ||
+        cp(s_w, w, 4 * (size_t)nnz) != cudaSuccess || cp(s_mask, fid_mask, (size_t)n) != cudaSuccess ||
+        cp(s_lab, labels, 4 * (size_t)n) != cudaSuccess ||
+        cudaMemsetAsync(s_status, 0, 16, sm) != cudaSuccess)
+        return fail(PDCA_ERR_CUDA);
+    if (launch_validate(n, k, s_rp, s_col, s_w, s_mask, s_lab, s_deg, s_status, sm) != cudaSuccess)
+        return fail(PDCA_ERR_CUDA);
+    uint32_t status = 0;
+    if (cudaMemcpyAsync(&status, s_status, 4, cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
+        cudaStreamSynchronize(sm) != cudaSuccess)
+        return fail(PDCA_ERR_CUDA);
+    if (status & kBadGraph) return fail(PDCA_ERR_BAD_GRAPH);
+    if (status & kNotSymmetric) return fail(PDCA_ERR_NOT_SYMMETRIC);
+    if (status & kIsolated) return fail(PDCA_ERR_ISOLATED_NODE);
+
+    if (launch_window_sort(n, L.n_pad, L.sigma, s_rp, h->perm, h->iperm, sm) != cudaSuccess ||
+        cp(h->slice_off, L.slice_off.data(), 8 * L.slice_off.size()) != cudaSuccess ||
+        launch_pack(n, L.n_pad, k, s_rp, s_col, s_w, s_deg, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
+                    h->sell_col, h->sell_w, h->rowinfo, sm) != cudaSuccess)
+        return fail(PDCA_ERR_CUDA);
+    if (prm.precond == PDCA_RICHARDSON) {
+        if (prm.lambda_max > 0) {
+            h->lambda_used = prm.lambda_max;
+        } else {
+            st = power_method(h);
+            if (st != PDCA_OK) return fail(st);
+        }
+        st = feasible(prm, omega, h->lambda_used);
+        if (st != PDCA_OK) return fail(st);
+    }
+    h->cf = make_coeffs(prm, omega, h->lambda_used);
+    if (launch_init_u(L.n_pad, k, h->rowinfo, h->U[0], sm) != cudaSuccess) return fail(PDCA_ERR_CUDA);
+    h->cur = 0;
+    h->prev = 1;
+    h->has_prev = false;
+    if (cudaStreamSynchronize(sm) != cudaSuccess) return fail(PDCA_ERR_CUDA);
+    *out = h;
+    return PDCA_OK;
+}
+
+pdca_status pdca_set_u(pdca_problem *h, const float *u) {
+    if (!h) return PDCA_ERR_INVALID_ARG;
+    const Layout &L = h->L;
+    const int stage = (h->cur + 1) % 3, target = (h->cur + 2) % 3;
+    if (!u) {
+        PDCA_TRY(launch_init_u(L.n_pad, L.K, h->rowinfo, h->U[target], h->stream));
+    } else {
+        const float *src = u;
+        if (!is_device_ptr(u)) {
+            PDCA_TRY(cudaMemcpyAsync(h->U[stage], u, sizeof(float) * (size_t)L.n * L.K, cudaMemcpyHostToDevice,
+                                     h->stream));
+            src = h->U[stage];
+        }
+        PDCA_TRY(launch_permute_in(L.K, L.n, L.n_pad, src, h->perm, h->U[target], h->stream));
+    }
+    h->cur = target;
+    h->prev = stage;
+    h->has_prev = false;
+    return PDCA_OK;
+}
+
+pdca_status pdca_step(pdca_problem *h, int32_t inner_sweeps) {
+    if (!h || inner_sweeps < 1) return PDCA_ERR_INVALID_ARG;
+    return outer_step(h, inner_sweeps);
+}
+
+pdca_status pdca_solve(pdca_problem *h, int32_t outer_iters, int32_t inner_sweeps, double damping,
+                       double *energy_trace, double *residual_trace) {
+    if (!h || outer_iters < 0 || inner_sweeps < 1 || !(damping >= 0.0)) return PDCA_ERR_INVALID_ARG;
+    if (damping > 0.0 && h->prm.precond == PDCA_JACOBI_DAMPED && damping != h->omega) {
+        pdca_status st = feasible(h->prm, damping, h->lambda_used);
+        if (st != PDCA_OK) return st;
+        h->omega = damping;
+        h->prm.damping = damping;
+        h->cf = make_coeffs(h->prm, h->omega, h->lambda_used);
+    }
+    const bool tracing = energy_trace || residual_trace;
+    int chunk0 = 0;
+    for (int32_t t = 0; t < outer_iters; ++t) {
+        pdca_status st = outer_step(h, inner_sweeps);
+        if (st != PDCA_OK) return st;
+        if (tracing) {
+            const int slot = t - chunk0;
+            st = reduce_energy(h, h->trace + slot, h->trace + kTraceCap + slot);
+            if (st != PDCA_OK) return st;
+            if (slot == kTraceCap - 1 || t == outer_iters - 1) {
+                const size_t cnt = (size_t)slot + 1;
+                if (energy_trace)
+                    PDCA_TRY(cudaMemcpyAsync(energy_trace + chunk0, h->trace, 8 * cnt, cudaMemcpyDefault, h->stream));
+                if (residual_trace)
+                    PDCA_TRY(cudaMemcpyAsync(residual_trace + chunk0, h->trace + kTraceCap, 8 * cnt,
+                                             cudaMemcpyDefault, h->stream));
+                PDCA_TRY(cudaStreamSynchronize(h->stream));
+                chunk0 = t + 1;
+            }
+        }
+    }
+    return PDCA_OK;
+}
+
+pdca_status pdca_energy(pdca_problem *h, double *F, double *rel_residual) {
+    if (!h) return PDCA_ERR_INVALID_ARG;
+    pdca_status st = reduce_energy(h, nullptr, nullptr);
+    if (st != PDCA_OK) return st;
+    RedOut o;
+    PDCA_TRY(cudaMemcpyAsync(&o, h->red, sizeof(RedOut), cudaMemcpyDeviceToHost, h->stream));
+    PDCA_TRY(cudaStreamSynchronize(h->stream));
+    if (F) *F = o.F;
+    if (rel_residual) *rel_residual = o.rel_res;
+    if (o.nonfinite > 0 || !std::isfinite(o.F)) return PDCA_ERR_NONFINITE;
+    return PDCA_OK;
+}
+
+pdca_status pdca_get_u(pdca_problem *h, float *u_out) {
+    if (!h || !u_out) return PDCA_ERR_INVALID_ARG;
+    const Layout &L = h->L;
+    if (is_device_ptr(u_out)) {
+        PDCA_TRY(launch_permute_out(L.K, L.n, h->U[h->cur], h->perm, u_out, h->stream));
+        PDCA_TRY(cudaStreamSynchronize(h->stream));
+        return PDCA_OK;
+    }
+    float *stage = h->U[h->spare()];
+    PDCA_TRY(launch_permute_out(L.K, L.n, h->U[h->cur], h->perm, stage, h->stream));
+    PDCA_TRY(cudaMemcpyAsync(u_out, stage, sizeof(float) * (size_t)L.n * L.K, cudaMemcpyDeviceToHost, h->stream));
+    PDCA_TRY(cudaStreamSynchronize(h->stream));
+    return PDCA_OK;
+}
+
+pdca_status pdca_labels(pdca_problem *h, int32_t *labels_out) {
+    if (!h || !labels_out) return PDCA_ERR_INVALID_ARG;
+    const Layout &L = h->L;
+    if (is_device_ptr(labels_out)) {
+        PDCA_TRY(launch_labels(L.K, L.n, h->U[h->cur], h->perm, labels_out, h->stream));
+        PDCA_TRY(cudaStreamSynchronize(h->stream));
+        return PDCA_OK;
+    }
+    int32_t *stage = reinterpret_cast<int32_t *>(h->U[h->spare()]);
+    PDCA_TRY(launch_labels(L.K, L.n, h->U[h->cur], h->perm, stage, h->stream));
+    PDCA_TRY(cudaMemcpyAsync(labels_out, stage, sizeof(int32_t) * (size_t)L.n, cudaMemcpyDeviceToHost, h->stream));
+    PDCA_TRY(cudaStreamSynchronize(h->stream));
+    return PDCA_OK;
+}
+
+pdca_status pdca_lambda_max(pdca_problem *h, double *lambda_used, double *lambda_estimate) {
+    if (!h) return PDCA_ERR_INVALID_ARG;
+    if (lambda_used) *lambda_used = h->lambda_used;
+    if (lambda_estimate) *lambda_estimate = h->lambda_est;
+    return PDCA_OK;
+}
+
+pdca_status pdca_layout(pdca_problem *h, int64_t *sell_entries, int64_t *n_slices, int32_t *sort_window) {
+    if (!h) return PDCA_ERR_INVALID_ARG;
+    if (sell_entries) *sell_entries = h->L.sell_entries;
+    if (n_slices) *n_slices = h->L.n_slices;
+    if (sort_window) *sort_window = h->L.sigma;
+    return PDCA_OK;
+}
+
+pdca_status pdca_profile_enable(pdca_problem *h, int32_t on) {
+    if (!h) return PDCA_ERR_INVALID_ARG;
+    h->prof = on != 0;
+    return PDCA_OK;
+}
+
+pdca_status pdca_profile_read(pdca_problem *h, double *sweep_ms, int64_t *sweep_launches) {
+    if (!h) return PDCA_ERR_INVALID_ARG;
+    PDCA_TRY(cudaStreamSynchronize(h->stream));
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+        float ms = 0.f;
+        PDCA_TRY(cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]));
+        tot += ms;
+    }
+    if (sweep_ms) *sweep_ms = tot;
+    if (sweep_launches) *sweep_launches = (int64_t)(h->ev_used / 2);
+    h->ev_used = 0;
+    return PDCA_OK;
+}
+
+void pdca_destroy(pdca_problem *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// Internal declarations shared by the library's translation units.
+//
+// Data layout in device memory (all inside the caller's workspace):
+//   * nodes are renumbered: inside every window of `sigma` consecutive rows,
+//     rows are sorted by degree (descending, ties by original index); the
+//     renumbering is applied to rows and columns alike, so u, the tags and
+//     the operator all live in the new order;
+//   * the operator D^{-1/2} W D^{-1/2} (Sec. 2.2) is stored as sliced ELL
+//     with slices of 32 rows (one warp, one lane per row): entry j of lane l
+//     of slice s sits at slice_off[s] + 32 j + l, so a warp reads 128
+//     contiguous bytes of column indices and of weights per entry step;
+//     slice width = longest row of the slice; padding entries point at the
+//     row itself with weight 0;
+//   * rowinfo[r] = (row length << 8) | tag, tag = prior class or 0xFF;
+//   * u is n_pad x K float32 row-major (n_pad = 32 * number of slices).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pdca.h"
+
+namespace pdca {
+
+constexpr int kSliceRows = 32;
+constexpr uint32_t kTagUnlabelled = 0xFFu;
+constexpr int kBlockThreads = 256;             // 8 warps = 8 slices per block
+constexpr int kWarpsPerBlock = kBlockThreads / 32;
+constexpr int kRedSlots = 8;                   // doubles per block partial
+
+// Validation status bits (OR-ed by the validation kernel).
+constexpr uint32_t kBadGraph = 1u;
+constexpr uint32_t kNotSymmetric = 2u;
+constexpr uint32_t kIsolated = 4u;
+
+struct SellView {
+    const int32_t *col;        // padded sliced-ELL column indices (new numbering)
+    const float *w;            // w_ij / sqrt(d_i d_j), FP32
+    const int64_t *slice_off;  // n_slices + 1 entry offsets
+    const uint32_t *rowinfo;   // (len << 8) | tag, n_pad
+    int32_t n_slices;
+    int32_t n;                 // real rows; rows >= n are padding
+};
+
+// Scalars of one sweep (Sec. 3): T = eps L_s + eta Lambda + c I and the two
+// values of 1/g_i (unlabelled, labelled rows).
+struct Coeffs {
+    float eps, inv_eps, c, eta, inv_g0, inv_g1;
+};
+
+// Reduction results written by finalize kernels.
+struct RedOut {
+    double F;           // energy
+    double rel_res;     // ||b - T u|| / ||b|| (NaN if no previous iterate)
+    double quad, well, fid, rr, bb;
+    double nonfinite;
+};
+
+// --- sweep / reductions (sweep_kernels.cu) ---------------------------------
+cudaError_t launch_sweep(int K, bool project, const SellView &A, const Coeffs &cf,
+                         const float *v_src, const float *u_t, float *v_dst, cudaStream_t st);
+cudaError_t launch_energy(int K, const SellView &A, const Coeffs &cf, const float *u,
+                          const float *u_prev, double *partials, cudaStream_t st);
+cudaError_t launch_energy_finalize(const double *partials, int n_parts, double eps, double eta,
+                                   int has_prev, RedOut *out, double *trace_F,
+                                   double *trace_r, cudaStream_t st);
+cudaError_t launch_power_init(const SellView &A, const int32_t *perm, float *x,
+                              double *partials, cudaStream_t st);
+cudaError_t launch_power_spmv(const SellView &A, const float *x, const double *scale,
+                              float *y, double *partials, cudaStream_t st);
+cudaError_t launch_power_finalize(const double *partials, int n_parts, double *scale,
+                                  double *lambda, cudaStream_t st);
+cudaError_t launch_labels(int K, int32_t n, const float *u, const int32_t *perm,
+                          int32_t *out, cudaStream_t st);
+cudaError_t launch_permute_out(int K, int32_t n, const float *u, const int32_t *perm,
+                               float *out, cudaStream_t st);
+cudaError_t launch_permute_in(int K, int32_t n, int32_t n_pad, const float *in,
+                              const int32_t *perm, float *u, cudaStream_t st);
+int energy_blocks(int32_t n_slices);
+
+// --- preparation (prep_kernels.cu) -----------------------------------------
+cudaError_t launch_validate(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *col,
+                            const float *w, const uint8_t *mask, const int32_t *labels,
+                            double *deg, uint32_t *status, cudaStream_t st);
+cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const int64_t *row_ptr,
+                               int32_t *perm, int32_t *iperm, cudaStream_t st);
+cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_ptr,
+                        const int32_t *col, const float *w, const double *deg,
+                        const uint8_t *mask, const int32_t *labels, const int32_t *perm,
+                        const int32_t *iperm, const int64_t *slice_off, int32_t *sell_col,
+                        float *sell_w, uint32_t *rowinfo, cudaStream_t st);
+cudaError_t launch_init_u(int32_t n_pad, int32_t K, const uint32_t *rowinfo, float *u,
+                          cudaStream_t st);
+
+// Kernel launch counter (every launch_* above adds its launches).
+void count_launches(uint64_t k);
+
+}  // namespace pdca

@@ -1,0 +1,202 @@
+// Operator preparation on the GPU (create time, Sec. 2.2):
+//   validate_kernel     CSR checks (range, no self loop, strictly increasing
+//                       columns, finite non-negative weights, w_ij == w_ji)
+//                       and the degrees d_i = sum_j w_ij (FP64, CSR order);
+//   window_sort_kernel  renumbering: rows sorted by degree inside windows;
+//   pack_kernel         sliced-ELL with w_ij / sqrt(d_i d_j) and the row tags;
+//   init_u_kernel       u^0 (prior on labelled rows, centre elsewhere).
+#include "pdca_internal.cuh"
+
+#include <math.h>
+
+namespace pdca {
+namespace {
+
+__global__ void validate_kernel(int32_t n, int32_t K, const int64_t *__restrict__ row_ptr,
+                                const int32_t *__restrict__ col, const float *__restrict__ w,
+                                const uint8_t *__restrict__ mask, const int32_t *__restrict__ labels,
+                                double *__restrict__ deg, uint32_t *__restrict__ status) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t bad = 0;
+    double d = 0.0;
+    int32_t prev = -1;
+    const int64_t e0 = row_ptr[i], e1 = row_ptr[i + 1];
+    for (int64_t e = e0; e < e1; ++e) {
+        const int32_t j = col[e];
+        const float wv = w[e];
+        if (j < 0 || j >= n) {
+            bad |= kBadGraph;
+            continue;
+        }
+        if (j == i || j <= prev) bad |= kBadGraph;
+        prev = j > prev ? j : prev;
+        if (!(isfinite(wv) && wv >= 0.0f)) bad |= kBadGraph;
+        d += (double)wv;
+        // w_ji must be stored with the same value: binary search in row j
+        int64_t lo = row_ptr[j], hi = row_ptr[j + 1] - 1;
+        bool ok = false;
+        while (lo <= hi) {
+            const int64_t mid = lo + ((hi - lo) >> 1);
+            const int32_t cm = col[mid];
+            if (cm == i) {
+                ok = (w[mid] == wv);
+                break;
+            }
+            if (cm < i) lo = mid + 1;
+            else hi = mid - 1;
+        }
+        if (!ok) bad |= kNotSymmetric;
+    }
+    if (!(d > 0.0)) bad |= kIsolated;
+    const uint8_t m = mask[i];
+    if (m > 1) bad |= kBadGraph;
+    if (m == 1) {
+        const int32_t l = labels[i];
+        const int32_t hiK = K == 1 ? 2 : K;
+        if (l < 0 || l >= hiK) bad |= kBadGraph;
+    }
+    deg[i] = d;
+    if (bad) atomicOr(status, bad);
+}
+
+// One block per window of `sigma` rows: bitonic sort of keys
+// ((2^32-1 - degree) << 32 | position), i.e. degree descending, ties by the
+// original index.  Rows past n sort last and become padding (perm = -1).
+__global__ void window_sort_kernel(int32_t n, int32_t n_pad, int32_t sigma,
+                                   const int64_t *__restrict__ row_ptr, int32_t *__restrict__ perm,
+                                   int32_t *__restrict__ iperm) {
+    extern __shared__ unsigned long long keys[];
+    const int64_t base = (int64_t)blockIdx.x * sigma;
+    for (int p = threadIdx.x; p < sigma; p += blockDim.x) {
+        const int64_t i = base + p;
+        unsigned long long key = ~0ull;
+        if (i < n) {
+            const uint32_t dgr = (uint32_t)(row_ptr[i + 1] - row_ptr[i]);
+            key = ((unsigned long long)(0xFFFFFFFFu - dgr) << 32) | (uint32_t)p;
+        }
+        keys[p] = key;
+    }
+    __syncthreads();
+    for (int k = 2; k <= sigma; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int p = threadIdx.x; p < sigma; p += blockDim.x) {
+                const int q = p ^ jj;
+                if (q > p) {
+                    const unsigned long long a = keys[p], b = keys[q];
+                    const bool up = (p & k) == 0;
+                    if ((a > b) == up) {
+                        keys[p] = b;
+                        keys[q] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int p = threadIdx.x; p < sigma; p += blockDim.x) {
+        const int64_t r = base + p;
+        if (r >= n_pad) continue;
+        const unsigned long long key = keys[p];
+        if (key == ~0ull) {
+            perm[r] = -1;
+        } else {
+            const int32_t old = (int32_t)(base + (int64_t)(key & 0xFFFFFFFFull));
+            perm[r] = old;
+            iperm[old] = (int32_t)r;
+        }
+    }
+}
+
+__global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
+                            const int32_t *__restrict__ col, const float *__restrict__ w,
+                            const double *__restrict__ deg, const uint8_t *__restrict__ mask,
+                            const int32_t *__restrict__ labels, const int32_t *__restrict__ perm,
+                            const int32_t *__restrict__ iperm, const int64_t *__restrict__ slice_off,
+                            int32_t *__restrict__ sell_col, float *__restrict__ sell_w,
+                            uint32_t *__restrict__ rowinfo) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_pad) return;
+    const int32_t s = r >> 5, lane = r & 31;
+    const int64_t base = slice_off[s];
+    const int32_t width = (int32_t)((slice_off[s + 1] - base) >> 5);
+    const int32_t old = perm[r];
+    int32_t len = 0;
+    uint32_t tag = kTagUnlabelled;
+    if (old >= 0) {
+        const int64_t e0 = row_ptr[old];
+        len = (int32_t)(row_ptr[old + 1] - e0);
+        const double di = deg[old];
+        for (int32_t j = 0; j < len; ++j) {
+            const int32_t oj = col[e0 + j];
+            const int64_t at = base + 32 * (int64_t)j + lane;
+            sell_col[at] = iperm[oj];
+            sell_w[at] = (float)((double)w[e0 + j] / sqrt(di * deg[oj]));
+        }
+        if (mask[old]) tag = (uint32_t)labels[old];
+    }
+    for (int32_t j = len; j < width; ++j) {
+        const int64_t at = base + 32 * (int64_t)j + lane;
+        sell_col[at] = r;
+        sell_w[at] = 0.0f;
+    }
+    rowinfo[r] = ((uint32_t)len << 8) | tag;
+}
+
+__global__ void init_u_kernel(int32_t n_pad, int32_t K, const uint32_t *__restrict__ rowinfo,
+                              float *__restrict__ u) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n_pad * K) return;
+    const int64_t r = q / K;
+    const int32_t k = (int32_t)(q - r * K);
+    const uint32_t tag = rowinfo[r] & 0xFFu;
+    float v;
+    if (tag == kTagUnlabelled) v = K == 1 ? 0.0f : 2.0f / K - 1.0f;
+    else if (K == 1) v = tag == 1u ? 1.0f : -1.0f;
+    else v = tag == (uint32_t)k ? 1.0f : -1.0f;
+    u[q] = v;
+}
+
+}  // namespace
+
+cudaError_t launch_validate(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *col,
+                            const float *w, const uint8_t *mask, const int32_t *labels, double *deg,
+                            uint32_t *status, cudaStream_t st) {
+    count_launches(1);
+    validate_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, K, row_ptr, col, w, mask, labels, deg, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const int64_t *row_ptr,
+                               int32_t *perm, int32_t *iperm, cudaStream_t st) {
+    const size_t smem = (size_t)sigma * sizeof(unsigned long long);
+    cudaError_t e = cudaFuncSetAttribute(window_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int windows = (int)(((int64_t)n + sigma - 1) / sigma);
+    const int threads = sigma / 2 < 1024 ? sigma / 2 : 1024;
+    count_launches(1);
+    window_sort_kernel<<<windows, threads, smem, st>>>(n, n_pad, sigma, row_ptr, perm, iperm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_ptr, const int32_t *col,
+                        const float *w, const double *deg, const uint8_t *mask, const int32_t *labels,
+                        const int32_t *perm, const int32_t *iperm, const int64_t *slice_off,
+                        int32_t *sell_col, float *sell_w, uint32_t *rowinfo, cudaStream_t st) {
+    (void)n;
+    (void)K;
+    count_launches(1);
+    pack_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, mask, labels, perm,
+                                                     iperm, slice_off, sell_col, sell_w, rowinfo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_u(int32_t n_pad, int32_t K, const uint32_t *rowinfo, float *u, cudaStream_t st) {
+    const int64_t tot = (int64_t)n_pad * K;
+    count_launches(1);
+    init_u_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n_pad, K, rowinfo, u);
+    return cudaGetLastError();
+}
+
+}  // namespace pdca

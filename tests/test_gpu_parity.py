@@ -1,0 +1,418 @@
+"""Parity of the CUDA pDCA path with the FP64 oracle (GPU required).
+
+Bar (FP32 path): relative L2 error of u at most 1e-5 after every outer step;
+identical labels except at ties (|u_i| < 1e-6 for K = 1, top-two gap < 1e-6
+for K >= 2); energies within 1e-5 relative.  Every case runs through the C
+interface (ctypes binding of libpdca.so).
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gen import make_workload, random_graph, csr_from_pairs
+
+pytestmark = pytest.mark.gpu
+
+TOL_U = 1e-5
+TOL_F = 1e-5
+
+
+@pytest.fixture(scope="module")
+def B(cuda_lib):
+    from paper_2303_14495_gb300 import binding
+    return binding
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def label_mismatch(lab_gpu, u_ref, K):
+    """Indices where labels differ, excluding ties of the oracle iterate."""
+    if K == 1:
+        ref = (u_ref >= 0).astype(np.int32)
+        tie = np.abs(u_ref) < 1e-6
+    else:
+        ref = np.argmax(u_ref, axis=1).astype(np.int32)
+        srt = np.sort(u_ref, axis=1)
+        tie = (srt[:, -1] - srt[:, -2]) < 1e-6
+    return np.nonzero((lab_gpu != ref) & ~tie)[0]
+
+
+def make_pair(B, rp, col, w, K, mask, lab, eps, eta, c, precond, damping=0.5, lam=0.0,
+              sort_window=0, omp=False):
+    prm = B.make_params(eps=eps, eta=eta, c=c, precond=precond, damping=damping, lambda_max=lam,
+                        sort_window=sort_window)
+    gpu = B.Problem(rp, col, w, K, mask, lab, prm)
+    ref = oracle.Problem(rp, col, w, K, mask, lab, eps, eta, c, precond=precond, damping=damping,
+                         lambda_max=lam, omp=omp)
+    return gpu, ref
+
+
+def run_parity(gpu, ref, outer, inner, check_energy=True):
+    """Step both sides one outer step at a time and compare after each."""
+    u_ref = ref.init_u()
+    u0 = gpu.get_u()
+    assert rel_l2(u0, u_ref) <= 1e-7
+    errs = []
+    for t in range(outer):
+        gpu.step(inner)
+        u_ref, e_ref, r_ref = ref.solve(1, inner, u_ref)
+        u = gpu.get_u()
+        err = rel_l2(u, u_ref)
+        errs.append(err)
+        assert err <= TOL_U, f"step {t}: rel L2 {err:.3e}"
+        if check_energy:
+            F, rel = gpu.energy()
+            assert abs(F - e_ref[0]) <= TOL_F * abs(e_ref[0]), (t, F, e_ref[0])
+            assert abs(rel - r_ref[0]) <= 1e-3 * abs(r_ref[0]) + 1e-7, (t, rel, r_ref[0])
+    lab = gpu.labels()
+    bad = label_mismatch(lab, u_ref, gpu.K)
+    assert bad.size == 0, f"{bad.size} label mismatches"
+    return errs
+
+
+# ---------------------------------------------------------------------------
+# small random graphs: ragged tails, every K, every preconditioner
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [2, 31, 33, 257, 1031])
+@pytest.mark.parametrize("K", [1, 3, 4])
+def test_random_graph_sizes(B, n, K):
+    rp, col, w = random_graph(n, 6, seed=n * 7 + K)
+    rng = np.random.default_rng(n + K)
+    mask = (rng.uniform(size=n) < 0.2).astype(np.uint8)
+    lab = rng.integers(0, max(K, 2), size=n).astype(np.int32)
+    gpu, ref = make_pair(B, rp, col, w, K, mask, lab, 1.0, 5.0, 4.0, B.PDCA_JACOBI_PERTURBED)
+    run_parity(gpu, ref, 4, 3)
+
+
+@pytest.mark.parametrize("K", [2, 5, 6, 7, 8, 10, 12, 16])
+def test_every_K(B, K):
+    n = 613
+    rp, col, w = random_graph(n, 8, seed=K)
+    rng = np.random.default_rng(K)
+    mask = (rng.uniform(size=n) < 0.1).astype(np.uint8)
+    lab = rng.integers(0, K, size=n).astype(np.int32)
+    gpu, ref = make_pair(B, rp, col, w, K, mask, lab, 1.0, 50.0, 52.0, B.PDCA_JACOBI_DAMPED, damping=0.8)
+    run_parity(gpu, ref, 5, 4)
+
+
+@pytest.mark.parametrize("precond", [0, 1, 2])
+@pytest.mark.parametrize("setting", ["config", "paper"])
+def test_preconditioners(B, precond, setting):
+    n = 900
+    rp, col, w = random_graph(n, 10, seed=3)
+    rng = np.random.default_rng(5)
+    mask = (rng.uniform(size=n) < 0.05).astype(np.uint8)
+    lab = rng.integers(0, 2, size=n).astype(np.int32)
+    if setting == "config":
+        eps, eta, c, om = 1.0, 500.0, 502.0, 0.8
+    else:  # eps=100, c=11, eta=100 (Sec. 5); damped Jacobi at the paper's omega = 1/2
+        eps, eta, c, om = 100.0, 100.0, 11.0, 0.5
+    lam = 0.0
+    if precond == 2:
+        lam = oracle.safe_lambda(oracle.Problem(rp, col, w, 1, mask, lab, eps, eta, c).power_max_eig(150))
+    gpu, ref = make_pair(B, rp, col, w, 1, mask, lab, eps, eta, c, precond, damping=om, lam=lam)
+    run_parity(gpu, ref, 6, 4)
+
+
+@pytest.mark.parametrize("sw", [32, 64, 128, 1024, 8192])
+def test_sort_windows(B, sw):
+    n = 5000
+    rp, col, w = random_graph(n, 12, seed=sw)
+    rng = np.random.default_rng(sw)
+    mask = (rng.uniform(size=n) < 0.05).astype(np.uint8)
+    lab = rng.integers(0, 4, size=n).astype(np.int32)
+    gpu, ref = make_pair(B, rp, col, w, 4, mask, lab, 1.0, 20.0, 22.0, B.PDCA_JACOBI_PERTURBED,
+                         sort_window=sw)
+    assert gpu.layout()["sort_window"] == sw
+    run_parity(gpu, ref, 3, 3)
+
+
+def test_hub_rows(B):
+    """A star-like hub (degree n-1) next to short rows: very uneven slices."""
+    n = 700
+    i = np.zeros(n - 1, np.int64)
+    j = np.arange(1, n)
+    extra = np.arange(1, n - 1)
+    I = np.concatenate([i, extra])
+    J = np.concatenate([j, extra + 1])
+    w = np.random.default_rng(0).uniform(0.1, 1, I.size).astype(np.float32)
+    rp, col, ww = csr_from_pairs(n, I, J, w)
+    mask = np.zeros(n, np.uint8)
+    mask[[3, 400]] = 1
+    lab = np.zeros(n, np.int32)
+    lab[400] = 1
+    gpu, ref = make_pair(B, rp, col, ww, 1, mask, lab, 1.0, 10.0, 12.0, B.PDCA_JACOBI_PERTURBED)
+    run_parity(gpu, ref, 5, 5)
+
+
+# ---------------------------------------------------------------------------
+# the synthetic workloads (full size where the oracle finishes in seconds)
+# ---------------------------------------------------------------------------
+
+def workload_pair(B, wl, omp=True, lam=None):
+    p = wl.params
+    if p["precond"] == 2 and lam is None:
+        lam = oracle.safe_lambda(oracle.Problem(wl.row_ptr, wl.col, wl.w, 1, wl.fid_mask, wl.fid_labels,
+                                                p["eps"], p["eta"], p["c"], omp=omp).power_max_eig(150))
+    return make_pair(B, wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, p["eps"], p["eta"],
+                     p["c"], p["precond"], damping=p["damping"] or 0.5, lam=lam or 0.0, omp=omp)
+
+
+def test_moons2k(B):
+    wl = make_workload("moons2k")
+    gpu, ref = workload_pair(B, wl)
+    p = wl.params
+    run_parity(gpu, ref, p["outer"], p["inner"])
+
+
+def test_ellipses256(B):
+    wl = make_workload("ellipses256")
+    gpu, ref = workload_pair(B, wl)
+    run_parity(gpu, ref, wl.params["outer"], wl.params["inner"])
+
+
+def test_ellipses256_paper_setting(B):
+    """eps = 100, c = 11, eta = 100 with 4 Richardson sweeps (Sec. 5)."""
+    wl = make_workload("ellipses256")
+    rp, col, w = wl.row_ptr, wl.col, wl.w
+    lam = oracle.safe_lambda(oracle.Problem(rp, col, w, 1, wl.fid_mask, wl.fid_labels, 100, 100, 11,
+                                            omp=True).power_max_eig(150))
+    gpu, ref = make_pair(B, rp, col, w, 1, wl.fid_mask, wl.fid_labels, 100.0, 100.0, 11.0,
+                         B.PDCA_RICHARDSON, lam=lam, omp=True)
+    run_parity(gpu, ref, 8, 4)
+
+
+def test_gmm70k(B):
+    wl = make_workload("gmm70k")
+    gpu, ref = workload_pair(B, wl)
+    run_parity(gpu, ref, wl.params["outer"], wl.params["inner"])
+
+
+def test_voronoi_small(B):
+    wl = make_workload("voronoi2048", size=256)
+    gpu, ref = workload_pair(B, wl)
+    run_parity(gpu, ref, wl.params["outer"], wl.params["inner"])
+
+
+def test_voronoi2048_full(B):
+    """The 4M-node, K = 4 graph at full size, in the benchmark's configuration
+    (4 outer steps x 8 Richardson sweeps), element by element against the
+    OpenMP build of the oracle."""
+    wl = make_workload("voronoi2048")
+    gpu, ref = workload_pair(B, wl)
+    run_parity(gpu, ref, wl.params["outer"], wl.params["inner"], check_energy=False)
+    F, _ = gpu.energy()
+    e_ref = ref.energy(gpu.get_u())
+    # energy of the same (GPU) iterate: FP32-row / FP64-sum reduction vs FP64
+    assert abs(F - e_ref) <= TOL_F * abs(e_ref)
+
+
+# ---------------------------------------------------------------------------
+# power method, energy, residual, labels
+# ---------------------------------------------------------------------------
+
+def complete(n, a=0.4):
+    i, j = np.triu_indices(n, 1)
+    return csr_from_pairs(n, i, j, np.full(i.size, a, np.float32))
+
+
+def path(n):
+    i = np.arange(n - 1)
+    return csr_from_pairs(n, i, i + 1, np.linspace(0.3, 1.0, n - 1).astype(np.float32))
+
+
+@pytest.mark.parametrize("graph,expect", [
+    (lambda: complete(2), 2.0), (lambda: complete(40), 40 / 39), (lambda: path(64), None),
+])
+def test_power_method_closed_forms(B, graph, expect):
+    rp, col, w = graph()
+    n = rp.size - 1
+    prm = B.make_params(precond=B.PDCA_RICHARDSON, power_iters=3000)
+    g = B.Problem(rp, col, w, 1, np.zeros(n, np.uint8), np.zeros(n, np.int32), prm)
+    used, est = g.lambda_max()
+    if expect is None:  # bipartite path: 2 at convergence; 3000 iterations get close
+        W = np.zeros((n, n))
+        for i in range(n):
+            W[i, col[rp[i]:rp[i + 1]]] = w[rp[i]:rp[i + 1]]
+        d = W.sum(1)
+        expect = np.linalg.eigvalsh(np.eye(n) - W / np.sqrt(np.outer(d, d))).max()
+        assert abs(est - expect) < 1e-3
+    else:
+        assert abs(est - expect) < 1e-5 * expect
+    assert used == min(2.0, 1.001 * est)
+
+
+def test_power_method_vs_oracle(B):
+    wl = make_workload("ellipses256")
+    prm = B.params_from_workload(wl.params)
+    g = B.Problem(wl.row_ptr, wl.col, wl.w, 1, wl.fid_mask, wl.fid_labels, prm)
+    used, est = g.lambda_max()
+    ref = oracle.Problem(wl.row_ptr, wl.col, wl.w, 1, wl.fid_mask, wl.fid_labels, 1, 1, 1, omp=True)
+    lam = ref.power_max_eig(150)
+    assert abs(est - lam) <= 2e-5 * lam
+    assert 0 < est <= 2.0
+
+
+def test_energy_trace_monotone_binary(B):
+    """Thm. decay:energy on the GPU: F(u^t) non-increasing (binary model, c
+    large enough for P_2 to be convex on the iterates)."""
+    wl = make_workload("moons2k")
+    p = wl.params
+    g = B.Problem(wl.row_ptr, wl.col, wl.w, 1, wl.fid_mask, wl.fid_labels, B.params_from_workload(p))
+    F0, r0 = g.energy()
+    assert np.isnan(r0)
+    e, r = g.solve(30, 5, trace=True)
+    seq = np.concatenate([[F0], e])
+    assert np.all(np.diff(seq) <= 1e-6 * np.abs(seq[:-1])), seq
+    assert np.all(np.isfinite(r)) and np.all(r >= 0)
+    # trace equals a separate energy evaluation of the final iterate
+    F, rel = g.energy()
+    assert F == e[-1] and rel == r[-1]
+
+
+def test_labels_tie_rule(B):
+    rp, col, w = complete(5)
+    g = B.Problem(rp, col, w, 3, np.zeros(5, np.uint8), np.zeros(5, np.int32), B.make_params())
+    u = np.array([[0.1, 0.1, -1], [-1, 0.2, 0.2], [0.3, -0.2, 0.3], [-1, -1, 0], [0, 0, 0]], np.float32)
+    g.set_u(u)
+    np.testing.assert_array_equal(g.get_u(), u)
+    np.testing.assert_array_equal(g.labels(), [0, 1, 0, 2, 0])
+    g1 = B.Problem(rp, col, w, 1, np.zeros(5, np.uint8), np.zeros(5, np.int32), B.make_params())
+    g1.set_u(np.array([0.0, -1e-9, 2.0, -3.0, 1e-30], np.float32))
+    np.testing.assert_array_equal(g1.labels(), [1, 0, 1, 0, 1])
+
+
+def test_nonfinite_detected(B):
+    rp, col, w = complete(6)
+    g = B.Problem(rp, col, w, 1, np.zeros(6, np.uint8), np.zeros(6, np.int32), B.make_params())
+    g.set_u(np.array([0, 1, np.nan, 0, 0, 0], np.float32))
+    with pytest.raises(B.PdcaError, match="NONFINITE"):
+        g.energy()
+
+
+# ---------------------------------------------------------------------------
+# interface behaviour: checkpoint/resume, device pointers, determinism, errors
+# ---------------------------------------------------------------------------
+
+def test_checkpoint_resume_bit_exact(B):
+    wl = make_workload("gmm70k", n_per=500, dim=64)
+    p = wl.params
+    prm = B.params_from_workload(p)
+    a = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm)
+    a.solve(10, 5)
+    ua = a.get_u()
+    b = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm)
+    b.solve(5, 5)
+    ck = b.get_u()
+    c = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm)
+    c.set_u(ck)
+    c.solve(5, 5)
+    np.testing.assert_array_equal(c.get_u(), ua)
+    # a second run is bit-identical (deterministic reductions)
+    d = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm)
+    d.solve(10, 5)
+    np.testing.assert_array_equal(d.get_u(), ua)
+    assert a.energy() == d.energy()
+
+
+def test_device_pointers(B):
+    import torch
+    wl = make_workload("ellipses256", size=64)
+    p = wl.params
+    prm = B.params_from_workload(p)
+    host = B.Problem(wl.row_ptr, wl.col, wl.w, 1, wl.fid_mask, wl.fid_labels, prm)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dev = B.Problem(t(wl.row_ptr), t(wl.col), t(wl.w), 1, t(wl.fid_mask), t(wl.fid_labels), prm)
+    host.solve(3, 5)
+    dev.solve(3, 5)
+    ud = torch.empty(wl.n, dtype=torch.float32, device="cuda")
+    dev.get_u(ud)
+    np.testing.assert_array_equal(ud.cpu().numpy(), host.get_u())
+    ld = torch.empty(wl.n, dtype=torch.int32, device="cuda")
+    dev.labels(ld)
+    np.testing.assert_array_equal(ld.cpu().numpy(), host.labels())
+    dev.set_u(ud * 0.5)
+    np.testing.assert_array_equal(dev.get_u(), host.get_u() * np.float32(0.5))
+
+
+def test_two_streams_independent(B):
+    import torch
+    wl = make_workload("voronoi2048", size=128)
+    prm = B.params_from_workload(wl.params)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    a = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm, stream=s1)
+    b = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm, stream=s2)
+    a.solve(4, 8)
+    b.solve(4, 8)
+    np.testing.assert_array_equal(a.get_u(), b.get_u())
+
+
+def _err_create(B, rp, col, w, n=None, K=1, mask=None, lab=None):
+    n = rp.size - 1 if n is None else n
+    mask = np.zeros(n, np.uint8) if mask is None else mask
+    lab = np.zeros(n, np.int32) if lab is None else lab
+    try:
+        B.Problem(rp, col, w, K, mask, lab, B.make_params())
+    except B.PdcaError as e:
+        return B.STATUS_NAMES[e.status]
+    return "PDCA_OK"
+
+
+def test_graph_errors(B):
+    rp, col, w = complete(6)
+    assert _err_create(B, rp, col, w) == "PDCA_OK"
+    w2 = w.copy(); w2[3] = np.nan
+    assert _err_create(B, rp, col, w2) == "PDCA_ERR_BAD_GRAPH"
+    w3 = w.copy(); w3[3] = -0.5
+    assert _err_create(B, rp, col, w3) == "PDCA_ERR_BAD_GRAPH"
+    w4 = w.copy(); w4[3] = 0.41
+    assert _err_create(B, rp, col, w4) == "PDCA_ERR_NOT_SYMMETRIC"
+    c2 = col.copy(); c2[1] = 99
+    assert _err_create(B, rp, c2, w) == "PDCA_ERR_BAD_GRAPH"
+    c3 = col.copy(); c3[0], c3[1] = c3[1], c3[0]
+    assert _err_create(B, rp, c3, w) == "PDCA_ERR_BAD_GRAPH"
+    c4 = col.copy(); c4[0] = 0
+    assert _err_create(B, rp, c4, w) == "PDCA_ERR_BAD_GRAPH"
+    # a node whose only weights are zero is isolated
+    r5, c5, w5 = csr_from_pairs(4, np.array([0, 1, 2]), np.array([1, 2, 3]), np.array([1, 1, 0], np.float32))
+    assert _err_create(B, r5, c5, w5) == "PDCA_ERR_ISOLATED_NODE"
+    r6, c6, w6 = csr_from_pairs(5, np.array([0, 1]), np.array([1, 2]), np.ones(2, np.float32))
+    assert _err_create(B, r6, c6, w6) == "PDCA_ERR_ISOLATED_NODE"
+    # fidelity input
+    m = np.zeros(6, np.uint8); m[2] = 2
+    assert _err_create(B, rp, col, w, mask=m) == "PDCA_ERR_BAD_GRAPH"
+    m[2] = 1
+    lab = np.zeros(6, np.int32); lab[2] = 3
+    assert _err_create(B, rp, col, w, K=3, mask=m, lab=lab) == "PDCA_ERR_BAD_GRAPH"
+    lab[2] = 2
+    assert _err_create(B, rp, col, w, K=3, mask=m, lab=lab) == "PDCA_OK"
+    lab[2] = 2
+    assert _err_create(B, rp, col, w, K=1, mask=m, lab=lab) == "PDCA_ERR_BAD_GRAPH"
+
+
+def test_profile_and_launch_counter(B):
+    wl = make_workload("moons2k")
+    g = B.Problem(wl.row_ptr, wl.col, wl.w, 1, wl.fid_mask, wl.fid_labels,
+                  B.params_from_workload(wl.params))
+    n0 = B.pdca_kernel_launches()
+    g.profile(True)
+    g.solve(3, 5)
+    ms, cnt = g.profile_read()
+    assert cnt == 15 and ms > 0
+    assert B.pdca_kernel_launches() - n0 == 15
+    g.profile(False)
+    g.solve(1, 5)
+    assert g.profile_read() == (0.0, 0)
+
+
+def test_native_library_loaded(B):
+    maps = open("/proc/self/maps").read()
+    assert "libpdca.so" in maps
