@@ -450,7 +450,7 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     if (launch_window_sort(n, L.n_pad, L.sigma, s_rp, h->perm, h->iperm, sm) != cudaSuccess ||
         cp(h->slice_off, L.slice_off.data(), 8 * L.slice_off.size()) != cudaSuccess ||
         launch_pack(n, L.n_pad, k, s_rp, s_col, s_w, s_deg, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
-                    h->sell_col, h->sell_w, h->rowinfo, sm) != cudaSuccess)
+                    h->sell_col, h->sell_w, h->rowinfo, s_status, sm) != cudaSuccess)
         return fail(PDCA_ERR_CUDA);
     if (prm.precond == PDCA_RICHARDSON) {
         if (prm.lambda_max > 0) {
@@ -467,7 +467,10 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     h->cur = 0;
     h->prev = 1;
     h->has_prev = false;
-    if (cudaStreamSynchronize(sm) != cudaSuccess) return fail(PDCA_ERR_CUDA);
+    if (cudaMemcpyAsync(&status, s_status, 4, cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
+        cudaStreamSynchronize(sm) != cudaSuccess)
+        return fail(PDCA_ERR_CUDA);
+    if (status & kLayoutMismatch) return fail(PDCA_ERR_CUDA);
     *out = h;
     return PDCA_OK;
 }

@@ -32,6 +32,7 @@ constexpr int kRedSlots = 8;                   // doubles per block partial
 constexpr uint32_t kBadGraph = 1u;
 constexpr uint32_t kNotSymmetric = 2u;
 constexpr uint32_t kIsolated = 4u;
+constexpr uint32_t kLayoutMismatch = 8u;   // internal: packed row longer than its slice
 
 struct SellView {
     const int32_t *col;        // padded sliced-ELL column indices (new numbering)
@@ -88,7 +89,7 @@ cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_
                         const int32_t *col, const float *w, const double *deg,
                         const uint8_t *mask, const int32_t *labels, const int32_t *perm,
                         const int32_t *iperm, const int64_t *slice_off, int32_t *sell_col,
-                        float *sell_w, uint32_t *rowinfo, cudaStream_t st);
+                        float *sell_w, uint32_t *rowinfo, uint32_t *status, cudaStream_t st);
 cudaError_t launch_init_u(int32_t n_pad, int32_t K, const uint32_t *rowinfo, float *u,
                           cudaStream_t st);
 

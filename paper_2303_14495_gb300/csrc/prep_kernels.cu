@@ -114,7 +114,7 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
                             const int32_t *__restrict__ labels, const int32_t *__restrict__ perm,
                             const int32_t *__restrict__ iperm, const int64_t *__restrict__ slice_off,
                             int32_t *__restrict__ sell_col, float *__restrict__ sell_w,
-                            uint32_t *__restrict__ rowinfo) {
+                            uint32_t *__restrict__ rowinfo, uint32_t *__restrict__ status) {
     const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_pad) return;
     const int32_t s = r >> 5, lane = r & 31;
@@ -126,6 +126,10 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
     if (old >= 0) {
         const int64_t e0 = row_ptr[old];
         len = (int32_t)(row_ptr[old + 1] - e0);
+        if (len > width) {  // host and device layouts disagree: never write past the slice
+            atomicOr(status, kLayoutMismatch);
+            len = width;
+        }
         const double di = deg[old];
         for (int32_t j = 0; j < len; ++j) {
             const int32_t oj = col[e0 + j];
@@ -183,12 +187,13 @@ cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const in
 cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_ptr, const int32_t *col,
                         const float *w, const double *deg, const uint8_t *mask, const int32_t *labels,
                         const int32_t *perm, const int32_t *iperm, const int64_t *slice_off,
-                        int32_t *sell_col, float *sell_w, uint32_t *rowinfo, cudaStream_t st) {
+                        int32_t *sell_col, float *sell_w, uint32_t *rowinfo, uint32_t *status,
+                        cudaStream_t st) {
     (void)n;
     (void)K;
     count_launches(1);
     pack_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, mask, labels, perm,
-                                                     iperm, slice_off, sell_col, sell_w, rowinfo);
+                                                     iperm, slice_off, sell_col, sell_w, rowinfo, status);
     return cudaGetLastError();
 }
 
