@@ -48,6 +48,10 @@ extern "C" {
 /* Largest number of label columns K supported by the kernels. */
 #define PDCA_MAX_K 16
 
+/* Largest graph, in nodes, that pdca_energy_static accepts: its fixed device
+ * scratch holds one float per node (4 MiB) plus 64 KiB of partial sums. */
+#define PDCA_STATIC_MAX_N (1 << 20)
+
 typedef enum {
     PDCA_OK = 0,
     PDCA_ERR_INVALID_ARG = 1,    /* bad size, pointer, parameter or call order        */
@@ -58,9 +62,10 @@ typedef enum {
     PDCA_ERR_OOM = 6,            /* workspace smaller than pdca_workspace_size         */
     PDCA_ERR_CUDA = 7,           /* a CUDA runtime call failed                         */
     PDCA_ERR_TIMEOUT = 8,        /* a bounded device-side wait ran out                 */
-    PDCA_ERR_BAD_GRAPH = 9       /* column out of range, self loop, columns not
+    PDCA_ERR_BAD_GRAPH = 9,      /* column out of range, self loop, columns not
                                     strictly increasing, weight < 0 or not finite,
                                     mask not 0/1, or prior label out of range           */
+    PDCA_ERR_TOO_LARGE = 10      /* n above PDCA_STATIC_MAX_N in pdca_energy_static    */
 } pdca_status;
 
 /* Laplacian (Sec. 2.2). */
@@ -187,6 +192,32 @@ pdca_status pdca_profile_read(pdca_problem *h, double *sweep_ms, int64_t *sweep_
 
 /* Number of kernels this library has launched in the process so far. */
 uint64_t pdca_kernel_launches(void);
+
+/* GL energy F(u) of an iterate, computed directly from a device CSR graph,
+ * for callers that cannot allocate device memory: they cannot hand the
+ * library a workspace, e.g. code running inside a CUDA stream capture (where
+ * cudaMalloc is not allowed), a host framework that owns all device memory
+ * through its own fixed pool, or a loop that must not pay cudaMalloc's
+ * implicit synchronisation.  The paper has no counterpart of this call; it
+ * evaluates the same F as pdca_energy (normalized Laplacian).
+ *   row_ptr (n+1 int64), col (nnz int32), w (nnz float32), u (n x k float32,
+ *   row-major), fid_mask (n uint8), labels (n int32): DEVICE pointers, same
+ *   conventions as pdca_create (the graph is not checked for symmetry);
+ *   eps > 0, eta >= 0; stream: cudaStream_t as void*;
+ *   F_out: host or device pointer receiving F (written on success).
+ * Allocates nothing: the scratch is a fixed device array inside the library
+ * (about 4.1 MiB, held on every GPU that loads the library until the process
+ * exits).  The first call on a device looks up that array's address; make
+ * that first call before any stream capture.  All calls share the array
+ * and overwrite it; calls whose kernels overlap on the GPU race and must be
+ * serialised by the caller.  Synchronises the stream.
+ * Errors: INVALID_ARG (bad sizes or a host pointer among the inputs),
+ * TOO_LARGE (n > PDCA_STATIC_MAX_N), BAD_GRAPH (row_ptr outside [0, nnz] or
+ * a column out of range), ISOLATED_NODE, NONFINITE, CUDA. */
+pdca_status pdca_energy_static(const int64_t *row_ptr, const int32_t *col, const float *w,
+                               int32_t n, int64_t nnz, int32_t k, const float *u,
+                               const uint8_t *fid_mask, const int32_t *labels, double eps,
+                               double eta, void *stream, double *F_out);
 
 /* Release the handle's host-side state (the workspace stays the caller's).
  * Synchronises the handle's stream first.  NULL is ignored. */

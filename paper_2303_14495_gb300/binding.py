@@ -27,7 +27,9 @@ STATUS_NAMES = {
     0: "PDCA_OK", 1: "PDCA_ERR_INVALID_ARG", 2: "PDCA_ERR_NOT_SYMMETRIC",
     3: "PDCA_ERR_ISOLATED_NODE", 4: "PDCA_ERR_INFEASIBLE", 5: "PDCA_ERR_NONFINITE",
     6: "PDCA_ERR_OOM", 7: "PDCA_ERR_CUDA", 8: "PDCA_ERR_TIMEOUT", 9: "PDCA_ERR_BAD_GRAPH",
+    10: "PDCA_ERR_TOO_LARGE",
 }
+PDCA_STATIC_MAX_N = 1 << 20
 PDCA_LAP_NORMALIZED, PDCA_LAP_UNNORMALIZED = 0, 1
 PDCA_JACOBI_DAMPED, PDCA_JACOBI_PERTURBED, PDCA_RICHARDSON = 0, 1, 2
 PDCA_FP32 = 0
@@ -37,7 +39,7 @@ EXPORTS = [
     "pdca_default_params", "pdca_workspace_size", "pdca_create", "pdca_set_u", "pdca_step",
     "pdca_solve", "pdca_energy", "pdca_get_u", "pdca_labels", "pdca_lambda_max", "pdca_layout",
     "pdca_profile_enable", "pdca_profile_read", "pdca_kernel_launches", "pdca_destroy",
-    "pdca_status_string",
+    "pdca_status_string", "pdca_energy_static",
 ]
 
 
@@ -89,6 +91,8 @@ def lib():
                 "pdca_kernel_launches": (u64, []),
                 "pdca_destroy": (None, [vp]),
                 "pdca_status_string": (C.c_char_p, [C.c_int]),
+                "pdca_energy_static": (C.c_int, [vp, vp, vp, i32, i64, i32, vp, vp, vp, dbl, dbl,
+                                                 vp, C.POINTER(dbl)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -208,6 +212,16 @@ def pdca_kernel_launches() -> int:
 
 def pdca_destroy(h) -> None:
     lib().pdca_destroy(h)
+
+
+def pdca_energy_static(row_ptr, col, w, n, nnz, k, u, fid_mask, labels, eps, eta, stream=0):
+    """F(u) from a device CSR without any allocation (fixed library scratch);
+    returns (status, F)."""
+    F = C.c_double(float("nan"))
+    st = lib().pdca_energy_static(_ptr(row_ptr), _ptr(col), _ptr(w), int(n), int(nnz), int(k),
+                                  _ptr(u), _ptr(fid_mask), _ptr(labels), float(eps), float(eta),
+                                  C.c_void_p(int(stream)), C.byref(F))
+    return st, F.value
 
 
 def pdca_status_string(st: int) -> str:

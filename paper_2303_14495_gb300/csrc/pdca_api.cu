@@ -348,6 +348,7 @@ const char *pdca_status_string(pdca_status s) {
     case PDCA_ERR_CUDA: return "CUDA runtime error";
     case PDCA_ERR_TIMEOUT: return "bounded device wait ran out";
     case PDCA_ERR_BAD_GRAPH: return "malformed graph or fidelity input";
+    case PDCA_ERR_TOO_LARGE: return "graph larger than the fixed scratch of pdca_energy_static";
     }
     return "unknown status";
 }
