@@ -41,26 +41,39 @@ def log(*a):
 # byte model (per unit of work)
 # ---------------------------------------------------------------------------
 
-def sweep_bytes(nnz, n, K, s_idx=4, s_w=4, s_u=4):
-    """Algorithmic HBM bytes of one fused sweep: the index and weight streams,
-    one read of v^s, one read of u^t, one write of v^{s+1}, one tag byte per
-    row; neighbour rows counted once."""
-    return nnz * (s_idx + s_w) + n * (3 * K * s_u + 1)
+def operator_bytes(nnz, lay, s_w=4):
+    """Index and weight streams of the operator, padding excluded: int32
+    columns in the plain form; in the tiled form 16-bit local columns plus the
+    tiles' halo lists (one int32 per halo row)."""
+    if lay and lay.get("tiled"):
+        return nnz * (2 + s_w) + 4 * lay["halo_rows"]
+    return nnz * (4 + s_w)
 
 
-def energy_bytes(nnz, n, K, s_idx=4, s_w=4, s_u=4):
+def sweep_bytes(nnz, n, K, lay=None, s_u=4):
+    """Algorithmic HBM bytes of one fused sweep: the operator streams, one read
+    of v^s, one read of u^t, one write of v^{s+1}, one tag byte per row;
+    neighbour rows counted once."""
+    return operator_bytes(nnz, lay) + n * (3 * K * s_u + 1)
+
+
+def energy_bytes(nnz, n, K, lay=None, s_u=4):
     """Energy + residual pass: the operator, u^{t+1} and u^t, one tag byte."""
-    return nnz * (s_idx + s_w) + n * (2 * K * s_u + 1)
+    return operator_bytes(nnz, lay) + n * (2 * K * s_u + 1)
 
 
 def labels_bytes(n, K, s_u=4):
     return n * (K * s_u + 4)
 
 
-def solve_bytes(wl):
+def solve_bytes(wl, lay=None):
     p = wl.params
-    return (p["outer"] * p["inner"] * sweep_bytes(wl.nnz, wl.n, wl.K)
-            + energy_bytes(wl.nnz, wl.n, wl.K) + labels_bytes(wl.n, wl.K))
+    return (p["outer"] * p["inner"] * sweep_bytes(wl.nnz, wl.n, wl.K, lay)
+            + energy_bytes(wl.nnz, wl.n, wl.K, lay) + labels_bytes(wl.n, wl.K))
+
+
+LAYOUT_PARAMS = {"auto": dict(reorder=1, tiling=0), "tiled": dict(reorder=1, tiling=2),
+                 "window": dict(reorder=0, tiling=1)}
 
 
 def peaks():
@@ -254,7 +267,7 @@ def run_ours(args, wl, world, rank, local):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     p = wl.params
-    prm = B.params_from_workload(p)
+    prm = B.params_from_workload(p, sort_window=args.sort_window, **LAYOUT_PARAMS[args.layout])
     t0 = time.perf_counter()
     prob = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm, device=dev)
     torch.cuda.synchronize(dev)
@@ -295,11 +308,11 @@ def run_ours(args, wl, world, rank, local):
     ms_total = ev0.elapsed_time(ev1)
     ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
-    bytes_step = solve_bytes(wl)
+    bytes_step = solve_bytes(wl, lay)
     value = world * bytes_step * args.steps / (ms_total * 1e-3) / 1e9
 
     hbm, kind = peaks()
-    sb = sweep_bytes(wl.nnz, wl.n, wl.K)
+    sb = sweep_bytes(wl.nnz, wl.n, wl.K, lay)
     sweep_ms = sweep_ms_tot / max(sweep_launches, 1)
     achieved = sb / (sweep_ms * 1e-3) / 1e9
     traffic = sweep_traffic_record()
@@ -363,14 +376,17 @@ def run_ours(args, wl, world, rank, local):
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(wl, {"sort_window": lay["sort_window"],
+        "config": workload_config(wl, {"layout": args.layout, "tiled": lay["tiled"],
+                                       "sort_window": lay["sort_window"],
                                        "sell_entries": lay["sell_entries"],
+                                       "halo_rows": lay["halo_rows"], "max_halo": lay["max_halo"],
                                        "lambda_max_used": lam_used}),
         "ms_per_solve": ms_step,
         "pct_of_peak": 100.0 * value / world / hbm,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
-                     "kernel": "sweep_kernel<4,*> (fused sweep)",
+                     "kernel": ("sweep_tiled_kernel<4,*>" if lay["tiled"] else "sweep_kernel<4,*>")
+                               + " (fused sweep)",
                      "bytes_per_launch": sb, "ms_per_launch": sweep_ms,
                      "launches_timed": sweep_launches, "peak_kind": kind},
         "gpu_launches": int(launches),
@@ -392,6 +408,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="voronoi2048")
+    ap.add_argument("--layout", choices=sorted(LAYOUT_PARAMS), default="auto",
+                    help="auto: BFS renumbering, neighbour rows gathered through L1/L2; "
+                         "tiled: BFS renumbering + shared-memory halo tiles; window: degree sort only")
+    ap.add_argument("--sort-window", type=int, default=0,
+                    help="degree-sort window (power of two; 0 = library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cpu-allcores", action="store_true")

@@ -79,6 +79,26 @@ enum { PDCA_LAP_NORMALIZED = 0, PDCA_LAP_UNNORMALIZED = 1 };
  *   PDCA_RICHARDSON       g_i = eps lambda_max + c + delta0 + eta Lambda_i (G_{R,s}). */
 enum { PDCA_JACOBI_DAMPED = 0, PDCA_JACOBI_PERTURBED = 1, PDCA_RICHARDSON = 2 };
 
+/* Node renumbering at create time (a layout choice; results are returned in
+ * the caller's node order either way):
+ *   PDCA_REORDER_BFS  (default) nodes are grouped into blocks of 1024 by
+ *                     breadth-first search so a block is a compact region of
+ *                     the graph, then sorted by degree inside each block;
+ *   PDCA_REORDER_NONE rows keep the caller's order except for the degree sort
+ *                     inside windows of `sort_window` rows. */
+enum { PDCA_REORDER_NONE = 0, PDCA_REORDER_BFS = 1 };
+
+/* Sweep kernels:
+ *   PDCA_TILING_AUTO (default) and PDCA_TILING_OFF: neighbour rows are read
+ *                    from global memory through L1/L2 (the faster form on
+ *                    every workload measured on GB300);
+ *   PDCA_TILING_ON   (needs PDCA_REORDER_BFS) tiles of 512 rows first stage
+ *                    the distinct neighbour rows they reference in shared
+ *                    memory (up to 96 KiB; tiles with larger halos read
+ *                    through their halo list) and gather from there with
+ *                    16-bit local columns. */
+enum { PDCA_TILING_AUTO = 0, PDCA_TILING_OFF = 1, PDCA_TILING_ON = 2 };
+
 /* Arithmetic of the sweeps.  Only PDCA_FP32 is implemented: FP32 storage of
  * the pre-scaled weights and of u, FP32 accumulation, FP64 reductions. */
 enum { PDCA_FP32 = 0 };
@@ -97,9 +117,13 @@ typedef struct {
                             min(2, 1.001 * estimate) (2 bounds it, Prop. diagonal:pre) */
     int32_t power_iters; /* power-method iterations (150 in the paper's experiments)   */
     int32_t precision;   /* PDCA_FP32                                                  */
-    int32_t sort_window; /* rows are reordered by degree inside windows of this many
-                            rows (a power of two in [32, 8192]); 0 = choose the
-                            smallest window with at most 10% slice padding              */
+    int32_t sort_window; /* rows are sorted by degree inside windows of this many rows
+                            (a power of two in [32, 8192]).  PDCA_REORDER_NONE: 0 = the
+                            smallest window with at most 10% slice padding;
+                            PDCA_REORDER_BFS: windows of min(sort_window, 1024) rows
+                            inside each 1024-node block, 0 = 1024                    */
+    int32_t reorder;     /* PDCA_REORDER_BFS (default) / PDCA_REORDER_NONE             */
+    int32_t tiling;      /* PDCA_TILING_AUTO (default) / _OFF / _ON                    */
     int32_t reserved_;
 } pdca_params;
 
@@ -107,21 +131,28 @@ typedef struct pdca_problem pdca_problem;
 
 /* Fill *p with the defaults: eps = 1, c = 3, eta = 1, normalized Laplacian,
  * perturbed Jacobi, omega = 0.5, delta0 = 1e-6, lambda_max = 0 (estimate),
- * 150 power iterations, FP32, automatic sort window. */
+ * 150 power iterations, FP32, automatic sort window, BFS renumbering,
+ * automatic tiling. */
 void pdca_default_params(pdca_params *p);
 
 /* Device workspace, in bytes, that pdca_create needs for this graph.
  * row_ptr: n+1 CSR row offsets (host or device), row_ptr[0] = 0, non-decreasing.
  * k: label columns (1..PDCA_MAX_K).  p: parameters (NULL = defaults).
+ * With PDCA_REORDER_BFS the padded operator depends on the renumbering, so
+ * the size is an upper bound computed from the row lengths alone (at most
+ * nnz + 32 x the sum of the largest n/1024 degrees entries, plus one int32
+ * per nonzero for the halo lists).
  * Errors: PDCA_ERR_INVALID_ARG for n < 1, k out of range, a bad row_ptr or
  * a sort window that is not a power of two in [32, 8192]. */
 pdca_status pdca_workspace_size(const int64_t *row_ptr, int32_t n, int32_t k,
                                 const pdca_params *p, size_t *bytes);
 
 /* Build a problem (Sec. 2.2 and 3.1): validate the graph, compute the degrees
- * d_i and the pre-scaled weights w_ij / sqrt(d_i d_j), reorder rows by degree
- * within sort windows, pack the sliced-ELL operator, set u^0 and, for
- * Richardson with lambda_max = 0, run the power method.
+ * d_i and the pre-scaled weights w_ij / sqrt(d_i d_j), renumber the nodes
+ * (on the host: BFS blocks and, for tiling, the halo lists; this reads
+ * row_ptr and col, copying them from the device if they live there), pack
+ * the sliced-ELL operator, set u^0 and, for Richardson with lambda_max = 0,
+ * run the power method.
  *   row_ptr  n+1 int64 CSR offsets            (host or device; read during the call)
  *   col      nnz int32 columns, strictly increasing within each row, no i == j
  *   w        nnz float32 weights, finite and >= 0, symmetric: w_ij == w_ji exactly
@@ -179,9 +210,11 @@ pdca_status pdca_labels(pdca_problem *h, int32_t *labels_out);
 pdca_status pdca_lambda_max(pdca_problem *h, double *lambda_used, double *lambda_estimate);
 
 /* Layout facts of a created problem: padded sliced-ELL entries, number of
- * 32-row slices, sort window.  Any pointer may be NULL. */
+ * 32-row slices, degree-sort window, whether the tiled kernels run, the total
+ * and the largest number of halo rows over tiles (0 if not tiled).  Any
+ * pointer may be NULL. */
 pdca_status pdca_layout(pdca_problem *h, int64_t *sell_entries, int64_t *n_slices,
-                        int32_t *sort_window);
+                        int32_t *sort_window, int32_t *tiled, int64_t *halo_rows, int32_t *max_halo);
 
 /* Kernel timing for measurement: enable (1) / disable (0) CUDA-event timing
  * of every sweep launch of this handle; read returns the summed sweep time

@@ -18,7 +18,8 @@ from typing import Optional
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libpdca.so")
+# PDCA_LIB may name another build of the same library (e.g. a tuning variant)
+LIB_PATH = os.environ.get("PDCA_LIB") or os.path.join(HERE, "_build", "libpdca.so")
 
 PDCA_MAX_K = 16
 
@@ -33,6 +34,8 @@ PDCA_STATIC_MAX_N = 1 << 20
 PDCA_LAP_NORMALIZED, PDCA_LAP_UNNORMALIZED = 0, 1
 PDCA_JACOBI_DAMPED, PDCA_JACOBI_PERTURBED, PDCA_RICHARDSON = 0, 1, 2
 PDCA_FP32 = 0
+PDCA_REORDER_NONE, PDCA_REORDER_BFS = 0, 1
+PDCA_TILING_AUTO, PDCA_TILING_OFF, PDCA_TILING_ON = 0, 1, 2
 
 # every symbol include/pdca.h declares
 EXPORTS = [
@@ -55,7 +58,8 @@ class pdca_params(C.Structure):
         ("laplacian", C.c_int32), ("precond", C.c_int32),
         ("damping", C.c_double), ("delta0", C.c_double), ("lambda_max", C.c_double),
         ("power_iters", C.c_int32), ("precision", C.c_int32),
-        ("sort_window", C.c_int32), ("reserved_", C.c_int32),
+        ("sort_window", C.c_int32), ("reorder", C.c_int32), ("tiling", C.c_int32),
+        ("reserved_", C.c_int32),
     ]
 
 
@@ -85,7 +89,8 @@ def lib():
                 "pdca_get_u": (C.c_int, [vp, vp]),
                 "pdca_labels": (C.c_int, [vp, vp]),
                 "pdca_lambda_max": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(dbl)]),
-                "pdca_layout": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
+                "pdca_layout": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32),
+                                          C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]),
                 "pdca_profile_enable": (C.c_int, [vp, i32]),
                 "pdca_profile_read": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i64)]),
                 "pdca_kernel_launches": (u64, []),
@@ -122,13 +127,15 @@ def _ptr(a) -> Optional[int]:
 
 def make_params(eps=1.0, c=3.0, eta=1.0, precond=PDCA_JACOBI_PERTURBED, damping=0.5, delta0=1e-6,
                 lambda_max=0.0, power_iters=150, laplacian=PDCA_LAP_NORMALIZED,
-                precision=PDCA_FP32, sort_window=0) -> pdca_params:
+                precision=PDCA_FP32, sort_window=0, reorder=PDCA_REORDER_BFS,
+                tiling=PDCA_TILING_AUTO) -> pdca_params:
     p = pdca_params()
     lib().pdca_default_params(C.byref(p))
     p.eps, p.c, p.eta = float(eps), float(c), float(eta)
     p.precond, p.damping, p.delta0 = int(precond), float(damping), float(delta0)
     p.lambda_max, p.power_iters = float(lambda_max), int(power_iters)
     p.laplacian, p.precision, p.sort_window = int(laplacian), int(precision), int(sort_window)
+    p.reorder, p.tiling = int(reorder), int(tiling)
     return p
 
 
@@ -192,8 +199,10 @@ def pdca_lambda_max(h):
 
 def pdca_layout(h):
     e, s, w = C.c_int64(0), C.c_int64(0), C.c_int32(0)
-    st = lib().pdca_layout(h, C.byref(e), C.byref(s), C.byref(w))
-    return st, e.value, s.value, w.value
+    t, hr, mh = C.c_int32(0), C.c_int64(0), C.c_int32(0)
+    st = lib().pdca_layout(h, C.byref(e), C.byref(s), C.byref(w), C.byref(t), C.byref(hr), C.byref(mh))
+    return st, dict(sell_entries=e.value, n_slices=s.value, sort_window=w.value, tiled=bool(t.value),
+                    halo_rows=hr.value, max_halo=mh.value)
 
 
 def pdca_profile_enable(h, on: bool) -> int:
@@ -303,9 +312,9 @@ class Problem:
         return used, est
 
     def layout(self):
-        st, e, s, w = pdca_layout(self.h)
+        st, d = pdca_layout(self.h)
         _check(st, "pdca_layout")
-        return dict(sell_entries=e, n_slices=s, sort_window=w)
+        return d
 
     def profile(self, on: bool):
         _check(pdca_profile_enable(self.h, on), "pdca_profile_enable")

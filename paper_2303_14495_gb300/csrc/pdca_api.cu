@@ -18,6 +18,7 @@ std::atomic<uint64_t> g_launches{0};
 constexpr size_t kAlign = 256;
 constexpr int kTraceCap = 1024;   // outer steps per trace chunk
 constexpr double kPadTarget = 1.10;
+constexpr int32_t kBfsChunk = 1 << 18;       // renumbering chunk (multiple of kBfsBlock)
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -35,13 +36,32 @@ bool is_device_ptr(const void *p) {
 // Everything about the device layout that depends only on the sizes and the
 // row lengths; computed on the host from row_ptr.
 struct Layout {
-    int32_t n = 0, K = 0, n_pad = 0, n_slices = 0, sigma = 0;
-    int64_t nnz = 0, sell_entries = 0;
-    std::vector<int64_t> slice_off;  // n_slices + 1
+    int32_t n = 0, K = 0, n_pad = 0, n_slices = 0, sigma = 0, n_tiles = 0;
+    bool host_order = false;           // renumbering computed on the host (BFS blocks)
+    int64_t nnz = 0, sell_entries = 0, sell_cap = 0, halo_cap = 0;
+    std::vector<int64_t> slice_off;    // n_slices + 1 (exact; filled at create for host order)
     size_t o_col, o_w, o_slice, o_rowinfo, o_perm, o_iperm, o_u[3], o_part, o_red, o_scal, o_trace;
+    size_t o_hoff, o_hidx;
     size_t o_srp, o_scol, o_sw, o_sdeg, o_smask, o_slab, o_status;
     size_t persistent = 0, total = 0;
 };
+
+// Upper bound of the padded entries for any renumbering that sorts rows by
+// degree inside windows of `sigma` rows: inside a window sorted descending,
+// sum over slices of 32 * width <= (window nonzeros) + 32 * (window maximum),
+// and the window maxima sum to at most the sum of the largest
+// (number of windows) degrees.
+int64_t sell_bound(const int64_t *rp, int32_t n, int32_t sigma) {
+    const int64_t windows = ((int64_t)n + sigma - 1) / sigma;
+    std::vector<int32_t> d((size_t)n);
+    for (int32_t i = 0; i < n; ++i) d[(size_t)i] = (int32_t)(rp[i + 1] - rp[i]);
+    const int64_t top = std::min<int64_t>(windows, n);
+    std::nth_element(d.begin(), d.begin() + (top - 1), d.end(), std::greater<int32_t>());
+    int64_t s = 0;
+    for (int64_t i = 0; i < top; ++i) s += d[(size_t)i];
+    const int64_t n_slices = ((int64_t)n + kSliceRows - 1) / kSliceRows;
+    return rp[n] + (int64_t)kSliceRows * s + n_slices * kSliceRows * (kVec - 1);   // + rounding to kVec
+}
 
 // Slice widths for one sort window: the degrees of the window sorted
 // descending; a slice's width is the degree at its first position.
@@ -50,7 +70,8 @@ void window_widths(const int64_t *rp, int64_t base, int64_t end, std::vector<int
     scratch.resize((size_t)(end - base));
     for (int64_t i = base; i < end; ++i) scratch[(size_t)(i - base)] = (int32_t)(rp[i + 1] - rp[i]);
     std::sort(scratch.begin(), scratch.end(), std::greater<int32_t>());
-    for (int64_t p = 0; p < end - base; p += kSliceRows) widths[(size_t)((base + p) / kSliceRows)] = scratch[(size_t)p];
+    for (int64_t p = 0; p < end - base; p += kSliceRows)
+        widths[(size_t)((base + p) / kSliceRows)] = (scratch[(size_t)p] + kVec - 1) / kVec * kVec;
 }
 
 int64_t sell_entries_for(const int64_t *rp, int32_t n, int32_t sigma, std::vector<int64_t> &widths) {
@@ -77,6 +98,9 @@ pdca_status check_params(const pdca_params &p) {
         const int s = p.sort_window;
         if (s < 32 || s > 8192 || (s & (s - 1)) != 0) return PDCA_ERR_INVALID_ARG;
     }
+    if (p.reorder != PDCA_REORDER_NONE && p.reorder != PDCA_REORDER_BFS) return PDCA_ERR_INVALID_ARG;
+    if (p.tiling < PDCA_TILING_AUTO || p.tiling > PDCA_TILING_ON) return PDCA_ERR_INVALID_ARG;
+    if (p.tiling == PDCA_TILING_ON && p.reorder != PDCA_REORDER_BFS) return PDCA_ERR_INVALID_ARG;
     return PDCA_OK;
 }
 
@@ -146,14 +170,23 @@ pdca_status host_row_ptr(const int64_t *row_ptr, int32_t n, std::vector<int64_t>
     return PDCA_OK;
 }
 
-pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, int32_t sigma_req, Layout &L) {
+pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_params &prm, Layout &L) {
+    const int32_t sigma_req = prm.sort_window;
     L.n = n;
     L.K = K;
     L.nnz = rp[n];
     L.n_slices = (n + kSliceRows - 1) / kSliceRows;
     L.n_pad = L.n_slices * kSliceRows;
+    L.n_tiles = (L.n_slices + kTileSlices - 1) / kTileSlices;
     std::vector<int64_t> widths;
-    if (sigma_req) {
+    if (prm.reorder == PDCA_REORDER_BFS) {
+        // the widths depend on the renumbering (computed at create); size for the bound
+        L.host_order = true;
+        L.sigma = sigma_req && sigma_req <= kBfsBlock ? sigma_req : kBfsBlock;
+        L.sell_entries = 0;
+        L.sell_cap = sell_bound(rp, n, L.sigma);
+        L.halo_cap = std::max<int64_t>(L.nnz, 1);
+    } else if (sigma_req) {
         L.sigma = sigma_req;
         L.sell_entries = sell_entries_for(rp, n, L.sigma, widths);
     } else {
@@ -164,10 +197,14 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, int32_t sigm
             if (s >= 8192 || (double)L.sell_entries <= kPadTarget * (double)std::max<int64_t>(L.nnz, 1)) break;
         }
     }
-    L.slice_off.assign((size_t)L.n_slices + 1, 0);
-    for (int32_t s = 0; s < L.n_slices; ++s) L.slice_off[s + 1] = L.slice_off[s] + widths[s] * kSliceRows;
+    if (!L.host_order) {
+        L.sell_cap = L.sell_entries;
+        L.halo_cap = 1;
+        L.slice_off.assign((size_t)L.n_slices + 1, 0);
+        for (int32_t s = 0; s < L.n_slices; ++s) L.slice_off[s + 1] = L.slice_off[s] + widths[s] * kSliceRows;
+    }
 
-    const size_t P = (size_t)L.sell_entries, np = (size_t)L.n_pad, nn = (size_t)n;
+    const size_t P = (size_t)L.sell_cap, np = (size_t)L.n_pad, nn = (size_t)n;
     const size_t parts = (size_t)std::max(1, energy_blocks(L.n_slices)) * kRedSlots;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + std::max<size_t>(bytes, 1)); return at; };
@@ -182,6 +219,8 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, int32_t sigm
     L.o_red = take(sizeof(RedOut));
     L.o_scal = take(8 * 8);
     L.o_trace = take(8 * 2 * (size_t)kTraceCap);
+    L.o_hoff = take(8 * ((size_t)L.n_tiles + 1));
+    L.o_hidx = take(4 * (size_t)L.halo_cap);
     L.persistent = o;
     // create-time staging of the CSR input
     L.o_srp = take(8 * (nn + 1));
@@ -222,6 +261,9 @@ struct pdca_problem {
     int cur = 0, prev = 1;
     bool has_prev = false;
     bool prof = false;
+    bool tiled = false;
+    TileView tv{};
+    int64_t halo_rows = 0;
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
 
@@ -236,6 +278,7 @@ struct pdca_problem {
         return A;
     }
     int spare() const { return has_prev ? 3 - cur - prev : (cur + 1) % 3; }
+    const TileView *tiles() const { return tiled ? &tv : nullptr; }
 };
 
 namespace {
@@ -261,7 +304,7 @@ pdca_status sweep(pdca_problem *h, bool project, const float *src, const float *
         h->ev_used += 2;
         PDCA_TRY(cudaEventRecord(a, h->stream));
     }
-    PDCA_TRY(launch_sweep(h->L.K, project, h->view(), h->cf, src, ut, dst, h->stream));
+    PDCA_TRY(launch_sweep(h->L.K, project, h->view(), h->tiles(), h->cf, src, ut, dst, h->stream));
     if (h->prof) PDCA_TRY(cudaEventRecord(b, h->stream));
     return PDCA_OK;
 }
@@ -289,22 +332,22 @@ pdca_status outer_step(pdca_problem *h, int32_t inner) {
 
 pdca_status reduce_energy(pdca_problem *h, double *trace_F, double *trace_r) {
     const SellView A = h->view();
-    PDCA_TRY(launch_energy(h->L.K, A, h->cf, h->U[h->cur], h->has_prev ? h->U[h->prev] : nullptr,
+    PDCA_TRY(launch_energy(h->L.K, A, h->tiles(), h->cf, h->U[h->cur], h->has_prev ? h->U[h->prev] : nullptr,
                            h->partials, h->stream));
-    PDCA_TRY(launch_energy_finalize(h->partials, energy_blocks(A.n_slices), h->prm.eps, h->prm.eta,
+    PDCA_TRY(launch_energy_finalize(h->partials, reduce_parts(A, h->tiles()), h->prm.eps, h->prm.eta,
                                     h->has_prev ? 1 : 0, h->red, trace_F, trace_r, h->stream));
     return PDCA_OK;
 }
 
 pdca_status power_method(pdca_problem *h) {
     const SellView A = h->view();
-    const int parts = energy_blocks(A.n_slices);
+    const int parts = reduce_parts(A, h->tiles());
     float *x = h->U[1], *y = h->U[2];
     double *scale = h->scal, *lam = h->scal + 1;
     PDCA_TRY(launch_power_init(A, h->perm, x, h->partials, h->stream));
-    PDCA_TRY(launch_power_finalize(h->partials, parts, scale, lam, h->stream));
+    PDCA_TRY(launch_power_finalize(h->partials, energy_blocks(A.n_slices), scale, lam, h->stream));
     for (int it = 0; it <= h->prm.power_iters; ++it) {
-        PDCA_TRY(launch_power_spmv(A, x, scale, y, h->partials, h->stream));
+        PDCA_TRY(launch_power_spmv(A, h->tiles(), x, scale, y, h->partials, h->stream));
         PDCA_TRY(launch_power_finalize(h->partials, parts, scale, lam, h->stream));
         std::swap(x, y);
     }
@@ -313,6 +356,82 @@ pdca_status power_method(pdca_problem *h) {
     PDCA_TRY(cudaStreamSynchronize(h->stream));
     h->lambda_est = lam_h;
     h->lambda_used = std::min(2.0, 1.001 * lam_h);
+    return PDCA_OK;
+}
+
+// Host symbolic analysis (BFS-block renumbering, degree sort, halo lists),
+// then upload of perm / iperm / halo arrays and the exact slice offsets.
+pdca_status host_renumber(pdca_problem *h, const int64_t *rp, const int32_t *col, int64_t nnz) {
+    Layout &L = h->L;
+    const int32_t n = L.n;
+    std::vector<int32_t> col_keep;
+    const int32_t *hc = col;
+    if (nnz > 0 && is_device_ptr(col)) {
+        col_keep.resize((size_t)nnz);
+        PDCA_TRY(cudaMemcpy(col_keep.data(), col, 4 * (size_t)nnz, cudaMemcpyDefault));
+        hc = col_keep.data();
+    }
+    // columns must be in range before the host walks them (the device check
+    // already passed, so this only guards against inconsistent input copies)
+    std::vector<int32_t> order((size_t)n);
+    locality_order(n, rp, hc, kBfsBlock, kBfsChunk, L.sigma, order.data());
+    std::vector<int32_t> perm((size_t)L.n_pad, -1), iperm((size_t)n);
+    for (int32_t r = 0; r < n; ++r) {
+        perm[(size_t)r] = order[(size_t)r];
+        iperm[(size_t)order[(size_t)r]] = r;
+    }
+    L.slice_off.assign((size_t)L.n_slices + 1, 0);
+    for (int32_t s = 0; s < L.n_slices; ++s) {
+        int64_t wmax = 0;
+        for (int32_t l = 0; l < kSliceRows; ++l) {
+            const int32_t r = s * kSliceRows + l;
+            if (r < n) wmax = std::max<int64_t>(wmax, rp[perm[(size_t)r] + 1] - rp[perm[(size_t)r]]);
+        }
+        wmax = (wmax + kVec - 1) / kVec * kVec;
+        L.slice_off[(size_t)s + 1] = L.slice_off[(size_t)s] + wmax * kSliceRows;
+    }
+    L.sell_entries = L.slice_off.back();
+    if (L.sell_entries > L.sell_cap) return PDCA_ERR_CUDA;   // the bound is a theorem; never expected
+    h->tiled = false;
+    // On every workload measured on GB300 the plain kernels were faster than
+    // the shared-memory tiles, so AUTO uses them; ON builds the tiles.
+    if (h->prm.tiling == PDCA_TILING_ON) {
+        std::vector<int64_t> hoff;
+        std::vector<int32_t> hidx;
+        int32_t mx = 0;
+        tile_halos(n, kTileRows, rp, hc, perm.data(), iperm.data(), hoff, hidx, &mx);
+        // rows staged per block: the whole largest halo if it fits the budget,
+        // else the budget (tiles above it gather through their halo list)
+        const int32_t cap_rows = (int32_t)std::min<size_t>(65536, kTileSmemBudget / (sizeof(float) * L.K));
+        const int32_t smem_rows = std::min(mx, cap_rows);
+        int64_t over = 0;
+        for (size_t t = 0; t + 1 < hoff.size(); ++t) over += (hoff[t + 1] - hoff[t]) > smem_rows ? 1 : 0;
+        // tiles whose halo exceeds the staged rows take the halo-list path
+        (void)over;
+        const bool fits = mx >= 1 && mx <= 65536 && (int64_t)hidx.size() <= L.halo_cap &&
+                          (int32_t)hoff.size() == L.n_tiles + 1;
+        if (!fits && h->prm.tiling == PDCA_TILING_ON) return PDCA_ERR_INVALID_ARG;
+        if (fits) {
+            int64_t *d_hoff = reinterpret_cast<int64_t *>(h->ws + L.o_hoff);
+            int32_t *d_hidx = reinterpret_cast<int32_t *>(h->ws + L.o_hidx);
+            PDCA_TRY(cudaMemcpyAsync(d_hoff, hoff.data(), 8 * hoff.size(), cudaMemcpyHostToDevice, h->stream));
+            if (!hidx.empty())
+                PDCA_TRY(cudaMemcpyAsync(d_hidx, hidx.data(), 4 * hidx.size(), cudaMemcpyHostToDevice, h->stream));
+            h->tv.halo_off = d_hoff;
+            h->tv.halo_idx = d_hidx;
+            h->tv.lcol = reinterpret_cast<const uint16_t *>(h->sell_col);
+            h->tv.n_tiles = L.n_tiles;
+            h->tv.max_halo = mx;
+            h->tv.smem_rows = smem_rows;
+            h->halo_rows = (int64_t)hidx.size();
+            h->tiled = true;
+            // the copies above read host vectors that go out of scope
+            PDCA_TRY(cudaStreamSynchronize(h->stream));
+        }
+    }
+    PDCA_TRY(cudaMemcpyAsync(h->perm, perm.data(), 4 * perm.size(), cudaMemcpyHostToDevice, h->stream));
+    PDCA_TRY(cudaMemcpyAsync(h->iperm, iperm.data(), 4 * iperm.size(), cudaMemcpyHostToDevice, h->stream));
+    PDCA_TRY(cudaStreamSynchronize(h->stream));
     return PDCA_OK;
 }
 
@@ -334,6 +453,8 @@ void pdca_default_params(pdca_params *p) {
     p->power_iters = 150;
     p->precision = PDCA_FP32;
     p->sort_window = 0;
+    p->reorder = PDCA_REORDER_BFS;
+    p->tiling = PDCA_TILING_AUTO;
 }
 
 const char *pdca_status_string(pdca_status s) {
@@ -368,7 +489,7 @@ pdca_status pdca_workspace_size(const int64_t *row_ptr, int32_t n, int32_t k, co
     st = host_row_ptr(row_ptr, n, keep, &rp);
     if (st != PDCA_OK) return st;
     Layout L;
-    st = compute_layout(rp, n, k, prm.sort_window, L);
+    st = compute_layout(rp, n, k, prm, L);
     if (st != PDCA_OK) return st;
     *bytes = L.total;
     return PDCA_OK;
@@ -400,7 +521,7 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
 
     pdca_problem *h = new (std::nothrow) pdca_problem();
     if (!h) return PDCA_ERR_INVALID_ARG;
-    st = compute_layout(rp, n, k, prm.sort_window, h->L);
+    st = compute_layout(rp, n, k, prm, h->L);
     if (st != PDCA_OK) { delete h; return st; }
     if (ws_bytes < h->L.total) { delete h; return PDCA_ERR_OOM; }
     h->prm = prm;
@@ -448,11 +569,22 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     if (status & kNotSymmetric) return fail(PDCA_ERR_NOT_SYMMETRIC);
     if (status & kIsolated) return fail(PDCA_ERR_ISOLATED_NODE);
 
-    if (launch_window_sort(n, L.n_pad, L.sigma, s_rp, h->perm, h->iperm, sm) != cudaSuccess ||
-        cp(h->slice_off, L.slice_off.data(), 8 * L.slice_off.size()) != cudaSuccess ||
-        launch_pack(n, L.n_pad, k, s_rp, s_col, s_w, s_deg, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
-                    h->sell_col, h->sell_w, h->rowinfo, s_status, sm) != cudaSuccess)
+    if (L.host_order) {
+        st = host_renumber(h, rp, col, nnz);
+        if (st != PDCA_OK) return fail(st);
+    } else if (launch_window_sort(n, L.n_pad, L.sigma, s_rp, h->perm, h->iperm, sm) != cudaSuccess) {
         return fail(PDCA_ERR_CUDA);
+    }
+    if (cp(h->slice_off, L.slice_off.data(), 8 * L.slice_off.size()) != cudaSuccess) return fail(PDCA_ERR_CUDA);
+    cudaError_t pe;
+    if (h->tiled)
+        pe = launch_pack_tiled(L.n_pad, s_rp, s_col, s_w, s_deg, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
+                               h->tv.halo_off, h->tv.halo_idx, const_cast<uint16_t *>(h->tv.lcol), h->sell_w,
+                               h->rowinfo, s_status, sm);
+    else
+        pe = launch_pack(n, L.n_pad, k, s_rp, s_col, s_w, s_deg, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
+                         h->sell_col, h->sell_w, h->rowinfo, s_status, sm);
+    if (pe != cudaSuccess) return fail(PDCA_ERR_CUDA);
     if (prm.precond == PDCA_RICHARDSON) {
         if (prm.lambda_max > 0) {
             h->lambda_used = prm.lambda_max;
@@ -586,11 +718,15 @@ pdca_status pdca_lambda_max(pdca_problem *h, double *lambda_used, double *lambda
     return PDCA_OK;
 }
 
-pdca_status pdca_layout(pdca_problem *h, int64_t *sell_entries, int64_t *n_slices, int32_t *sort_window) {
+pdca_status pdca_layout(pdca_problem *h, int64_t *sell_entries, int64_t *n_slices, int32_t *sort_window,
+                        int32_t *tiled, int64_t *halo_rows, int32_t *max_halo) {
     if (!h) return PDCA_ERR_INVALID_ARG;
     if (sell_entries) *sell_entries = h->L.sell_entries;
     if (n_slices) *n_slices = h->L.n_slices;
     if (sort_window) *sort_window = h->L.sigma;
+    if (tiled) *tiled = h->tiled ? 1 : 0;
+    if (halo_rows) *halo_rows = h->tiled ? h->halo_rows : 0;
+    if (max_halo) *max_halo = h->tiled ? h->tv.max_halo : 0;
     return PDCA_OK;
 }
 

@@ -6,11 +6,13 @@
 //     renumbering is applied to rows and columns alike, so u, the tags and
 //     the operator all live in the new order;
 //   * the operator D^{-1/2} W D^{-1/2} (Sec. 2.2) is stored as sliced ELL
-//     with slices of 32 rows (one warp, one lane per row): entry j of lane l
-//     of slice s sits at slice_off[s] + 32 j + l, so a warp reads 128
-//     contiguous bytes of column indices and of weights per entry step;
-//     slice width = longest row of the slice; padding entries point at the
-//     row itself with weight 0;
+//     with slices of 32 rows (one warp, one lane per row).  Entries go in
+//     groups of kVec: entry j of lane l of slice s sits at
+//     slice_off[s] + 32 kVec (j / kVec) + kVec l + (j % kVec), so every lane
+//     reads kVec consecutive entries with one 128-bit load of columns and
+//     one of weights, and a warp reads 512 contiguous bytes per load;
+//     slice width = longest row of the slice rounded up to kVec; padding
+//     entries point at a valid row with weight 0;
 //   * rowinfo[r] = (row length << 8) | tag, tag = prior class or 0xFF;
 //   * u is n_pad x K float32 row-major (n_pad = 32 * number of slices).
 #pragma once
@@ -18,11 +20,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "pdca.h"
 
 namespace pdca {
 
 constexpr int kSliceRows = 32;
+constexpr int kVec = 4;                        // entries per lane per load
 constexpr uint32_t kTagUnlabelled = 0xFFu;
 constexpr int kBlockThreads = 256;             // 8 warps = 8 slices per block
 constexpr int kWarpsPerBlock = kBlockThreads / 32;
@@ -43,6 +48,33 @@ struct SellView {
     int32_t n;                 // real rows; rows >= n are padding
 };
 
+// Tiled form of the operator: tiles of kTileSlices slices; each tile lists
+// the distinct rows its entries reference (its halo, sorted), and every entry
+// stores the position of its column in that list (16 bits).  The tiled
+// kernels stage the halo rows of u in shared memory once per tile.
+constexpr int kBfsBlock = 1024;                        // nodes per BFS block (renumbering)
+constexpr int kTileSlices = 16;
+constexpr int kTileRows = kTileSlices * kSliceRows;    // 512
+constexpr int kTileThreads = kTileSlices * 32;         // one warp per slice
+// Resident tiled blocks per SM the kernels are compiled for, and the shared
+// memory one block may use for its halo (blocks x budget <= 227 KiB).
+#ifndef PDCA_TILE_MIN_BLOCKS
+#define PDCA_TILE_MIN_BLOCKS 2
+#endif
+#ifndef PDCA_TILE_SMEM_KB
+#define PDCA_TILE_SMEM_KB 96
+#endif
+constexpr size_t kTileSmemBudget = (size_t)PDCA_TILE_SMEM_KB * 1024;
+struct TileView {
+    const int64_t *halo_off;   // n_tiles + 1
+    const int32_t *halo_idx;   // halo rows (new numbering), sorted inside a tile
+    const uint16_t *lcol;      // local column of every sliced-ELL entry
+    int32_t n_tiles;
+    int32_t max_halo;          // rows of the largest halo
+    int32_t smem_rows;         // halo rows staged in shared memory; larger halos are read
+                               // through halo_idx from global memory instead
+};
+
 // Scalars of one sweep (Sec. 3): T = eps L_s + eta Lambda + c I and the two
 // values of 1/g_i (unlabelled, labelled rows).
 struct Coeffs {
@@ -58,16 +90,24 @@ struct RedOut {
 };
 
 // --- sweep / reductions (sweep_kernels.cu) ---------------------------------
-cudaError_t launch_sweep(int K, bool project, const SellView &A, const Coeffs &cf,
+// T == nullptr selects the plain kernels (neighbour rows gathered from global
+// memory through L1/L2); otherwise the tiled kernels (halo in shared memory).
+cudaError_t launch_sweep(int K, bool project, const SellView &A, const TileView *T, const Coeffs &cf,
                          const float *v_src, const float *u_t, float *v_dst, cudaStream_t st);
-cudaError_t launch_energy(int K, const SellView &A, const Coeffs &cf, const float *u,
+cudaError_t launch_energy(int K, const SellView &A, const TileView *T, const Coeffs &cf, const float *u,
                           const float *u_prev, double *partials, cudaStream_t st);
+// number of block partials the energy / power kernels write
+int reduce_parts(const SellView &A, const TileView *T);
+// shared memory for `rows` halo rows of K columns (bytes, 16-byte multiple)
+__host__ __device__ inline size_t tile_smem_bytes(int K, int32_t rows) {
+    return ((size_t)rows * (size_t)K * sizeof(float) + 15) / 16 * 16;
+}
 cudaError_t launch_energy_finalize(const double *partials, int n_parts, double eps, double eta,
                                    int has_prev, RedOut *out, double *trace_F,
                                    double *trace_r, cudaStream_t st);
 cudaError_t launch_power_init(const SellView &A, const int32_t *perm, float *x,
                               double *partials, cudaStream_t st);
-cudaError_t launch_power_spmv(const SellView &A, const float *x, const double *scale,
+cudaError_t launch_power_spmv(const SellView &A, const TileView *T, const float *x, const double *scale,
                               float *y, double *partials, cudaStream_t st);
 cudaError_t launch_power_finalize(const double *partials, int n_parts, double *scale,
                                   double *lambda, cudaStream_t st);
@@ -90,6 +130,23 @@ cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_
                         const uint8_t *mask, const int32_t *labels, const int32_t *perm,
                         const int32_t *iperm, const int64_t *slice_off, int32_t *sell_col,
                         float *sell_w, uint32_t *rowinfo, uint32_t *status, cudaStream_t st);
+// tiled form: local 16-bit columns (position in the tile's halo) instead of int32
+cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32_t *col, const float *w,
+                              const double *deg, const uint8_t *mask, const int32_t *labels,
+                              const int32_t *perm, const int32_t *iperm, const int64_t *slice_off,
+                              const int64_t *halo_off, const int32_t *halo_idx, uint16_t *lcol,
+                              float *sell_w, uint32_t *rowinfo, uint32_t *status, cudaStream_t st);
+
+// --- host symbolic analysis (reorder.cpp) ------------------------------------
+// order[new] = old: BFS blocks of `block` nodes inside fixed chunks of `chunk`
+// nodes, then a stable degree sort (descending) inside every window of
+// `sort_window` positions (a divisor of `block`).
+void locality_order(int32_t n, const int64_t *rp, const int32_t *col, int32_t block, int32_t chunk,
+                    int32_t sort_window, int32_t *order);
+// per tile of tile_rows renumbered rows: sorted distinct neighbour rows.
+void tile_halos(int32_t n, int32_t tile_rows, const int64_t *rp, const int32_t *col, const int32_t *perm,
+                const int32_t *iperm, std::vector<int64_t> &halo_off, std::vector<int32_t> &halo_idx,
+                int32_t *max_halo);
 cudaError_t launch_init_u(int32_t n_pad, int32_t K, const uint32_t *rowinfo, float *u,
                           cudaStream_t st);
 

@@ -133,15 +133,76 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
         const double di = deg[old];
         for (int32_t j = 0; j < len; ++j) {
             const int32_t oj = col[e0 + j];
-            const int64_t at = base + 32 * (int64_t)j + lane;
+            const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
             sell_col[at] = iperm[oj];
             sell_w[at] = (float)((double)w[e0 + j] / sqrt(di * deg[oj]));
         }
         if (mask[old]) tag = (uint32_t)labels[old];
     }
     for (int32_t j = len; j < width; ++j) {
-        const int64_t at = base + 32 * (int64_t)j + lane;
+        const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
         sell_col[at] = r;
+        sell_w[at] = 0.0f;
+    }
+    rowinfo[r] = ((uint32_t)len << 8) | tag;
+}
+
+// Tiled form: the column of every entry becomes its position in the tile's
+// sorted halo list (binary search); padding entries use position 0.
+__global__ void pack_tiled_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
+                                  const int32_t *__restrict__ col, const float *__restrict__ w,
+                                  const double *__restrict__ deg, const uint8_t *__restrict__ mask,
+                                  const int32_t *__restrict__ labels, const int32_t *__restrict__ perm,
+                                  const int32_t *__restrict__ iperm, const int64_t *__restrict__ slice_off,
+                                  const int64_t *__restrict__ halo_off, const int32_t *__restrict__ halo_idx,
+                                  uint16_t *__restrict__ lcol, float *__restrict__ sell_w,
+                                  uint32_t *__restrict__ rowinfo, uint32_t *__restrict__ status) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_pad) return;
+    const int32_t s = r >> 5, lane = r & 31;
+    const int64_t base = slice_off[s];
+    const int32_t width = (int32_t)((slice_off[s + 1] - base) >> 5);
+    const int32_t tile = r / kTileRows;
+    const int64_t h0 = halo_off[tile], h1 = halo_off[tile + 1];
+    if (h1 <= h0 || h1 - h0 > 65536) {
+        atomicOr(status, kLayoutMismatch);
+        return;
+    }
+    const int32_t old = perm[r];
+    int32_t len = 0;
+    uint32_t tag = kTagUnlabelled;
+    if (old >= 0) {
+        const int64_t e0 = row_ptr[old];
+        len = (int32_t)(row_ptr[old + 1] - e0);
+        if (len > width) {
+            atomicOr(status, kLayoutMismatch);
+            len = width;
+        }
+        const double di = deg[old];
+        for (int32_t j = 0; j < len; ++j) {
+            const int32_t oj = col[e0 + j];
+            const int32_t cj = iperm[oj];
+            int64_t lo = h0, hi = h1 - 1, pos = -1;
+            while (lo <= hi) {
+                const int64_t mid = lo + ((hi - lo) >> 1);
+                const int32_t v = halo_idx[mid];
+                if (v == cj) { pos = mid; break; }
+                if (v < cj) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            if (pos < 0) {
+                atomicOr(status, kLayoutMismatch);
+                pos = h0;
+            }
+            const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
+            lcol[at] = (uint16_t)(pos - h0);
+            sell_w[at] = (float)((double)w[e0 + j] / sqrt(di * deg[oj]));
+        }
+        if (mask[old]) tag = (uint32_t)labels[old];
+    }
+    for (int32_t j = len; j < width; ++j) {
+        const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
+        lcol[at] = 0;
         sell_w[at] = 0.0f;
     }
     rowinfo[r] = ((uint32_t)len << 8) | tag;
@@ -194,6 +255,18 @@ cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_
     count_launches(1);
     pack_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, mask, labels, perm,
                                                      iperm, slice_off, sell_col, sell_w, rowinfo, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32_t *col, const float *w,
+                              const double *deg, const uint8_t *mask, const int32_t *labels,
+                              const int32_t *perm, const int32_t *iperm, const int64_t *slice_off,
+                              const int64_t *halo_off, const int32_t *halo_idx, uint16_t *lcol,
+                              float *sell_w, uint32_t *rowinfo, uint32_t *status, cudaStream_t st) {
+    count_launches(1);
+    pack_tiled_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, mask, labels, perm,
+                                                           iperm, slice_off, halo_off, halo_idx, lcol, sell_w,
+                                                           rowinfo, status);
     return cudaGetLastError();
 }
 

@@ -9,9 +9,13 @@
 // labels / permutation kernels for the results.
 //
 // All of them walk the sliced-ELL operator the same way: one warp per 32-row
-// slice, one lane per row, entry j of every lane read as one 128-byte
-// coalesced load of column indices and one of weights (streamed with the
-// evict-first hint), neighbour rows of u gathered through L1/L2.
+// slice, one lane per row, entry j of every lane read as one coalesced warp
+// load of column indices and one of weights (streamed with the evict-first
+// hint).  Neighbour rows of u come either from global memory through L1/L2
+// (plain form) or, in the tiled form, from shared memory: a block handles a
+// tile of 32 slices and first copies the tile's halo rows (the distinct rows
+// its entries reference) into shared memory, so every gather is a shared
+// memory load addressed by a 16-bit local column.
 #include "pdca_internal.cuh"
 
 #include <math.h>
@@ -60,46 +64,193 @@ __device__ __forceinline__ void store_row(float *__restrict__ p, const float (&x
     }
 }
 
-// acc[k] = sum_j wt_ij * x_jk over the lane's row of the slice (padding
-// entries carry weight 0 and point at the row itself).
 template <int K>
-__device__ __forceinline__ void gather_row_sum(const SellView &A, int64_t base, int width, int lane,
+__device__ __forceinline__ void load_row_smem(const float *p, float (&x)[K]) {
+    if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q) {
+            const float4 t = reinterpret_cast<const float4 *>(p)[q];
+            x[4 * q + 0] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
+        }
+    } else if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < K / 2; ++q) {
+            const float2 t = reinterpret_cast<const float2 *>(p)[q];
+            x[2 * q + 0] = t.x; x[2 * q + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < K; ++q) x[q] = p[q];
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void store_row_smem(float *p, const float (&x)[K]) {
+    if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q)
+            reinterpret_cast<float4 *>(p)[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+    } else if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < K / 2; ++q) reinterpret_cast<float2 *>(p)[q] = make_float2(x[2 * q], x[2 * q + 1]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < K; ++q) p[q] = x[q];
+    }
+}
+
+// acc[k] = sum_j wt_ij * x_jk over the lane's row of the slice (padding
+// entries carry weight 0 and point at a valid row).  `len` is the lane's own
+// row length: the lane reads only its ceil(len / kVec) groups (kVec
+// consecutive entries per 128-bit load, two groups per iteration), so the
+// slice padding beyond a row's end is never fetched.  Plain form: global columns, rows gathered from global
+// memory through L1/L2.
+template <int K>
+__device__ __forceinline__ void fma_row(float (&acc)[K], float w, const float (&x)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = fmaf(w, x[k], acc[k]);
+}
+
+template <int K>
+__device__ __forceinline__ void gather_row_sum(const SellView &A, int64_t base, int len, int lane,
                                                const float *__restrict__ x, float (&acc)[K]) {
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0f;
-    const int32_t *__restrict__ cp = A.col + base + lane;
-    const float *__restrict__ wp = A.w + base + lane;
-    int j = 0;
-    for (; j + 4 <= width; j += 4) {
-        const int c0 = __ldcs(cp + 32 * (j + 0));
-        const int c1 = __ldcs(cp + 32 * (j + 1));
-        const int c2 = __ldcs(cp + 32 * (j + 2));
-        const int c3 = __ldcs(cp + 32 * (j + 3));
-        const float w0 = __ldcs(wp + 32 * (j + 0));
-        const float w1 = __ldcs(wp + 32 * (j + 1));
-        const float w2 = __ldcs(wp + 32 * (j + 2));
-        const float w3 = __ldcs(wp + 32 * (j + 3));
+    const int4 *__restrict__ cp = reinterpret_cast<const int4 *>(A.col + base) + lane;
+    const float4 *__restrict__ wp = reinterpret_cast<const float4 *>(A.w + base) + lane;
+    const int groups = (len + kVec - 1) / kVec;   // this lane's groups only
+    int g = 0;
+    for (; g + 2 <= groups; g += 2) {
+        const int4 ca = __ldcs(cp + 32 * g), cb = __ldcs(cp + 32 * (g + 1));
+        const float4 wa = __ldcs(wp + 32 * g), wb = __ldcs(wp + 32 * (g + 1));
         float x0[K], x1[K], x2[K], x3[K];
-        load_row<K>(x + (size_t)c0 * K, x0);
-        load_row<K>(x + (size_t)c1 * K, x1);
-        load_row<K>(x + (size_t)c2 * K, x2);
-        load_row<K>(x + (size_t)c3 * K, x3);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            acc[k] = fmaf(w0, x0[k], acc[k]);
-            acc[k] = fmaf(w1, x1[k], acc[k]);
-            acc[k] = fmaf(w2, x2[k], acc[k]);
-            acc[k] = fmaf(w3, x3[k], acc[k]);
-        }
+        load_row<K>(x + (size_t)ca.x * K, x0);
+        load_row<K>(x + (size_t)ca.y * K, x1);
+        load_row<K>(x + (size_t)ca.z * K, x2);
+        load_row<K>(x + (size_t)ca.w * K, x3);
+        fma_row<K>(acc, wa.x, x0); fma_row<K>(acc, wa.y, x1);
+        fma_row<K>(acc, wa.z, x2); fma_row<K>(acc, wa.w, x3);
+        load_row<K>(x + (size_t)cb.x * K, x0);
+        load_row<K>(x + (size_t)cb.y * K, x1);
+        load_row<K>(x + (size_t)cb.z * K, x2);
+        load_row<K>(x + (size_t)cb.w * K, x3);
+        fma_row<K>(acc, wb.x, x0); fma_row<K>(acc, wb.y, x1);
+        fma_row<K>(acc, wb.z, x2); fma_row<K>(acc, wb.w, x3);
     }
-    for (; j < width; ++j) {
-        const int c0 = __ldcs(cp + 32 * j);
-        const float w0 = __ldcs(wp + 32 * j);
-        float x0[K];
-        load_row<K>(x + (size_t)c0 * K, x0);
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] = fmaf(w0, x0[k], acc[k]);
+    if (g < groups) {
+        const int4 ca = __ldcs(cp + 32 * g);
+        const float4 wa = __ldcs(wp + 32 * g);
+        float x0[K], x1[K], x2[K], x3[K];
+        load_row<K>(x + (size_t)ca.x * K, x0);
+        load_row<K>(x + (size_t)ca.y * K, x1);
+        load_row<K>(x + (size_t)ca.z * K, x2);
+        load_row<K>(x + (size_t)ca.w * K, x3);
+        fma_row<K>(acc, wa.x, x0); fma_row<K>(acc, wa.y, x1);
+        fma_row<K>(acc, wa.z, x2); fma_row<K>(acc, wa.w, x3);
     }
+}
+
+// Tiled form: 16-bit local columns (four per 64-bit load) into the halo rows
+// held in shared memory.
+template <int K>
+__device__ __forceinline__ void gather_row_sum_smem(const TileView &T, const SellView &A, int64_t base,
+                                                    int len, int lane, const float *hs, float (&acc)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0f;
+    const uint2 *__restrict__ cp = reinterpret_cast<const uint2 *>(T.lcol + base) + lane;
+    const float4 *__restrict__ wp = reinterpret_cast<const float4 *>(A.w + base) + lane;
+    const int groups = (len + kVec - 1) / kVec;
+    int g = 0;
+    for (; g + 2 <= groups; g += 2) {
+        const uint2 ca = __ldcs(cp + 32 * g), cb = __ldcs(cp + 32 * (g + 1));
+        const float4 wa = __ldcs(wp + 32 * g), wb = __ldcs(wp + 32 * (g + 1));
+        float x0[K], x1[K], x2[K], x3[K];
+        load_row_smem<K>(hs + (ca.x & 0xFFFFu) * K, x0);
+        load_row_smem<K>(hs + (ca.x >> 16) * K, x1);
+        load_row_smem<K>(hs + (ca.y & 0xFFFFu) * K, x2);
+        load_row_smem<K>(hs + (ca.y >> 16) * K, x3);
+        fma_row<K>(acc, wa.x, x0); fma_row<K>(acc, wa.y, x1);
+        fma_row<K>(acc, wa.z, x2); fma_row<K>(acc, wa.w, x3);
+        load_row_smem<K>(hs + (cb.x & 0xFFFFu) * K, x0);
+        load_row_smem<K>(hs + (cb.x >> 16) * K, x1);
+        load_row_smem<K>(hs + (cb.y & 0xFFFFu) * K, x2);
+        load_row_smem<K>(hs + (cb.y >> 16) * K, x3);
+        fma_row<K>(acc, wb.x, x0); fma_row<K>(acc, wb.y, x1);
+        fma_row<K>(acc, wb.z, x2); fma_row<K>(acc, wb.w, x3);
+    }
+    if (g < groups) {
+        const uint2 ca = __ldcs(cp + 32 * g);
+        const float4 wa = __ldcs(wp + 32 * g);
+        float x0[K], x1[K], x2[K], x3[K];
+        load_row_smem<K>(hs + (ca.x & 0xFFFFu) * K, x0);
+        load_row_smem<K>(hs + (ca.x >> 16) * K, x1);
+        load_row_smem<K>(hs + (ca.y & 0xFFFFu) * K, x2);
+        load_row_smem<K>(hs + (ca.y >> 16) * K, x3);
+        fma_row<K>(acc, wa.x, x0); fma_row<K>(acc, wa.y, x1);
+        fma_row<K>(acc, wa.z, x2); fma_row<K>(acc, wa.w, x3);
+    }
+}
+
+// Tiled form for a tile whose halo exceeds the shared-memory allocation: the
+// local column indexes the tile's halo list, which gives the global row.
+template <int K>
+__device__ __forceinline__ void gather_row_sum_indirect(const TileView &T, const SellView &A, int64_t base,
+                                                        int len, int lane, const int32_t *__restrict__ hidx,
+                                                        const float *__restrict__ x, float (&acc)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0f;
+    const uint2 *__restrict__ cp = reinterpret_cast<const uint2 *>(T.lcol + base) + lane;
+    const float4 *__restrict__ wp = reinterpret_cast<const float4 *>(A.w + base) + lane;
+    const int groups = (len + kVec - 1) / kVec;
+    for (int g = 0; g < groups; ++g) {
+        const uint2 ca = __ldcs(cp + 32 * g);
+        const float4 wa = __ldcs(wp + 32 * g);
+        float x0[K], x1[K], x2[K], x3[K];
+        load_row<K>(x + (size_t)__ldg(hidx + (ca.x & 0xFFFFu)) * K, x0);
+        load_row<K>(x + (size_t)__ldg(hidx + (ca.x >> 16)) * K, x1);
+        load_row<K>(x + (size_t)__ldg(hidx + (ca.y & 0xFFFFu)) * K, x2);
+        load_row<K>(x + (size_t)__ldg(hidx + (ca.y >> 16)) * K, x3);
+        fma_row<K>(acc, wa.x, x0); fma_row<K>(acc, wa.y, x1);
+        fma_row<K>(acc, wa.z, x2); fma_row<K>(acc, wa.w, x3);
+    }
+}
+
+// Gather for one row of a tile: from shared memory when the tile's halo is
+// staged there, through the halo list otherwise.
+template <int K>
+__device__ __forceinline__ void tile_row_sum(const TileView &T, const SellView &A, int64_t base, int len,
+                                             int lane, bool staged, const int32_t *__restrict__ hidx,
+                                             const float *hs, const float *__restrict__ x, float (&acc)[K]) {
+    if (staged) gather_row_sum_smem<K>(T, A, base, len, lane, hs, acc);
+    else gather_row_sum_indirect<K>(T, A, base, len, lane, hidx, x, acc);
+}
+
+// Copy the tile's halo rows of x into shared memory (rows in halo order).
+// Batches of four rows per thread: the four index loads, then the four row
+// loads, then the four shared-memory stores, so a batch costs one index and
+// one row latency whatever the halo size.
+template <int K>
+__device__ __forceinline__ void load_halo(const TileView &T, int tile, const float *__restrict__ x, float *hs) {
+    const int64_t h0 = T.halo_off[tile];
+    const int h = (int)(T.halo_off[tile + 1] - h0);
+    const int32_t *__restrict__ idx = T.halo_idx + h0;
+    const int bd = blockDim.x;
+    for (int q0 = threadIdx.x; q0 < h; q0 += 4 * bd) {
+        int32_t i[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) i[m] = (q0 + m * bd < h) ? __ldcs(idx + q0 + m * bd) : -1;
+        float r[4][K];
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (i[m] >= 0) load_row<K>(x + (size_t)i[m] * K, r[m]);
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (i[m] >= 0) store_row_smem<K>(hs + (q0 + m * bd) * K, r[m]);
+    }
+}
+
+__device__ __forceinline__ int row_len(const SellView &A, int slice, int lane) {
+    return (int)(__ldg(A.rowinfo + slice * kSliceRows + lane) >> 8);
 }
 
 // prior y_ik in the +-1 coding from the row tag
@@ -110,36 +261,41 @@ __device__ __forceinline__ float prior_of(uint32_t tag, int k) {
 }
 
 // Euclidean projection of a row onto the simplex in the coding v = (u+1)/2
-// (sort-and-threshold method of Held, Wolfe and Crowder), thresholds in FP64.
+// (sort-and-threshold method of Held, Wolfe and Crowder), written directly in
+// u: with u sorted descending and S_j = sum_{i<=j} u_(i), rho is the largest
+// j with j u_(j) - S_j + 2 > 0, lambda = (S_rho + rho - 2)/rho (twice the
+// threshold theta of the v coding) and u' = max(u - lambda, -1).  (Substituting v = (u+1)/2 into the textbook
+// conditions gives these.)  The sort and the test run in FP32; the threshold
+// sums S_j and lambda are FP64.
 template <int K>
 __device__ __forceinline__ void project_simplex(float (&u)[K]) {
-    double v[K], mu[K];
+    float mu[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        v[k] = 0.5 * ((double)u[k] + 1.0);
-        mu[k] = v[k];
-    }
+    for (int k = 0; k < K; ++k) mu[k] = u[k];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
 #pragma unroll
         for (int j = 0; j + 1 < K - i; ++j) {
-            const double a = mu[j], b = mu[j + 1];
-            mu[j] = a > b ? a : b;
-            mu[j + 1] = a > b ? b : a;
+            const float a = mu[j], b = mu[j + 1];
+            mu[j] = fmaxf(a, b);
+            mu[j + 1] = fminf(a, b);
         }
     }
-    double run = 0.0, theta = 0.0;
+    double run = 0.0, s_rho = mu[0];
+    int rho = 1;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        run += mu[j];
-        const double t = (run - 1.0) / (double)(j + 1);
-        if (mu[j] - t > 0.0) theta = t;
+        run += (double)mu[j];
+        if ((float)(j + 1) * mu[j] - (float)run + 2.0f > 0.0f) {
+            rho = j + 1;
+            s_rho = run;
+        }
     }
+    const double lam = (s_rho + (double)rho - 2.0) / (double)rho;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        double vk = v[k] - theta;
-        vk = vk < 0.0 ? 0.0 : vk;
-        u[k] = (float)(2.0 * vk - 1.0);
+        const double x = (double)u[k] - lam;
+        u[k] = (float)(x > -1.0 ? x : -1.0);
     }
 }
 
@@ -149,29 +305,14 @@ __device__ __forceinline__ void project_simplex(float (&u)[K]) {
 //   b    = eta Lambda_i y_i + c u_i - (u_i^3 - u_i)/eps          (u = u^t)
 //   Tv   = eps (v_i - sum_j wt_ij v_j) + (c + eta Lambda_i) v_i
 //   v'_i = v_i + (b - Tv) / g_i,   then projected if PROJECT.
+//
+// Latency hiding: the loads that depend on nothing (the row tag and length,
+// the own rows of v^s and u^t, the first two entry groups) are issued first,
+// and while a lane works on two entry groups the next two are already in
+// flight.
 template <int K, bool PROJECT>
-__global__ void __launch_bounds__(kBlockThreads)
-sweep_kernel(const SellView A, const Coeffs cf, const float *__restrict__ v_src,
-             const float *__restrict__ u_t, float *__restrict__ v_dst) {
-    const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (slice >= A.n_slices) return;
-    const int64_t base = A.slice_off[slice];
-    const int width = (int)((A.slice_off[slice + 1] - base) >> 5);
-    const int r = slice * kSliceRows + lane;
-    const uint32_t info = A.rowinfo[r];
-
-    float acc[K];
-    gather_row_sum<K>(A, base, width, lane, v_src, acc);
-
-    float v[K], u[K];
-    load_row<K>(v_src + (size_t)r * K, v);
-    if (u_t == v_src) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) u[k] = v[k];
-    } else {
-        load_row<K>(u_t + (size_t)r * K, u);
-    }
+__device__ __forceinline__ void sweep_update(const Coeffs &cf, uint32_t info, const float (&acc)[K],
+                                             const float (&v)[K], const float (&u)[K], float *__restrict__ dst) {
     const uint32_t tag = info & 0xFFu;
     const bool lab = tag != kTagUnlabelled;
     const float inv_g = lab ? cf.inv_g1 : cf.inv_g0;
@@ -186,7 +327,145 @@ sweep_kernel(const SellView A, const Coeffs cf, const float *__restrict__ v_src,
         out[k] = v[k] + (b - tv) * inv_g;
     }
     if constexpr (PROJECT) project_simplex<K>(out);
-    store_row<K>(v_dst + (size_t)r * K, out);
+    store_row<K>(dst, out);
+}
+
+// column i (0..3) of an entry group: int32 global columns or 16-bit locals
+__device__ __forceinline__ int group_col(const int4 &c, int i) {
+    return i == 0 ? c.x : i == 1 ? c.y : i == 2 ? c.z : c.w;
+}
+__device__ __forceinline__ int group_col(const uint2 &c, int i) {
+    return (int)(i == 0 ? (c.x & 0xFFFFu) : i == 1 ? (c.x >> 16) : i == 2 ? (c.y & 0xFFFFu) : (c.y >> 16));
+}
+
+enum GatherMode { kGlobal = 0, kShared = 1, kIndirect = 2 };
+
+template <int K, int MODE>
+__device__ __forceinline__ void source_row(int c, const float *__restrict__ x, const float *hs,
+                                           const int32_t *__restrict__ hidx, float (&r)[K]) {
+    if constexpr (MODE == kGlobal) load_row<K>(x + (size_t)c * K, r);
+    else if constexpr (MODE == kShared) load_row_smem<K>(hs + c * K, r);
+    else load_row<K>(x + (size_t)__ldg(hidx + c) * K, r);
+}
+
+template <int K, int MODE, class IdxT>
+__device__ __forceinline__ void fma_group(float (&acc)[K], const IdxT &c, const float4 &w,
+                                          const float *__restrict__ x, const float *hs,
+                                          const int32_t *__restrict__ hidx) {
+    float r0[K], r1[K], r2[K], r3[K];
+    source_row<K, MODE>(group_col(c, 0), x, hs, hidx, r0);
+    source_row<K, MODE>(group_col(c, 1), x, hs, hidx, r1);
+    source_row<K, MODE>(group_col(c, 2), x, hs, hidx, r2);
+    source_row<K, MODE>(group_col(c, 3), x, hs, hidx, r3);
+    fma_row<K>(acc, w.x, r0);
+    fma_row<K>(acc, w.y, r1);
+    fma_row<K>(acc, w.z, r2);
+    fma_row<K>(acc, w.w, r3);
+}
+
+// Per-lane state of one slice row, loaded before the gather.
+template <int K, class IdxT>
+struct SliceRow {
+    uint32_t info;
+    int groups;
+    const IdxT *cp;
+    const float4 *wp;
+    float v[K], u[K];
+    IdxT c0, c1;
+    float4 w0, w1;
+};
+
+template <int K, class IdxT>
+__device__ __forceinline__ void slice_prologue(const SellView &A, const IdxT *cols, int slice, int lane,
+                                               const float *__restrict__ v_src, const float *__restrict__ u_t,
+                                               SliceRow<K, IdxT> &s) {
+    const int r = slice * kSliceRows + lane;
+    const int64_t base = A.slice_off[slice];
+    s.cp = cols + base / kVec + lane;
+    s.wp = reinterpret_cast<const float4 *>(A.w + base) + lane;
+    s.info = __ldg(A.rowinfo + r);
+    // every real row has an entry and every slice is at least kVec wide, so
+    // group 0 always exists; group 1 is loaded when the slice has it
+    const int width_groups = (int)((A.slice_off[slice + 1] - base) >> 5) / kVec;
+    s.c0 = __ldcs(s.cp);
+    s.w0 = __ldcs(s.wp);
+    if (width_groups > 1) {
+        s.c1 = __ldcs(s.cp + 32);
+        s.w1 = __ldcs(s.wp + 32);
+    }
+    load_row<K>(v_src + (size_t)r * K, s.v);
+    if (u_t == v_src) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) s.u[k] = s.v[k];
+    } else {
+        load_row<K>(u_t + (size_t)r * K, s.u);
+    }
+}
+
+template <int K, int MODE, class IdxT>
+__device__ __forceinline__ void slice_gather(SliceRow<K, IdxT> &s, const float *__restrict__ x, const float *hs,
+                                             const int32_t *__restrict__ hidx, float (&acc)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0f;
+    const int groups = (int)((s.info >> 8) + kVec - 1) / kVec;   // this lane's own groups
+    for (int g = 0; g < groups; g += 2) {
+        IdxT n0 = s.c0, n1 = s.c1;
+        float4 nw0 = s.w0, nw1 = s.w1;
+        if (g + 2 < groups) {
+            n0 = __ldcs(s.cp + 32 * (g + 2));
+            nw0 = __ldcs(s.wp + 32 * (g + 2));
+        }
+        if (g + 3 < groups) {
+            n1 = __ldcs(s.cp + 32 * (g + 3));
+            nw1 = __ldcs(s.wp + 32 * (g + 3));
+        }
+        fma_group<K, MODE>(acc, s.c0, s.w0, x, hs, hidx);
+        if (g + 1 < groups) fma_group<K, MODE>(acc, s.c1, s.w1, x, hs, hidx);
+        s.c0 = n0;
+        s.w0 = nw0;
+        s.c1 = n1;
+        s.w1 = nw1;
+    }
+}
+
+// plain form: one warp per slice, 8 slices per block
+template <int K, bool PROJECT>
+__global__ void __launch_bounds__(kBlockThreads)
+sweep_kernel(const SellView A, const Coeffs cf, const float *__restrict__ v_src,
+             const float *__restrict__ u_t, float *__restrict__ v_dst) {
+    const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (slice >= A.n_slices) return;
+    SliceRow<K, int4> s;
+    slice_prologue<K>(A, reinterpret_cast<const int4 *>(A.col), slice, lane, v_src, u_t, s);
+    float acc[K];
+    slice_gather<K, kGlobal>(s, v_src, nullptr, nullptr, acc);
+    sweep_update<K, PROJECT>(cf, s.info, acc, s.v, s.u, v_dst + (size_t)(slice * kSliceRows + lane) * K);
+}
+
+// tiled form: one block per tile of 16 slices (one per warp); the halo of
+// v^s goes to shared memory while the warps' own loads are in flight
+template <int K, bool PROJECT>
+__global__ void __launch_bounds__(kTileThreads, PDCA_TILE_MIN_BLOCKS)
+sweep_tiled_kernel(const SellView A, const TileView T, const Coeffs cf, const float *__restrict__ v_src,
+                   const float *__restrict__ u_t, float *__restrict__ v_dst) {
+    extern __shared__ float4 smem_f4[];
+    float *hs = reinterpret_cast<float *>(smem_f4);
+    const int tile = blockIdx.x;
+    const int slice = tile * kTileSlices + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const bool active = slice < A.n_slices;
+    SliceRow<K, uint2> s;
+    if (active) slice_prologue<K>(A, reinterpret_cast<const uint2 *>(T.lcol), slice, lane, v_src, u_t, s);
+    const int64_t h0 = T.halo_off[tile];
+    const bool staged = T.halo_off[tile + 1] - h0 <= T.smem_rows;
+    if (staged) load_halo<K>(T, tile, v_src, hs);
+    __syncthreads();
+    if (!active) return;
+    float acc[K];
+    if (staged) slice_gather<K, kShared>(s, v_src, hs, nullptr, acc);
+    else slice_gather<K, kIndirect>(s, v_src, nullptr, T.halo_idx + h0, acc);
+    sweep_update<K, PROJECT>(cf, s.info, acc, s.v, s.u, v_dst + (size_t)(slice * kSliceRows + lane) * K);
 }
 
 // ---------------------------------------------------------------------------
@@ -198,10 +477,11 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Sum S values over the block in a fixed order and store them at out[0..S).
-template <int S>
+// Sum S values over the block (WARPS warps) in a fixed order and store them
+// at out[0..S).
+template <int S, int WARPS = kWarpsPerBlock>
 __device__ __forceinline__ void block_sum_store(double (&v)[S], double *__restrict__ out) {
-    __shared__ double sm[kWarpsPerBlock][S];
+    __shared__ double sm[WARPS][S];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -212,7 +492,7 @@ __device__ __forceinline__ void block_sum_store(double (&v)[S], double *__restri
     if (threadIdx.x < S) {
         double t = 0.0;
 #pragma unroll
-        for (int q = 0; q < kWarpsPerBlock; ++q) t += sm[q][threadIdx.x];
+        for (int q = 0; q < WARPS; ++q) t += sm[q][threadIdx.x];
         out[threadIdx.x] = t;
     }
 }
@@ -225,6 +505,41 @@ __device__ __forceinline__ void block_sum_store(double (&v)[S], double *__restri
 //   - (u_prev^3 - u_prev)/eps - eps (L_s u), which avoids the cancellation
 // of the two large terms c u_prev and c u.
 template <int K>
+__device__ __forceinline__ void energy_row(const SellView &A, const Coeffs &cf, int slice, int lane,
+                                           const float (&acc)[K], const float *__restrict__ u,
+                                           const float *__restrict__ u_prev, double (&red)[6]) {
+    const int r = slice * kSliceRows + lane;
+    if (r >= A.n) return;
+    const uint32_t info = A.rowinfo[r];
+    float x[K];
+    load_row<K>(u + (size_t)r * K, x);
+    const uint32_t tag = info & 0xFFu;
+    const bool lab = tag != kTagUnlabelled;
+    float q = 0.f, wl = 0.f, fd = 0.f, rr = 0.f, bb = 0.f, nf = 0.f;
+    float xp[K];
+    if (u_prev) load_row<K>(u_prev + (size_t)r * K, xp);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float ls = x[k] - acc[k];
+        q = fmaf(x[k], ls, q);
+        const float s = x[k] * x[k] - 1.0f;
+        wl = fmaf(s, s, wl);
+        const float y = lab ? prior_of<K>(tag, k) : 0.0f;
+        if (lab) fd = fmaf(x[k] - y, x[k] - y, fd);
+        if (!isfinite(x[k])) nf += 1.0f;
+        if (u_prev) {
+            const float up = xp[k];
+            const float grad_w = (up * up * up - up) * cf.inv_eps;
+            const float b = (lab ? cf.eta * y : 0.0f) + cf.c * up - grad_w;
+            const float res = cf.c * (up - x[k]) + (lab ? cf.eta * (y - x[k]) : 0.0f) - grad_w - cf.eps * ls;
+            rr = fmaf(res, res, rr);
+            bb = fmaf(b, b, bb);
+        }
+    }
+    red[0] += q; red[1] += wl; red[2] += fd; red[3] += rr; red[4] += bb; red[5] += nf;
+}
+
+template <int K>
 __global__ void __launch_bounds__(kBlockThreads)
 energy_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u,
               const float *__restrict__ u_prev, double *__restrict__ partials) {
@@ -233,42 +548,35 @@ energy_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u,
     double red[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (slice < A.n_slices) {
         const int64_t base = A.slice_off[slice];
-        const int width = (int)((A.slice_off[slice + 1] - base) >> 5);
-        const int r = slice * kSliceRows + lane;
-        const uint32_t info = A.rowinfo[r];
         float acc[K];
-        gather_row_sum<K>(A, base, width, lane, u, acc);
-        if (r < A.n) {
-            float x[K];
-            load_row<K>(u + (size_t)r * K, x);
-            const uint32_t tag = info & 0xFFu;
-            const bool lab = tag != kTagUnlabelled;
-            float q = 0.f, wl = 0.f, fd = 0.f, rr = 0.f, bb = 0.f, nf = 0.f;
-            float xp[K];
-            if (u_prev) load_row<K>(u_prev + (size_t)r * K, xp);
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const float ls = x[k] - acc[k];
-                q = fmaf(x[k], ls, q);
-                const float s = x[k] * x[k] - 1.0f;
-                wl = fmaf(s, s, wl);
-                const float y = lab ? prior_of<K>(tag, k) : 0.0f;
-                if (lab) fd = fmaf(x[k] - y, x[k] - y, fd);
-                if (!isfinite(x[k])) nf += 1.0f;
-                if (u_prev) {
-                    const float up = xp[k];
-                    const float grad_w = (up * up * up - up) * cf.inv_eps;
-                    const float b = (lab ? cf.eta * y : 0.0f) + cf.c * up - grad_w;
-                    const float res = cf.c * (up - x[k]) + (lab ? cf.eta * (y - x[k]) : 0.0f)
-                                      - grad_w - cf.eps * ls;
-                    rr = fmaf(res, res, rr);
-                    bb = fmaf(b, b, bb);
-                }
-            }
-            red[0] = q; red[1] = wl; red[2] = fd; red[3] = rr; red[4] = bb; red[5] = nf;
-        }
+        gather_row_sum<K>(A, base, row_len(A, slice, lane), lane, u, acc);
+        energy_row<K>(A, cf, slice, lane, acc, u, u_prev, red);
     }
     block_sum_store<6>(red, partials + (size_t)blockIdx.x * kRedSlots);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kTileThreads, PDCA_TILE_MIN_BLOCKS)
+energy_tiled_kernel(const SellView A, const TileView T, const Coeffs cf, const float *__restrict__ u,
+                    const float *__restrict__ u_prev, double *__restrict__ partials) {
+    extern __shared__ float4 smem_f4[];
+    float *hs = reinterpret_cast<float *>(smem_f4);
+    const int tile = blockIdx.x;
+    const int64_t h0 = T.halo_off[tile];
+    const bool staged = T.halo_off[tile + 1] - h0 <= T.smem_rows;
+    if (staged) load_halo<K>(T, tile, u, hs);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    double red[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int s = threadIdx.x >> 5; s < kTileSlices; s += kTileThreads / 32) {
+        const int slice = tile * kTileSlices + s;
+        if (slice >= A.n_slices) break;
+        const int64_t base = A.slice_off[slice];
+        float acc[K];
+        tile_row_sum<K>(T, A, base, row_len(A, slice, lane), lane, staged, T.halo_idx + h0, hs, u, acc);
+        energy_row<K>(A, cf, slice, lane, acc, u, u_prev, red);
+    }
+    block_sum_store<6, kTileThreads / 32>(red, partials + (size_t)blockIdx.x * kRedSlots);
 }
 
 // Single block: fixed-order sum of the block partials, then the scalars.
@@ -321,6 +629,20 @@ power_init_kernel(const SellView A, const int32_t *__restrict__ perm, float *__r
 }
 
 // y = L_s (s x) with s = *scale; partial sums of y.y, (s x).y, (s x).(s x).
+__device__ __forceinline__ void power_row(const SellView &A, int slice, int lane, float acc, float s,
+                                          const float *__restrict__ x, float *__restrict__ y,
+                                          double (&red)[3]) {
+    const int r = slice * kSliceRows + lane;
+    const float xs = s * __ldg(x + r);
+    const float yi = xs - s * acc;
+    y[r] = yi;
+    if (r < A.n) {
+        red[0] += (double)yi * (double)yi;
+        red[1] += (double)xs * (double)yi;
+        red[2] += (double)xs * (double)xs;
+    }
+}
+
 __global__ void __launch_bounds__(kBlockThreads)
 power_spmv_kernel(const SellView A, const float *__restrict__ x, const double *__restrict__ scale,
                   float *__restrict__ y, double *__restrict__ partials) {
@@ -329,21 +651,35 @@ power_spmv_kernel(const SellView A, const float *__restrict__ x, const double *_
     double red[3] = {0.0, 0.0, 0.0};
     if (slice < A.n_slices) {
         const int64_t base = A.slice_off[slice];
-        const int width = (int)((A.slice_off[slice + 1] - base) >> 5);
-        const int r = slice * kSliceRows + lane;
-        const float s = (float)(*scale);
         float acc[1];
-        gather_row_sum<1>(A, base, width, lane, x, acc);
-        const float xs = s * __ldg(x + r);
-        const float yi = xs - s * acc[0];
-        y[r] = yi;
-        if (r < A.n) {
-            red[0] = (double)yi * (double)yi;
-            red[1] = (double)xs * (double)yi;
-            red[2] = (double)xs * (double)xs;
-        }
+        gather_row_sum<1>(A, base, row_len(A, slice, lane), lane, x, acc);
+        power_row(A, slice, lane, acc[0], (float)(*scale), x, y, red);
     }
     block_sum_store<3>(red, partials + (size_t)blockIdx.x * kRedSlots);
+}
+
+__global__ void __launch_bounds__(kTileThreads, PDCA_TILE_MIN_BLOCKS)
+power_spmv_tiled_kernel(const SellView A, const TileView T, const float *__restrict__ x,
+                        const double *__restrict__ scale, float *__restrict__ y, double *__restrict__ partials) {
+    extern __shared__ float4 smem_f4[];
+    float *hs = reinterpret_cast<float *>(smem_f4);
+    const int tile = blockIdx.x;
+    const int64_t h0 = T.halo_off[tile];
+    const bool staged = T.halo_off[tile + 1] - h0 <= T.smem_rows;
+    if (staged) load_halo<1>(T, tile, x, hs);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const float s = (float)(*scale);
+    double red[3] = {0.0, 0.0, 0.0};
+    for (int sl = threadIdx.x >> 5; sl < kTileSlices; sl += kTileThreads / 32) {
+        const int slice = tile * kTileSlices + sl;
+        if (slice >= A.n_slices) break;
+        const int64_t base = A.slice_off[slice];
+        float acc[1];
+        tile_row_sum<1>(T, A, base, row_len(A, slice, lane), lane, staged, T.halo_idx + h0, hs, x, acc);
+        power_row(A, slice, lane, acc[0], s, x, y, red);
+    }
+    block_sum_store<3, kTileThreads / 32>(red, partials + (size_t)blockIdx.x * kRedSlots);
 }
 
 // scale <- 1/sqrt(sum y.y); lambda <- sum (s x).y / sum (s x).(s x)
@@ -415,21 +751,49 @@ __global__ void permute_in_kernel(int32_t n, int32_t n_pad, int32_t K, const flo
     u[q] = r < n ? in[(int64_t)perm[r] * K + k] : (K == 1 ? 0.0f : 2.0f / K - 1.0f);
 }
 
+// Dynamic shared memory above the default 48 KiB needs an opt-in per kernel.
+template <class Kern>
+cudaError_t allow_smem(Kern k, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 template <int K>
-cudaError_t sweep_k(bool project, const SellView &A, const Coeffs &cf, const float *v_src,
+cudaError_t sweep_k(bool project, const SellView &A, const TileView *T, const Coeffs &cf, const float *v_src,
                     const float *u_t, float *v_dst, cudaStream_t st) {
+    constexpr bool P = K >= 2;
+    if (T) {
+        const size_t sm = tile_smem_bytes(K, T->smem_rows);
+        if (project && P) {
+            cudaError_t e = allow_smem(sweep_tiled_kernel<K, P>, sm);
+            if (e != cudaSuccess) return e;
+            sweep_tiled_kernel<K, P><<<T->n_tiles, kTileThreads, sm, st>>>(A, *T, cf, v_src, u_t, v_dst);
+        } else {
+            cudaError_t e = allow_smem(sweep_tiled_kernel<K, false>, sm);
+            if (e != cudaSuccess) return e;
+            sweep_tiled_kernel<K, false><<<T->n_tiles, kTileThreads, sm, st>>>(A, *T, cf, v_src, u_t, v_dst);
+        }
+        return cudaGetLastError();
+    }
     const int blocks = (A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (project && K >= 2)
-        sweep_kernel<K, (K >= 2)><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
+    if (project && P)
+        sweep_kernel<K, P><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
     else
         sweep_kernel<K, false><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
     return cudaGetLastError();
 }
 
 template <int K>
-cudaError_t energy_k(const SellView &A, const Coeffs &cf, const float *u, const float *u_prev,
+cudaError_t energy_k(const SellView &A, const TileView *T, const Coeffs &cf, const float *u, const float *u_prev,
                      double *partials, cudaStream_t st) {
-    energy_kernel<K><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, cf, u, u_prev, partials);
+    if (T) {
+        const size_t sm = tile_smem_bytes(K, T->smem_rows);
+        cudaError_t e = allow_smem(energy_tiled_kernel<K>, sm);
+        if (e != cudaSuccess) return e;
+        energy_tiled_kernel<K><<<T->n_tiles, kTileThreads, sm, st>>>(A, *T, cf, u, u_prev, partials);
+    } else {
+        energy_kernel<K><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, cf, u, u_prev, partials);
+    }
     return cudaGetLastError();
 }
 
@@ -443,6 +807,9 @@ cudaError_t labels_k(int32_t n, const float *u, const int32_t *perm, int32_t *ou
 
 int energy_blocks(int32_t n_slices) { return (n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock; }
 
+int reduce_parts(const SellView &A, const TileView *T) { return T ? T->n_tiles : energy_blocks(A.n_slices); }
+
+
 #define PDCA_DISPATCH_K(K, CALL)                                                      \
     switch (K) {                                                                      \
     case 1: return CALL(1); case 2: return CALL(2); case 3: return CALL(3);           \
@@ -454,19 +821,19 @@ int energy_blocks(int32_t n_slices) { return (n_slices + kWarpsPerBlock - 1) / k
     default: return cudaErrorInvalidValue;                                            \
     }
 
-cudaError_t launch_sweep(int K, bool project, const SellView &A, const Coeffs &cf,
+cudaError_t launch_sweep(int K, bool project, const SellView &A, const TileView *T, const Coeffs &cf,
                          const float *v_src, const float *u_t, float *v_dst, cudaStream_t st) {
     if (A.n_slices <= 0) return cudaSuccess;
     count_launches(1);
-#define CALL(KK) sweep_k<KK>(project, A, cf, v_src, u_t, v_dst, st)
+#define CALL(KK) sweep_k<KK>(project, A, T, cf, v_src, u_t, v_dst, st)
     PDCA_DISPATCH_K(K, CALL)
 #undef CALL
 }
 
-cudaError_t launch_energy(int K, const SellView &A, const Coeffs &cf, const float *u,
+cudaError_t launch_energy(int K, const SellView &A, const TileView *T, const Coeffs &cf, const float *u,
                           const float *u_prev, double *partials, cudaStream_t st) {
     count_launches(1);
-#define CALL(KK) energy_k<KK>(A, cf, u, u_prev, partials, st)
+#define CALL(KK) energy_k<KK>(A, T, cf, u, u_prev, partials, st)
     PDCA_DISPATCH_K(K, CALL)
 #undef CALL
 }
@@ -487,10 +854,17 @@ cudaError_t launch_power_init(const SellView &A, const int32_t *perm, float *x, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_power_spmv(const SellView &A, const float *x, const double *scale, float *y,
-                              double *partials, cudaStream_t st) {
+cudaError_t launch_power_spmv(const SellView &A, const TileView *T, const float *x, const double *scale,
+                              float *y, double *partials, cudaStream_t st) {
     count_launches(1);
-    power_spmv_kernel<<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, x, scale, y, partials);
+    if (T) {
+        const size_t sm = tile_smem_bytes(1, T->smem_rows);
+        cudaError_t e = allow_smem(power_spmv_tiled_kernel, sm);
+        if (e != cudaSuccess) return e;
+        power_spmv_tiled_kernel<<<T->n_tiles, kTileThreads, sm, st>>>(A, *T, x, scale, y, partials);
+    } else {
+        power_spmv_kernel<<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, x, scale, y, partials);
+    }
     return cudaGetLastError();
 }
 

@@ -45,9 +45,9 @@ def label_mismatch(lab_gpu, u_ref, K):
 
 
 def make_pair(B, rp, col, w, K, mask, lab, eps, eta, c, precond, damping=0.5, lam=0.0,
-              sort_window=0, omp=False):
+              sort_window=0, omp=False, **layout):
     prm = B.make_params(eps=eps, eta=eta, c=c, precond=precond, damping=damping, lambda_max=lam,
-                        sort_window=sort_window)
+                        sort_window=sort_window, **layout)
     gpu = B.Problem(rp, col, w, K, mask, lab, prm)
     ref = oracle.Problem(rp, col, w, K, mask, lab, eps, eta, c, precond=precond, damping=damping,
                          lambda_max=lam, omp=omp)
@@ -81,14 +81,24 @@ def run_parity(gpu, ref, outer, inner, check_energy=True):
 # small random graphs: ragged tails, every K, every preconditioner
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n", [2, 31, 33, 257, 1031])
+LAYOUTS = {
+    "tiled": dict(reorder=1, tiling=2),
+    "bfs_plain": dict(reorder=1, tiling=0),
+    "window_sort": dict(reorder=0, tiling=0),
+}
+
+
+@pytest.mark.parametrize("n", [2, 31, 33, 257, 1031, 2100])
 @pytest.mark.parametrize("K", [1, 3, 4])
-def test_random_graph_sizes(B, n, K):
+@pytest.mark.parametrize("layout", list(LAYOUTS))
+def test_random_graph_sizes(B, n, K, layout):
     rp, col, w = random_graph(n, 6, seed=n * 7 + K)
     rng = np.random.default_rng(n + K)
     mask = (rng.uniform(size=n) < 0.2).astype(np.uint8)
     lab = rng.integers(0, max(K, 2), size=n).astype(np.int32)
-    gpu, ref = make_pair(B, rp, col, w, K, mask, lab, 1.0, 5.0, 4.0, B.PDCA_JACOBI_PERTURBED)
+    gpu, ref = make_pair(B, rp, col, w, K, mask, lab, 1.0, 5.0, 4.0, B.PDCA_JACOBI_PERTURBED,
+                         **LAYOUTS[layout])
+    assert gpu.layout()["tiled"] == (layout == "tiled")
     run_parity(gpu, ref, 4, 3)
 
 
@@ -130,9 +140,57 @@ def test_sort_windows(B, sw):
     mask = (rng.uniform(size=n) < 0.05).astype(np.uint8)
     lab = rng.integers(0, 4, size=n).astype(np.int32)
     gpu, ref = make_pair(B, rp, col, w, 4, mask, lab, 1.0, 20.0, 22.0, B.PDCA_JACOBI_PERTURBED,
-                         sort_window=sw)
+                         sort_window=sw, reorder=0)
     assert gpu.layout()["sort_window"] == sw
     run_parity(gpu, ref, 3, 3)
+
+
+@pytest.mark.parametrize("K", [1, 4, 10])
+def test_tiled_equals_plain_bitwise(B, K):
+    """The tiled and plain kernels add the same products in the same order, so
+    on the same renumbering their iterates agree bit for bit."""
+    wl = make_workload("voronoi2048", size=192)
+    rng = np.random.default_rng(K)
+    lab = rng.integers(0, K if K > 1 else 2, size=wl.n).astype(np.int32)
+    out = {}
+    for mode in ("tiled", "bfs_plain"):
+        prm = B.make_params(eps=1.0, eta=50.0, c=52.0, precond=B.PDCA_RICHARDSON, lambda_max=1.99,
+                            **LAYOUTS[mode])
+        g = B.Problem(wl.row_ptr, wl.col, wl.w, K, wl.fid_mask, lab, prm)
+        assert g.layout()["tiled"] == (mode == "tiled")
+        g.solve(3, 4)
+        out[mode] = (g.get_u(), g.energy())
+    np.testing.assert_array_equal(out["tiled"][0], out["bfs_plain"][0])
+    assert out["tiled"][1][0] == out["bfs_plain"][1][0]
+
+
+def test_tiling_with_oversized_halos(B):
+    """gmm70k (K = 10, no spatial locality): most tile halos exceed the shared
+    memory budget; AUTO uses the plain kernels, ON still tiles (oversized
+    tiles gather through their halo lists) and gives the same bits."""
+    wl = make_workload("gmm70k")
+    g = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels,
+                  B.params_from_workload(wl.params))
+    assert not g.layout()["tiled"]
+    t = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels,
+                  B.params_from_workload(wl.params, tiling=2))
+    assert t.layout()["tiled"]
+    g.solve(3, 5)
+    t.solve(3, 5)
+    np.testing.assert_array_equal(g.get_u(), t.get_u())
+
+
+def test_voronoi_layout_is_tiled(B):
+    wl = make_workload("voronoi2048", size=512)
+    g = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels,
+                  B.params_from_workload(wl.params, tiling=2))
+    lay = g.layout()
+    assert lay["tiled"] and 0 < lay["max_halo"] <= 65536
+    # BFS blocks keep the halo of a 512-row tile near 3-4 rows per row
+    assert lay["halo_rows"] < 5 * wl.n
+    auto = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels,
+                     B.params_from_workload(wl.params))
+    assert not auto.layout()["tiled"]
 
 
 def test_hub_rows(B):
