@@ -264,9 +264,15 @@ __device__ __forceinline__ float prior_of(uint32_t tag, int k) {
 // (sort-and-threshold method of Held, Wolfe and Crowder), written directly in
 // u: with u sorted descending and S_j = sum_{i<=j} u_(i), rho is the largest
 // j with j u_(j) - S_j + 2 > 0, lambda = (S_rho + rho - 2)/rho (twice the
-// threshold theta of the v coding) and u' = max(u - lambda, -1).  (Substituting v = (u+1)/2 into the textbook
-// conditions gives these.)  The sort and the test run in FP32; the threshold
-// sums S_j and lambda are FP64.
+// threshold theta of the v coding) and u' = max(u - lambda, -1).
+// The threshold sums S_j are kept as an unevaluated pair hi + lo of floats
+// (Knuth's TwoSum), about 48 significant bits, so no FP64 unit is needed.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
 template <int K>
 __device__ __forceinline__ void project_simplex(float (&u)[K]) {
     float mu[K];
@@ -281,22 +287,22 @@ __device__ __forceinline__ void project_simplex(float (&u)[K]) {
             mu[j + 1] = fminf(a, b);
         }
     }
-    double run = 0.0, s_rho = mu[0];
+    float hi = 0.0f, lo = 0.0f, s_hi = mu[0], s_lo = 0.0f;
     int rho = 1;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        run += (double)mu[j];
-        if ((float)(j + 1) * mu[j] - (float)run + 2.0f > 0.0f) {
+        float e;
+        two_sum(hi, mu[j], hi, e);
+        lo += e;
+        if (((float)(j + 1) * mu[j] - hi) - lo + 2.0f > 0.0f) {
             rho = j + 1;
-            s_rho = run;
+            s_hi = hi;
+            s_lo = lo;
         }
     }
-    const double lam = (s_rho + (double)rho - 2.0) / (double)rho;
+    const float lam = (((s_hi - 2.0f) + (float)rho) + s_lo) / (float)rho;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const double x = (double)u[k] - lam;
-        u[k] = (float)(x > -1.0 ? x : -1.0);
-    }
+    for (int k = 0; k < K; ++k) u[k] = fmaxf(u[k] - lam, -1.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -478,15 +484,22 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Sum S values over the block (WARPS warps) in a fixed order and store them
-// at out[0..S).
+// at out[0..S): each warp sums its 32 lanes in FP32 (fixed shuffle tree),
+// the warp totals are summed in FP64.
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
 template <int S, int WARPS = kWarpsPerBlock>
-__device__ __forceinline__ void block_sum_store(double (&v)[S], double *__restrict__ out) {
+__device__ __forceinline__ void block_sum_store(float (&v)[S], double *__restrict__ out) {
     __shared__ double sm[WARPS][S];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        const double t = warp_sum(v[s]);
-        if (lane == 0) sm[warp][s] = t;
+        const float t = warp_sum_f(v[s]);
+        if (lane == 0) sm[warp][s] = (double)t;
     }
     __syncthreads();
     if (threadIdx.x < S) {
@@ -497,7 +510,7 @@ __device__ __forceinline__ void block_sum_store(double (&v)[S], double *__restri
     }
 }
 
-// Per-row contributions (FP32 inside a row, FP64 across rows):
+// Per-row contributions (FP32 inside a row and a warp, FP64 across warps):
 //   quad += u_i . (L_s u)_i,  well += sum_k (u_ik^2 - 1)^2,
 //   fid  += Lambda_i sum_k (u_ik - y_ik)^2,
 //   rr   += ||b_i - (T u)_i||^2 with b from u_prev, bb += ||b_i||^2.
@@ -507,7 +520,7 @@ __device__ __forceinline__ void block_sum_store(double (&v)[S], double *__restri
 template <int K>
 __device__ __forceinline__ void energy_row(const SellView &A, const Coeffs &cf, int slice, int lane,
                                            const float (&acc)[K], const float *__restrict__ u,
-                                           const float *__restrict__ u_prev, double (&red)[6]) {
+                                           const float *__restrict__ u_prev, float (&red)[6]) {
     const int r = slice * kSliceRows + lane;
     if (r >= A.n) return;
     const uint32_t info = A.rowinfo[r];
@@ -545,7 +558,7 @@ energy_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u,
               const float *__restrict__ u_prev, double *__restrict__ partials) {
     const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    double red[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    float red[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (slice < A.n_slices) {
         const int64_t base = A.slice_off[slice];
         float acc[K];
@@ -567,7 +580,7 @@ energy_tiled_kernel(const SellView A, const TileView T, const Coeffs cf, const f
     if (staged) load_halo<K>(T, tile, u, hs);
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    double red[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    float red[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int s = threadIdx.x >> 5; s < kTileSlices; s += kTileThreads / 32) {
         const int slice = tile * kTileSlices + s;
         if (slice >= A.n_slices) break;
@@ -617,13 +630,13 @@ power_init_kernel(const SellView A, const int32_t *__restrict__ perm, float *__r
                   double *__restrict__ partials) {
     const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    double red[3] = {0.0, 0.0, 0.0};
+    float red[3] = {0.f, 0.f, 0.f};
     if (slice < A.n_slices) {
         const int r = slice * kSliceRows + lane;
         float xi = 0.0f;
         if (r < A.n) xi = (float)(1.0 + 0.5 * sin((double)perm[r] + 1.0));
         x[r] = xi;
-        red[0] = (double)xi * (double)xi;
+        red[0] = xi * xi;
     }
     block_sum_store<3>(red, partials + (size_t)blockIdx.x * kRedSlots);
 }
@@ -631,15 +644,15 @@ power_init_kernel(const SellView A, const int32_t *__restrict__ perm, float *__r
 // y = L_s (s x) with s = *scale; partial sums of y.y, (s x).y, (s x).(s x).
 __device__ __forceinline__ void power_row(const SellView &A, int slice, int lane, float acc, float s,
                                           const float *__restrict__ x, float *__restrict__ y,
-                                          double (&red)[3]) {
+                                          float (&red)[3]) {
     const int r = slice * kSliceRows + lane;
     const float xs = s * __ldg(x + r);
     const float yi = xs - s * acc;
     y[r] = yi;
     if (r < A.n) {
-        red[0] += (double)yi * (double)yi;
-        red[1] += (double)xs * (double)yi;
-        red[2] += (double)xs * (double)xs;
+        red[0] = fmaf(yi, yi, red[0]);
+        red[1] = fmaf(xs, yi, red[1]);
+        red[2] = fmaf(xs, xs, red[2]);
     }
 }
 
@@ -648,7 +661,7 @@ power_spmv_kernel(const SellView A, const float *__restrict__ x, const double *_
                   float *__restrict__ y, double *__restrict__ partials) {
     const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    double red[3] = {0.0, 0.0, 0.0};
+    float red[3] = {0.f, 0.f, 0.f};
     if (slice < A.n_slices) {
         const int64_t base = A.slice_off[slice];
         float acc[1];
@@ -670,7 +683,7 @@ power_spmv_tiled_kernel(const SellView A, const TileView T, const float *__restr
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const float s = (float)(*scale);
-    double red[3] = {0.0, 0.0, 0.0};
+    float red[3] = {0.f, 0.f, 0.f};
     for (int sl = threadIdx.x >> 5; sl < kTileSlices; sl += kTileThreads / 32) {
         const int slice = tile * kTileSlices + sl;
         if (slice >= A.n_slices) break;
