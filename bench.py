@@ -66,10 +66,31 @@ def labels_bytes(n, K, s_u=4):
     return n * (K * s_u + 4)
 
 
-def solve_bytes(wl, lay=None):
+def mixed_pass_bytes(nnz, n, K, inner):
+    """Algorithmic bytes of the passes of one mixed-precision outer step:
+    int32 columns + BF16 weights per entry; pass 0 reads the FP32 iterate and
+    writes r and e^1 (16-bit); correction sweeps read e and r and write e; the
+    last reads e, r and u^t and writes u^{t+1} (FP32); one tag byte per row."""
+    op = nnz * (4 + 2)
+    if inner == 1:
+        return [op + n * (2 * K * 4 + 1)]
+    first = op + n * (K * 4 + 2 * K * 2 + 1)
+    mid = op + n * (3 * K * 2 + 1)
+    last = op + n * (2 * K * 2 + 2 * K * 4 + 1)
+    return [first] + [mid] * (inner - 2) + [last]
+
+
+def solve_bytes(wl, lay=None, precision=0):
     p = wl.params
+    if precision:
+        sweeps = p["outer"] * sum(mixed_pass_bytes(wl.nnz, wl.n, wl.K, p["inner"]))
+        ebytes = wl.nnz * (4 + 2) + wl.n * (2 * wl.K * 4 + 1)
+        return sweeps + ebytes + labels_bytes(wl.n, wl.K)
     return (p["outer"] * p["inner"] * sweep_bytes(wl.nnz, wl.n, wl.K, lay)
             + energy_bytes(wl.nnz, wl.n, wl.K, lay) + labels_bytes(wl.n, wl.K))
+
+
+PRECISIONS = {"fp32": 0, "fp16u": 1, "bf16u": 2}
 
 
 LAYOUT_PARAMS = {"auto": dict(reorder=1, tiling=0), "tiled": dict(reorder=1, tiling=2),
@@ -267,7 +288,9 @@ def run_ours(args, wl, world, rank, local):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     p = wl.params
-    prm = B.params_from_workload(p, sort_window=args.sort_window, **LAYOUT_PARAMS[args.layout])
+    precision = PRECISIONS[args.precision]
+    prm = B.params_from_workload(p, sort_window=args.sort_window, precision=precision,
+                                 **LAYOUT_PARAMS[args.layout])
     t0 = time.perf_counter()
     prob = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm, device=dev)
     torch.cuda.synchronize(dev)
@@ -308,14 +331,18 @@ def run_ours(args, wl, world, rank, local):
     ms_total = ev0.elapsed_time(ev1)
     ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
-    bytes_step = solve_bytes(wl, lay)
+    bytes_step = solve_bytes(wl, lay, precision)
     value = world * bytes_step * args.steps / (ms_total * 1e-3) / 1e9
 
     hbm, kind = peaks()
-    sb = sweep_bytes(wl.nnz, wl.n, wl.K, lay)
+    if precision:
+        passes = mixed_pass_bytes(wl.nnz, wl.n, wl.K, p["inner"])
+        sb = sum(passes) / len(passes)          # average algorithmic bytes per timed pass
+    else:
+        sb = sweep_bytes(wl.nnz, wl.n, wl.K, lay)
     sweep_ms = sweep_ms_tot / max(sweep_launches, 1)
     achieved = sb / (sweep_ms * 1e-3) / 1e9
-    traffic = sweep_traffic_record()
+    traffic = None if precision else sweep_traffic_record()
 
     # end to end through the C interface from pinned host buffers
     e2e = None
@@ -375,8 +402,11 @@ def run_ours(args, wl, world, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(wl, {"layout": args.layout, "tiled": lay["tiled"],
+        "vs_baseline": None, "dtype": {0: "f32", 1: "bf16 w / f16 u, f32 accumulate",
+                                       2: "bf16 w / bf16 u, f32 accumulate"}[precision],
+        "data": "synthetic",
+        "config": workload_config(wl, {"layout": args.layout, "precision": args.precision,
+                                       "tiled": lay["tiled"],
                                        "sort_window": lay["sort_window"],
                                        "sell_entries": lay["sell_entries"],
                                        "halo_rows": lay["halo_rows"], "max_halo": lay["max_halo"],
@@ -385,8 +415,9 @@ def run_ours(args, wl, world, rank, local):
         "pct_of_peak": 100.0 * value / world / hbm,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
-                     "kernel": ("sweep_tiled_kernel<4,*>" if lay["tiled"] else "sweep_kernel<4,*>")
-                               + " (fused sweep)",
+                     "kernel": ("mixed_residual_kernel + mixed_sweep_kernel (average per pass)" if precision
+                                else ("sweep_tiled_kernel<4,*>" if lay["tiled"] else "sweep_kernel<4,*>")
+                                + " (fused sweep)"),
                      "bytes_per_launch": sb, "ms_per_launch": sweep_ms,
                      "launches_timed": sweep_launches, "peak_kind": kind},
         "gpu_launches": int(launches),
@@ -411,6 +442,8 @@ def main():
     ap.add_argument("--layout", choices=sorted(LAYOUT_PARAMS), default="auto",
                     help="auto: BFS renumbering, neighbour rows gathered through L1/L2; "
                          "tiled: BFS renumbering + shared-memory halo tiles; window: degree sort only")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32",
+                    help="fp32, or BF16 weights with FP16 / BF16 correction storage")
     ap.add_argument("--sort-window", type=int, default=0,
                     help="degree-sort window (power of two; 0 = library default)")
     ap.add_argument("--no-e2e", action="store_true")

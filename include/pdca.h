@@ -99,9 +99,19 @@ enum { PDCA_REORDER_NONE = 0, PDCA_REORDER_BFS = 1 };
  *                    16-bit local columns. */
 enum { PDCA_TILING_AUTO = 0, PDCA_TILING_OFF = 1, PDCA_TILING_ON = 2 };
 
-/* Arithmetic of the sweeps.  Only PDCA_FP32 is implemented: FP32 storage of
- * the pre-scaled weights and of u, FP32 accumulation, FP64 reductions. */
-enum { PDCA_FP32 = 0 };
+/* Arithmetic of the sweeps.
+ *   PDCA_FP32               FP32 pre-scaled weights and iterates, FP32
+ *                           accumulation, FP64 accumulation across warps in the
+ *                           reductions;
+ *   PDCA_MIXED_BF16W_FP16U  BF16 weights; per outer step an FP32 pass forms the
+ *                           residual r = b^t - T u^t from the FP32 iterate, the
+ *                           inner sweeps then iterate the correction
+ *                           e <- e + G^{-1}(r - T e) with r and e stored in FP16
+ *                           (FP32 arithmetic), and u^{t+1} = u^t + e in FP32 --
+ *                           the same iteration as the FP32 sweeps, rearranged;
+ *   PDCA_MIXED_BF16W_BF16U  the same with r and e stored in BF16.
+ * The mixed forms use the plain (non-tiled) kernels. */
+enum { PDCA_FP32 = 0, PDCA_MIXED_BF16W_FP16U = 1, PDCA_MIXED_BF16W_BF16U = 2 };
 
 typedef struct {
     double eps;          /* diffuse interface parameter epsilon > 0                    */
@@ -116,7 +126,7 @@ typedef struct {
                             the power method at create time, then use
                             min(2, 1.001 * estimate) (2 bounds it, Prop. diagonal:pre) */
     int32_t power_iters; /* power-method iterations (150 in the paper's experiments)   */
-    int32_t precision;   /* PDCA_FP32                                                  */
+    int32_t precision;   /* PDCA_FP32 / PDCA_MIXED_BF16W_FP16U / PDCA_MIXED_BF16W_BF16U */
     int32_t sort_window; /* rows are sorted by degree inside windows of this many rows
                             (a power of two in [32, 8192]).  PDCA_REORDER_NONE: 0 = the
                             smallest window with at most 10% slice padding;

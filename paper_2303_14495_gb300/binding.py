@@ -33,7 +33,7 @@ STATUS_NAMES = {
 PDCA_STATIC_MAX_N = 1 << 20
 PDCA_LAP_NORMALIZED, PDCA_LAP_UNNORMALIZED = 0, 1
 PDCA_JACOBI_DAMPED, PDCA_JACOBI_PERTURBED, PDCA_RICHARDSON = 0, 1, 2
-PDCA_FP32 = 0
+PDCA_FP32, PDCA_MIXED_BF16W_FP16U, PDCA_MIXED_BF16W_BF16U = 0, 1, 2
 PDCA_REORDER_NONE, PDCA_REORDER_BFS = 0, 1
 PDCA_TILING_AUTO, PDCA_TILING_OFF, PDCA_TILING_ON = 0, 1, 2
 

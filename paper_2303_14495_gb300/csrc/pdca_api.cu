@@ -42,6 +42,7 @@ struct Layout {
     std::vector<int64_t> slice_off;    // n_slices + 1 (exact; filled at create for host order)
     size_t o_col, o_w, o_slice, o_rowinfo, o_perm, o_iperm, o_u[3], o_part, o_red, o_scal, o_trace;
     size_t o_hoff, o_hidx;
+    size_t o_mr, o_me[2];              // mixed precision: r and the two corrections (16-bit)
     size_t o_srp, o_scol, o_sw, o_sdeg, o_smask, o_slab, o_status;
     size_t persistent = 0, total = 0;
 };
@@ -89,7 +90,9 @@ pdca_status check_params(const pdca_params &p) {
     if (!(fin(p.eps) && p.eps > 0) || !(fin(p.c) && p.c > 0) || !(fin(p.eta) && p.eta >= 0))
         return PDCA_ERR_INVALID_ARG;
     if (p.laplacian != PDCA_LAP_NORMALIZED) return PDCA_ERR_INVALID_ARG;
-    if (p.precision != PDCA_FP32) return PDCA_ERR_INVALID_ARG;
+    if (p.precision != PDCA_FP32 && p.precision != PDCA_MIXED_BF16W_FP16U && p.precision != PDCA_MIXED_BF16W_BF16U)
+        return PDCA_ERR_INVALID_ARG;
+    if (p.precision != PDCA_FP32 && p.tiling == PDCA_TILING_ON) return PDCA_ERR_INVALID_ARG;
     if (p.precond < PDCA_JACOBI_DAMPED || p.precond > PDCA_RICHARDSON) return PDCA_ERR_INVALID_ARG;
     if (!(fin(p.delta0) && p.delta0 >= 0) || !(fin(p.lambda_max) && p.lambda_max >= 0))
         return PDCA_ERR_INVALID_ARG;
@@ -221,6 +224,10 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     L.o_trace = take(8 * 2 * (size_t)kTraceCap);
     L.o_hoff = take(8 * ((size_t)L.n_tiles + 1));
     L.o_hidx = take(4 * (size_t)L.halo_cap);
+    const size_t half_rows = prm.precision == PDCA_FP32 ? 0 : 2 * np * (size_t)K;
+    L.o_mr = take(half_rows);
+    L.o_me[0] = take(half_rows);
+    L.o_me[1] = take(half_rows);
     L.persistent = o;
     // create-time staging of the CSR input
     L.o_srp = take(8 * (nn + 1));
@@ -264,13 +271,16 @@ struct pdca_problem {
     bool tiled = false;
     TileView tv{};
     int64_t halo_rows = 0;
+    bool mixed = false, bf16u = false;
+    void *mr = nullptr, *me[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
 
     SellView view() const {
         SellView A;
         A.col = sell_col;
-        A.w = sell_w;
+        A.w = mixed ? nullptr : sell_w;
+        A.wb = mixed ? reinterpret_cast<const __nv_bfloat16 *>(sell_w) : nullptr;
         A.slice_off = slice_off;
         A.rowinfo = rowinfo;
         A.n_slices = L.n_slices;
@@ -291,7 +301,9 @@ pdca_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PDCA_OK : PDC
         if (_e != cudaSuccess) return PDCA_ERR_CUDA; \
     } while (0)
 
-pdca_status sweep(pdca_problem *h, bool project, const float *src, const float *ut, float *dst) {
+// Launch one sweep-like pass; with profiling on, bracket it with events.
+template <class F>
+pdca_status timed_pass(pdca_problem *h, F launch) {
     cudaEvent_t a = nullptr, b = nullptr;
     if (h->prof) {
         while (h->ev.size() < h->ev_used + 2) {
@@ -304,14 +316,47 @@ pdca_status sweep(pdca_problem *h, bool project, const float *src, const float *
         h->ev_used += 2;
         PDCA_TRY(cudaEventRecord(a, h->stream));
     }
-    PDCA_TRY(launch_sweep(h->L.K, project, h->view(), h->tiles(), h->cf, src, ut, dst, h->stream));
+    PDCA_TRY(launch());
     if (h->prof) PDCA_TRY(cudaEventRecord(b, h->stream));
+    return PDCA_OK;
+}
+
+pdca_status sweep(pdca_problem *h, bool project, const float *src, const float *ut, float *dst) {
+    return timed_pass(h, [&] { return launch_sweep(h->L.K, project, h->view(), h->tiles(), h->cf, src, ut, dst, h->stream); });
+}
+
+// Mixed-precision outer step: pass 0 forms r = b^t - T u^t and e^1 in FP32,
+// the following passes update the 16-bit correction, the last one writes
+// u^{t+1} = u^t + e^m in FP32 (projected for K >= 2).
+pdca_status outer_step_mixed(pdca_problem *h, int32_t inner) {
+    const int K = h->L.K;
+    const SellView A = h->view();
+    const int dst = (h->cur + 1) % 3;
+    const float *u = h->U[h->cur];
+    float *u_out = h->U[dst];
+    const bool proj = K >= 2;
+    pdca_status st = timed_pass(h, [&] {
+        return launch_mixed_residual(K, h->bf16u, inner == 1, proj, A, h->cf, u, h->mr, h->me[0], u_out, h->stream);
+    });
+    if (st != PDCA_OK) return st;
+    for (int32_t s = 1; s < inner; ++s) {
+        const bool last = s == inner - 1;
+        void *src = h->me[(s - 1) % 2], *dstb = h->me[s % 2];
+        st = timed_pass(h, [&] {
+            return launch_mixed_sweep(K, h->bf16u, last, proj, A, h->cf, src, h->mr, dstb, u, u_out, h->stream);
+        });
+        if (st != PDCA_OK) return st;
+    }
+    h->prev = h->cur;
+    h->cur = dst;
+    h->has_prev = true;
     return PDCA_OK;
 }
 
 // One outer step (Prop. nopre): sweeps ping-pong between the two buffers
 // that do not hold u^t; the last one projects rows for K >= 2.
 pdca_status outer_step(pdca_problem *h, int32_t inner) {
+    if (h->mixed) return outer_step_mixed(h, inner);
     const int a = (h->cur + 1) % 3, b = (h->cur + 2) % 3;
     const float *ut = h->U[h->cur];
     const float *src = ut;
@@ -537,6 +582,11 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     h->perm = reinterpret_cast<int32_t *>(W + L.o_perm);
     h->iperm = reinterpret_cast<int32_t *>(W + L.o_iperm);
     for (int b = 0; b < 3; ++b) h->U[b] = reinterpret_cast<float *>(W + L.o_u[b]);
+    h->mixed = prm.precision != PDCA_FP32;
+    h->bf16u = prm.precision == PDCA_MIXED_BF16W_BF16U;
+    h->mr = W + L.o_mr;
+    h->me[0] = W + L.o_me[0];
+    h->me[1] = W + L.o_me[1];
     h->partials = reinterpret_cast<double *>(W + L.o_part);
     h->red = reinterpret_cast<RedOut *>(W + L.o_red);
     h->scal = reinterpret_cast<double *>(W + L.o_scal);
@@ -583,7 +633,9 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
                                h->rowinfo, s_status, sm);
     else
         pe = launch_pack(n, L.n_pad, k, s_rp, s_col, s_w, s_deg, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
-                         h->sell_col, h->sell_w, h->rowinfo, s_status, sm);
+                         h->sell_col, h->mixed ? nullptr : h->sell_w,
+                         h->mixed ? reinterpret_cast<__nv_bfloat16 *>(h->sell_w) : nullptr, h->rowinfo, s_status,
+                         sm);
     if (pe != cudaSuccess) return fail(PDCA_ERR_CUDA);
     if (prm.precond == PDCA_RICHARDSON) {
         if (prm.lambda_max > 0) {

@@ -17,6 +17,7 @@
 //   * u is n_pad x K float32 row-major (n_pad = 32 * number of slices).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,7 +42,8 @@ constexpr uint32_t kLayoutMismatch = 8u;   // internal: packed row longer than i
 
 struct SellView {
     const int32_t *col;        // padded sliced-ELL column indices (new numbering)
-    const float *w;            // w_ij / sqrt(d_i d_j), FP32
+    const float *w;            // w_ij / sqrt(d_i d_j), FP32 (FP32 path)
+    const __nv_bfloat16 *wb;   // the same in BF16 (mixed-precision path)
     const int64_t *slice_off;  // n_slices + 1 entry offsets
     const uint32_t *rowinfo;   // (len << 8) | tag, n_pad
     int32_t n_slices;
@@ -113,6 +115,15 @@ cudaError_t launch_power_finalize(const double *partials, int n_parts, double *s
                                   double *lambda, cudaStream_t st);
 cudaError_t launch_labels(int K, int32_t n, const float *u, const int32_t *perm,
                           int32_t *out, cudaStream_t st);
+
+// --- mixed precision (mixed_kernels.cu) --------------------------------------
+// r and e are n_pad x K arrays of FP16 (bf16u = false) or BF16 (bf16u = true).
+cudaError_t launch_mixed_residual(int K, bool bf16u, bool last, bool project, const SellView &A,
+                                  const Coeffs &cf, const float *u, void *r, void *e, float *u_out,
+                                  cudaStream_t st);
+cudaError_t launch_mixed_sweep(int K, bool bf16u, bool last, bool project, const SellView &A, const Coeffs &cf,
+                               const void *e_src, const void *r, void *e_dst, const float *u, float *u_out,
+                               cudaStream_t st);
 cudaError_t launch_permute_out(int K, int32_t n, const float *u, const int32_t *perm,
                                float *out, cudaStream_t st);
 cudaError_t launch_permute_in(int K, int32_t n, int32_t n_pad, const float *in,
@@ -129,7 +140,8 @@ cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_
                         const int32_t *col, const float *w, const double *deg,
                         const uint8_t *mask, const int32_t *labels, const int32_t *perm,
                         const int32_t *iperm, const int64_t *slice_off, int32_t *sell_col,
-                        float *sell_w, uint32_t *rowinfo, uint32_t *status, cudaStream_t st);
+                        float *sell_w, __nv_bfloat16 *sell_wb, uint32_t *rowinfo, uint32_t *status,
+                        cudaStream_t st);
 // tiled form: local 16-bit columns (position in the tile's halo) instead of int32
 cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32_t *col, const float *w,
                               const double *deg, const uint8_t *mask, const int32_t *labels,

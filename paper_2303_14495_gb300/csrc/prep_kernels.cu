@@ -7,6 +7,7 @@
 //   init_u_kernel       u^0 (prior on labelled rows, centre elsewhere).
 #include "pdca_internal.cuh"
 
+#include <cuda_bf16.h>
 #include <math.h>
 
 namespace pdca {
@@ -114,7 +115,8 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
                             const int32_t *__restrict__ labels, const int32_t *__restrict__ perm,
                             const int32_t *__restrict__ iperm, const int64_t *__restrict__ slice_off,
                             int32_t *__restrict__ sell_col, float *__restrict__ sell_w,
-                            uint32_t *__restrict__ rowinfo, uint32_t *__restrict__ status) {
+                            __nv_bfloat16 *__restrict__ sell_wb, uint32_t *__restrict__ rowinfo,
+                            uint32_t *__restrict__ status) {
     const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_pad) return;
     const int32_t s = r >> 5, lane = r & 31;
@@ -135,14 +137,17 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
             const int32_t oj = col[e0 + j];
             const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
             sell_col[at] = iperm[oj];
-            sell_w[at] = (float)((double)w[e0 + j] / sqrt(di * deg[oj]));
+            const double wt = (double)w[e0 + j] / sqrt(di * deg[oj]);
+            if (sell_wb) sell_wb[at] = __double2bfloat16(wt);
+            else sell_w[at] = (float)wt;
         }
         if (mask[old]) tag = (uint32_t)labels[old];
     }
     for (int32_t j = len; j < width; ++j) {
         const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
         sell_col[at] = r;
-        sell_w[at] = 0.0f;
+        if (sell_wb) sell_wb[at] = __float2bfloat16(0.0f);
+        else sell_w[at] = 0.0f;
     }
     rowinfo[r] = ((uint32_t)len << 8) | tag;
 }
@@ -248,13 +253,14 @@ cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const in
 cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_ptr, const int32_t *col,
                         const float *w, const double *deg, const uint8_t *mask, const int32_t *labels,
                         const int32_t *perm, const int32_t *iperm, const int64_t *slice_off,
-                        int32_t *sell_col, float *sell_w, uint32_t *rowinfo, uint32_t *status,
-                        cudaStream_t st) {
+                        int32_t *sell_col, float *sell_w, __nv_bfloat16 *sell_wb, uint32_t *rowinfo,
+                        uint32_t *status, cudaStream_t st) {
     (void)n;
     (void)K;
     count_launches(1);
     pack_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, mask, labels, perm,
-                                                     iperm, slice_off, sell_col, sell_w, rowinfo, status);
+                                                     iperm, slice_off, sell_col, sell_w, sell_wb, rowinfo,
+                                                     status);
     return cudaGetLastError();
 }
 

@@ -16,294 +16,14 @@
 // tile of 32 slices and first copies the tile's halo rows (the distinct rows
 // its entries reference) into shared memory, so every gather is a shared
 // memory load addressed by a 16-bit local column.
-#include "pdca_internal.cuh"
+#include "device_common.cuh"
 
 #include <math.h>
 
 namespace pdca {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-// ---------------------------------------------------------------------------
-// row I/O: K floats per row, widest aligned vector access
-// ---------------------------------------------------------------------------
-template <int K>
-__device__ __forceinline__ void load_row(const float *__restrict__ p, float (&x)[K]) {
-    if constexpr (K % 4 == 0) {
-#pragma unroll
-        for (int q = 0; q < K / 4; ++q) {
-            const float4 t = __ldg(reinterpret_cast<const float4 *>(p) + q);
-            x[4 * q + 0] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
-        }
-    } else if constexpr (K % 2 == 0) {
-#pragma unroll
-        for (int q = 0; q < K / 2; ++q) {
-            const float2 t = __ldg(reinterpret_cast<const float2 *>(p) + q);
-            x[2 * q + 0] = t.x; x[2 * q + 1] = t.y;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < K; ++q) x[q] = __ldg(p + q);
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void store_row(float *__restrict__ p, const float (&x)[K]) {
-    if constexpr (K % 4 == 0) {
-#pragma unroll
-        for (int q = 0; q < K / 4; ++q)
-            reinterpret_cast<float4 *>(p)[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-    } else if constexpr (K % 2 == 0) {
-#pragma unroll
-        for (int q = 0; q < K / 2; ++q)
-            reinterpret_cast<float2 *>(p)[q] = make_float2(x[2 * q], x[2 * q + 1]);
-    } else {
-#pragma unroll
-        for (int q = 0; q < K; ++q) p[q] = x[q];
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void load_row_smem(const float *p, float (&x)[K]) {
-    if constexpr (K % 4 == 0) {
-#pragma unroll
-        for (int q = 0; q < K / 4; ++q) {
-            const float4 t = reinterpret_cast<const float4 *>(p)[q];
-            x[4 * q + 0] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
-        }
-    } else if constexpr (K % 2 == 0) {
-#pragma unroll
-        for (int q = 0; q < K / 2; ++q) {
-            const float2 t = reinterpret_cast<const float2 *>(p)[q];
-            x[2 * q + 0] = t.x; x[2 * q + 1] = t.y;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < K; ++q) x[q] = p[q];
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void store_row_smem(float *p, const float (&x)[K]) {
-    if constexpr (K % 4 == 0) {
-#pragma unroll
-        for (int q = 0; q < K / 4; ++q)
-            reinterpret_cast<float4 *>(p)[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-    } else if constexpr (K % 2 == 0) {
-#pragma unroll
-        for (int q = 0; q < K / 2; ++q) reinterpret_cast<float2 *>(p)[q] = make_float2(x[2 * q], x[2 * q + 1]);
-    } else {
-#pragma unroll
-        for (int q = 0; q < K; ++q) p[q] = x[q];
-    }
-}
-
-// acc[k] = sum_j wt_ij * x_jk over the lane's row of the slice (padding
-// entries carry weight 0 and point at a valid row).  `len` is the lane's own
-// row length: the lane reads only its ceil(len / kVec) groups (kVec
-// consecutive entries per 128-bit load, two groups per iteration), so the
-// slice padding beyond a row's end is never fetched.  Plain form: global columns, rows gathered from global
-// memory through L1/L2.
-template <int K>
-__device__ __forceinline__ void fma_row(float (&acc)[K], float w, const float (&x)[K]) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = fmaf(w, x[k], acc[k]);
-}
-
-template <int K>
-__device__ __forceinline__ void gather_row_sum(const SellView &A, int64_t base, int len, int lane,
-                                               const float *__restrict__ x, float (&acc)[K]) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = 0.0f;
-    const int4 *__restrict__ cp = reinterpret_cast<const int4 *>(A.col + base) + lane;
-    const float4 *__restrict__ wp = reinterpret_cast<const float4 *>(A.w + base) + lane;
-    const int groups = (len + kVec - 1) / kVec;   // this lane's groups only
-    int g = 0;
-    for (; g + 2 <= groups; g += 2) {
-        const int4 ca = __ldcs(cp + 32 * g), cb = __ldcs(cp + 32 * (g + 1));
-        const float4 wa = __ldcs(wp + 32 * g), wb = __ldcs(wp + 32 * (g + 1));
-        float x0[K], x1[K], x2[K], x3[K];
-        load_row<K>(x + (size_t)ca.x * K, x0);
-        load_row<K>(x + (size_t)ca.y * K, x1);
-        load_row<K>(x + (size_t)ca.z * K, x2);
-        load_row<K>(x + (size_t)ca.w * K, x3);
-        fma_row<K>(acc, wa.x, x0); fma_row<K>(acc, wa.y, x1);
-        fma_row<K>(acc, wa.z, x2); fma_row<K>(acc, wa.w, x3);
-        load_row<K>(x + (size_t)cb.x * K, x0);
-        load_row<K>(x + (size_t)cb.y * K, x1);
-        load_row<K>(x + (size_t)cb.z * K, x2);
-        load_row<K>(x + (size_t)cb.w * K, x3);
-        fma_row<K>(acc, wb.x, x0); fma_row<K>(acc, wb.y, x1);
-        fma_row<K>(acc, wb.z, x2); fma_row<K>(acc, wb.w, x3);
-    }
-    if (g < groups) {
-        const int4 ca = __ldcs(cp + 32 * g);
-        const float4 wa = __ldcs(wp + 32 * g);
-        float x0[K], x1[K], x2[K], x3[K];
-        load_row<K>(x + (size_t)ca.x * K, x0);
-        load_row<K>(x + (size_t)ca.y * K, x1);
-        load_row<K>(x + (size_t)ca.z * K, x2);
-        load_row<K>(x + (size_t)ca.w * K, x3);
-        fma_row<K>(acc, wa.x, x0); fma_row<K>(acc, wa.y, x1);
-        fma_row<K>(acc, wa.z, x2); fma_row<K>(acc, wa.w, x3);
-    }
-}
-
-// Tiled form: 16-bit local columns (four per 64-bit load) into the halo rows
-// held in shared memory.
-template <int K>
-__device__ __forceinline__ void gather_row_sum_smem(const TileView &T, const SellView &A, int64_t base,
-                                                    int len, int lane, const float *hs, float (&acc)[K]) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = 0.0f;
-    const uint2 *__restrict__ cp = reinterpret_cast<const uint2 *>(T.lcol + base) + lane;
-    const float4 *__restrict__ wp = reinterpret_cast<const float4 *>(A.w + base) + lane;
-    const int groups = (len + kVec - 1) / kVec;
-    int g = 0;
-    for (; g + 2 <= groups; g += 2) {
-        const uint2 ca = __ldcs(cp + 32 * g), cb = __ldcs(cp + 32 * (g + 1));
-        const float4 wa = __ldcs(wp + 32 * g), wb = __ldcs(wp + 32 * (g + 1));
-        float x0[K], x1[K], x2[K], x3[K];
-        load_row_smem<K>(hs + (ca.x & 0xFFFFu) * K, x0);
-        load_row_smem<K>(hs + (ca.x >> 16) * K, x1);
-        load_row_smem<K>(hs + (ca.y & 0xFFFFu) * K, x2);
-        load_row_smem<K>(hs + (ca.y >> 16) * K, x3);
-        fma_row<K>(acc, wa.x, x0); fma_row<K>(acc, wa.y, x1);
-        fma_row<K>(acc, wa.z, x2); fma_row<K>(acc, wa.w, x3);
-        load_row_smem<K>(hs + (cb.x & 0xFFFFu) * K, x0);
-        load_row_smem<K>(hs + (cb.x >> 16) * K, x1);
-        load_row_smem<K>(hs + (cb.y & 0xFFFFu) * K, x2);
-        load_row_smem<K>(hs + (cb.y >> 16) * K, x3);
-        fma_row<K>(acc, wb.x, x0); fma_row<K>(acc, wb.y, x1);
-        fma_row<K>(acc, wb.z, x2); fma_row<K>(acc, wb.w, x3);
-    }
-    if (g < groups) {
-        const uint2 ca = __ldcs(cp + 32 * g);
-        const float4 wa = __ldcs(wp + 32 * g);
-        float x0[K], x1[K], x2[K], x3[K];
-        load_row_smem<K>(hs + (ca.x & 0xFFFFu) * K, x0);
-        load_row_smem<K>(hs + (ca.x >> 16) * K, x1);
-        load_row_smem<K>(hs + (ca.y & 0xFFFFu) * K, x2);
-        load_row_smem<K>(hs + (ca.y >> 16) * K, x3);
-        fma_row<K>(acc, wa.x, x0); fma_row<K>(acc, wa.y, x1);
-        fma_row<K>(acc, wa.z, x2); fma_row<K>(acc, wa.w, x3);
-    }
-}
-
-// Tiled form for a tile whose halo exceeds the shared-memory allocation: the
-// local column indexes the tile's halo list, which gives the global row.
-template <int K>
-__device__ __forceinline__ void gather_row_sum_indirect(const TileView &T, const SellView &A, int64_t base,
-                                                        int len, int lane, const int32_t *__restrict__ hidx,
-                                                        const float *__restrict__ x, float (&acc)[K]) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = 0.0f;
-    const uint2 *__restrict__ cp = reinterpret_cast<const uint2 *>(T.lcol + base) + lane;
-    const float4 *__restrict__ wp = reinterpret_cast<const float4 *>(A.w + base) + lane;
-    const int groups = (len + kVec - 1) / kVec;
-    for (int g = 0; g < groups; ++g) {
-        const uint2 ca = __ldcs(cp + 32 * g);
-        const float4 wa = __ldcs(wp + 32 * g);
-        float x0[K], x1[K], x2[K], x3[K];
-        load_row<K>(x + (size_t)__ldg(hidx + (ca.x & 0xFFFFu)) * K, x0);
-        load_row<K>(x + (size_t)__ldg(hidx + (ca.x >> 16)) * K, x1);
-        load_row<K>(x + (size_t)__ldg(hidx + (ca.y & 0xFFFFu)) * K, x2);
-        load_row<K>(x + (size_t)__ldg(hidx + (ca.y >> 16)) * K, x3);
-        fma_row<K>(acc, wa.x, x0); fma_row<K>(acc, wa.y, x1);
-        fma_row<K>(acc, wa.z, x2); fma_row<K>(acc, wa.w, x3);
-    }
-}
-
-// Gather for one row of a tile: from shared memory when the tile's halo is
-// staged there, through the halo list otherwise.
-template <int K>
-__device__ __forceinline__ void tile_row_sum(const TileView &T, const SellView &A, int64_t base, int len,
-                                             int lane, bool staged, const int32_t *__restrict__ hidx,
-                                             const float *hs, const float *__restrict__ x, float (&acc)[K]) {
-    if (staged) gather_row_sum_smem<K>(T, A, base, len, lane, hs, acc);
-    else gather_row_sum_indirect<K>(T, A, base, len, lane, hidx, x, acc);
-}
-
-// Copy the tile's halo rows of x into shared memory (rows in halo order).
-// Batches of four rows per thread: the four index loads, then the four row
-// loads, then the four shared-memory stores, so a batch costs one index and
-// one row latency whatever the halo size.
-template <int K>
-__device__ __forceinline__ void load_halo(const TileView &T, int tile, const float *__restrict__ x, float *hs) {
-    const int64_t h0 = T.halo_off[tile];
-    const int h = (int)(T.halo_off[tile + 1] - h0);
-    const int32_t *__restrict__ idx = T.halo_idx + h0;
-    const int bd = blockDim.x;
-    for (int q0 = threadIdx.x; q0 < h; q0 += 4 * bd) {
-        int32_t i[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) i[m] = (q0 + m * bd < h) ? __ldcs(idx + q0 + m * bd) : -1;
-        float r[4][K];
-#pragma unroll
-        for (int m = 0; m < 4; ++m)
-            if (i[m] >= 0) load_row<K>(x + (size_t)i[m] * K, r[m]);
-#pragma unroll
-        for (int m = 0; m < 4; ++m)
-            if (i[m] >= 0) store_row_smem<K>(hs + (q0 + m * bd) * K, r[m]);
-    }
-}
-
-__device__ __forceinline__ int row_len(const SellView &A, int slice, int lane) {
-    return (int)(__ldg(A.rowinfo + slice * kSliceRows + lane) >> 8);
-}
-
-// prior y_ik in the +-1 coding from the row tag
-template <int K>
-__device__ __forceinline__ float prior_of(uint32_t tag, int k) {
-    if (K == 1) return tag == 1u ? 1.0f : -1.0f;
-    return tag == (uint32_t)k ? 1.0f : -1.0f;
-}
-
-// Euclidean projection of a row onto the simplex in the coding v = (u+1)/2
-// (sort-and-threshold method of Held, Wolfe and Crowder), written directly in
-// u: with u sorted descending and S_j = sum_{i<=j} u_(i), rho is the largest
-// j with j u_(j) - S_j + 2 > 0, lambda = (S_rho + rho - 2)/rho (twice the
-// threshold theta of the v coding) and u' = max(u - lambda, -1).
-// The threshold sums S_j are kept as an unevaluated pair hi + lo of floats
-// (Knuth's TwoSum), about 48 significant bits, so no FP64 unit is needed.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bp = s - a;
-    e = (a - (s - bp)) + (b - bp);
-}
-
-template <int K>
-__device__ __forceinline__ void project_simplex(float (&u)[K]) {
-    float mu[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) mu[k] = u[k];
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-#pragma unroll
-        for (int j = 0; j + 1 < K - i; ++j) {
-            const float a = mu[j], b = mu[j + 1];
-            mu[j] = fmaxf(a, b);
-            mu[j + 1] = fminf(a, b);
-        }
-    }
-    float hi = 0.0f, lo = 0.0f, s_hi = mu[0], s_lo = 0.0f;
-    int rho = 1;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        float e;
-        two_sum(hi, mu[j], hi, e);
-        lo += e;
-        if (((float)(j + 1) * mu[j] - hi) - lo + 2.0f > 0.0f) {
-            rho = j + 1;
-            s_hi = hi;
-            s_lo = lo;
-        }
-    }
-    const float lam = (((s_hi - 2.0f) + (float)rho) + s_lo) / (float)rho;
-#pragma unroll
-    for (int k = 0; k < K; ++k) u[k] = fmaxf(u[k] - lam, -1.0f);
-}
+using namespace dev;
 
 // ---------------------------------------------------------------------------
 // fused sweep
@@ -483,33 +203,6 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Sum S values over the block (WARPS warps) in a fixed order and store them
-// at out[0..S): each warp sums its 32 lanes in FP32 (fixed shuffle tree),
-// the warp totals are summed in FP64.
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-template <int S, int WARPS = kWarpsPerBlock>
-__device__ __forceinline__ void block_sum_store(float (&v)[S], double *__restrict__ out) {
-    __shared__ double sm[WARPS][S];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const float t = warp_sum_f(v[s]);
-        if (lane == 0) sm[warp][s] = (double)t;
-    }
-    __syncthreads();
-    if (threadIdx.x < S) {
-        double t = 0.0;
-#pragma unroll
-        for (int q = 0; q < WARPS; ++q) t += sm[q][threadIdx.x];
-        out[threadIdx.x] = t;
-    }
-}
-
 // Per-row contributions (FP32 inside a row and a warp, FP64 across warps):
 //   quad += u_i . (L_s u)_i,  well += sum_k (u_ik^2 - 1)^2,
 //   fid  += Lambda_i sum_k (u_ik - y_ik)^2,
@@ -552,7 +245,7 @@ __device__ __forceinline__ void energy_row(const SellView &A, const Coeffs &cf, 
     red[0] += q; red[1] += wl; red[2] += fd; red[3] += rr; red[4] += bb; red[5] += nf;
 }
 
-template <int K>
+template <int K, class WT>
 __global__ void __launch_bounds__(kBlockThreads)
 energy_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u,
               const float *__restrict__ u_prev, double *__restrict__ partials) {
@@ -562,7 +255,7 @@ energy_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u,
     if (slice < A.n_slices) {
         const int64_t base = A.slice_off[slice];
         float acc[K];
-        gather_row_sum<K>(A, base, row_len(A, slice, lane), lane, u, acc);
+        gather_row_sum<K, WT, float>(A, base, row_len(A, slice, lane), lane, u, acc);
         energy_row<K>(A, cf, slice, lane, acc, u, u_prev, red);
     }
     block_sum_store<6>(red, partials + (size_t)blockIdx.x * kRedSlots);
@@ -656,6 +349,7 @@ __device__ __forceinline__ void power_row(const SellView &A, int slice, int lane
     }
 }
 
+template <class WT>
 __global__ void __launch_bounds__(kBlockThreads)
 power_spmv_kernel(const SellView A, const float *__restrict__ x, const double *__restrict__ scale,
                   float *__restrict__ y, double *__restrict__ partials) {
@@ -665,7 +359,7 @@ power_spmv_kernel(const SellView A, const float *__restrict__ x, const double *_
     if (slice < A.n_slices) {
         const int64_t base = A.slice_off[slice];
         float acc[1];
-        gather_row_sum<1>(A, base, row_len(A, slice, lane), lane, x, acc);
+        gather_row_sum<1, WT, float>(A, base, row_len(A, slice, lane), lane, x, acc);
         power_row(A, slice, lane, acc[0], (float)(*scale), x, y, red);
     }
     block_sum_store<3>(red, partials + (size_t)blockIdx.x * kRedSlots);
@@ -805,7 +499,11 @@ cudaError_t energy_k(const SellView &A, const TileView *T, const Coeffs &cf, con
         if (e != cudaSuccess) return e;
         energy_tiled_kernel<K><<<T->n_tiles, kTileThreads, sm, st>>>(A, *T, cf, u, u_prev, partials);
     } else {
-        energy_kernel<K><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, cf, u, u_prev, partials);
+        if (A.wb)
+            energy_kernel<K, __nv_bfloat16><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, cf, u, u_prev,
+                                                                                                  partials);
+        else
+            energy_kernel<K, float><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, cf, u, u_prev, partials);
     }
     return cudaGetLastError();
 }
@@ -876,7 +574,11 @@ cudaError_t launch_power_spmv(const SellView &A, const TileView *T, const float 
         if (e != cudaSuccess) return e;
         power_spmv_tiled_kernel<<<T->n_tiles, kTileThreads, sm, st>>>(A, *T, x, scale, y, partials);
     } else {
-        power_spmv_kernel<<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, x, scale, y, partials);
+        if (A.wb)
+            power_spmv_kernel<__nv_bfloat16><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, x, scale, y,
+                                                                                                partials);
+        else
+            power_spmv_kernel<float><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, x, scale, y, partials);
     }
     return cudaGetLastError();
 }
