@@ -182,6 +182,20 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
                         const pdca_params *p, void *workspace, size_t ws_bytes,
                         void *stream, pdca_problem **out);
 
+/* A new problem on the graph of `base`: it borrows base's operator (the
+ * renumbering, the sliced-ELL pre-scaled weights and, for Richardson with
+ * lambda_max = 0, base's power-method estimate) read-only and owns only its
+ * per-problem state (row tags, iterates, reductions) in `workspace`.  K,
+ * fidelity data and the model parameters may differ from base's; the
+ * precision must be of base's family (FP32, or one of the mixed forms, which
+ * share the BF16 weights).  Arguments as for pdca_create; the new problem
+ * runs on base's stream.  `base` must outlive the new problem.  This is how a
+ * server keeps one prepared operator per graph resident while requests with
+ * different labels come and go (the paper solves one problem per graph). */
+pdca_status pdca_workspace_size_like(const pdca_problem *base, int32_t k, const pdca_params *p, size_t *bytes);
+pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t *fid_mask, const int32_t *labels,
+                             const pdca_params *p, void *workspace, size_t ws_bytes, pdca_problem **out);
+
 /* Replace the iterate: u (n x K row-major float32, host or device), or NULL
  * to restore u^0.  Clears the record of the last outer step. */
 pdca_status pdca_set_u(pdca_problem *h, const float *u);
@@ -261,6 +275,34 @@ pdca_status pdca_energy_static(const int64_t *row_ptr, const int32_t *col, const
                                int32_t n, int64_t nnz, int32_t k, const float *u,
                                const uint8_t *fid_mask, const int32_t *labels, double eps,
                                double eta, void *stream, double *F_out);
+
+/* ---- batches: many problems advanced together (continuous batching) ------
+ * A batch holds problems that were created on the batch's stream (plain
+ * kernels: not PDCA_TILING_ON).  pdca_batch_step advances every member by up
+ * to `passes` passes (one pass = one sweep of the FP32 form, or one pass of
+ * the mixed form), with one kernel launch per K class per pass: all members
+ * of a class share the launch, whatever their sizes, precisions and
+ * positions inside their outer steps.  A member leaves the batch after its
+ * `outer_iters` outer steps of `inner_sweeps` sweeps; pdca_batch_poll hands
+ * finished problems back.  Members may join between steps (continuous
+ * batching).  A member's iterates are bit-identical to those of pdca_solve
+ * with the same arguments: the batched kernel runs the same per-row code.
+ * The paper solves one problem at a time; batching is a serving extension.
+ * A batch allocates host memory only.  While a problem is a member, use it
+ * only through the batch (its u is mid-step between passes). */
+typedef struct pdca_batch pdca_batch;
+pdca_status pdca_batch_create(int32_t max_problems, void *stream, pdca_batch **out);
+/* INVALID_ARG for a problem on another stream, a tiled problem, a problem
+ * already in the batch, a full batch, or outer_iters / inner_sweeps < 1. */
+pdca_status pdca_batch_add(pdca_batch *b, pdca_problem *h, int32_t outer_iters, int32_t inner_sweeps);
+/* Asynchronous; active_after (nullable) receives the members still running. */
+pdca_status pdca_batch_step(pdca_batch *b, int32_t passes, int32_t *active_after);
+/* Up to `capacity` finished problems into done[] (count written); removes them. */
+pdca_status pdca_batch_poll(pdca_batch *b, pdca_problem **done, int32_t capacity, int32_t *count);
+/* Remove a problem (running or finished) without finishing it. */
+pdca_status pdca_batch_remove(pdca_batch *b, pdca_problem *h);
+/* Synchronises the stream; the member problems stay the caller's. */
+void pdca_batch_destroy(pdca_batch *b);
 
 /* Release the handle's host-side state (the workspace stays the caller's).
  * Synchronises the handle's stream first.  NULL is ignored. */

@@ -43,6 +43,8 @@ EXPORTS = [
     "pdca_solve", "pdca_energy", "pdca_get_u", "pdca_labels", "pdca_lambda_max", "pdca_layout",
     "pdca_profile_enable", "pdca_profile_read", "pdca_kernel_launches", "pdca_destroy",
     "pdca_status_string", "pdca_energy_static",
+    "pdca_batch_create", "pdca_batch_add", "pdca_batch_step", "pdca_batch_poll", "pdca_batch_remove",
+    "pdca_batch_destroy", "pdca_workspace_size_like", "pdca_create_like",
 ]
 
 
@@ -98,6 +100,14 @@ def lib():
                 "pdca_status_string": (C.c_char_p, [C.c_int]),
                 "pdca_energy_static": (C.c_int, [vp, vp, vp, i32, i64, i32, vp, vp, vp, dbl, dbl,
                                                  vp, C.POINTER(dbl)]),
+                "pdca_batch_create": (C.c_int, [i32, vp, C.POINTER(vp)]),
+                "pdca_batch_add": (C.c_int, [vp, vp, i32, i32]),
+                "pdca_batch_step": (C.c_int, [vp, i32, C.POINTER(i32)]),
+                "pdca_batch_poll": (C.c_int, [vp, C.POINTER(vp), i32, C.POINTER(i32)]),
+                "pdca_batch_remove": (C.c_int, [vp, vp]),
+                "pdca_batch_destroy": (None, [vp]),
+                "pdca_workspace_size_like": (C.c_int, [vp, i32, P, C.POINTER(C.c_size_t)]),
+                "pdca_create_like": (C.c_int, [vp, i32, vp, vp, P, vp, C.c_size_t, C.POINTER(vp)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -152,6 +162,13 @@ def pdca_workspace_size(row_ptr, n: int, k: int, params: Optional[pdca_params] =
     st = lib().pdca_workspace_size(_ptr(row_ptr), int(n), int(k),
                                    C.byref(params) if params is not None else None, C.byref(out))
     _check(st, "pdca_workspace_size")
+    return int(out.value)
+
+
+def workspace_size_like(base: "Problem", k: int, params: pdca_params) -> int:
+    out = C.c_size_t(0)
+    _check(lib().pdca_workspace_size_like(base.h, int(k), C.byref(params), C.byref(out)),
+           "pdca_workspace_size_like")
     return int(out.value)
 
 
@@ -262,6 +279,27 @@ class Problem:
         _check(st, "pdca_create")
         self.h = h
 
+    @classmethod
+    def like(cls, base: "Problem", K, fid_mask, fid_labels, params: pdca_params):
+        """A problem on base's graph (shared, read-only operator); see pdca_create_like."""
+        import torch
+        self = cls.__new__(cls)
+        self.torch = torch
+        self.n, self.K = base.n, int(K)
+        self.device, self.stream = base.device, base.stream
+        self._base = base                      # keeps the shared operator alive
+        self._keep = (fid_mask, fid_labels)
+        out = C.c_size_t(0)
+        _check(lib().pdca_workspace_size_like(base.h, self.K, C.byref(params), C.byref(out)),
+               "pdca_workspace_size_like")
+        self.ws_bytes = int(out.value)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        _check(lib().pdca_create_like(base.h, self.K, _ptr(fid_mask), _ptr(fid_labels), C.byref(params),
+                                      _ptr(self.workspace), self.ws_bytes, C.byref(h)), "pdca_create_like")
+        self.h = h
+        return self
+
     def close(self):
         if getattr(self, "h", None):
             pdca_destroy(self.h)
@@ -323,6 +361,52 @@ class Problem:
         st, ms, cnt = pdca_profile_read(self.h)
         _check(st, "pdca_profile_read")
         return ms, cnt
+
+
+class Batch:
+    """Continuous batch of problems advanced together (pdca_batch_*).
+
+    Problems must live on the batch's stream.  ``add`` a Problem with its
+    outer / inner counts, ``step`` passes, ``poll`` the finished Problems."""
+
+    def __init__(self, max_problems: int = 1024, stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib().pdca_batch_create(int(max_problems), C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+               "pdca_batch_create")
+        self.h = h
+        self._by_handle = {}
+
+    def add(self, prob: "Problem", outer: int, inner: int):
+        _check(lib().pdca_batch_add(self.h, prob.h, int(outer), int(inner)), "pdca_batch_add")
+        self._by_handle[prob.h.value] = prob
+
+    def step(self, passes: int) -> int:
+        active = C.c_int32(0)
+        _check(lib().pdca_batch_step(self.h, int(passes), C.byref(active)), "pdca_batch_step")
+        return int(active.value)
+
+    def poll(self, capacity: int = 4096):
+        arr = (C.c_void_p * max(capacity, 1))()
+        cnt = C.c_int32(0)
+        _check(lib().pdca_batch_poll(self.h, arr, int(capacity), C.byref(cnt)), "pdca_batch_poll")
+        return [self._by_handle.pop(arr[i]) for i in range(cnt.value)]
+
+    def remove(self, prob: "Problem"):
+        _check(lib().pdca_batch_remove(self.h, prob.h), "pdca_batch_remove")
+        self._by_handle.pop(prob.h.value, None)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pdca_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def params_from_workload(p: dict, **over) -> pdca_params:

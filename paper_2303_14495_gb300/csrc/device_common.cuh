@@ -417,5 +417,120 @@ __device__ __forceinline__ void block_sum_store(float (&v)[S], double *__restric
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// One pass over one slice (lane = row), shared by the single-problem kernels
+// and the batched kernel.
+// ---------------------------------------------------------------------------
+template <int K, bool PROJECT>
+__device__ __forceinline__ void sweep_update(const Coeffs &cf, uint32_t info, const float (&acc)[K],
+                                             const float (&v)[K], const float (&u)[K], float *__restrict__ dst) {
+    const uint32_t tag = info & 0xFFu;
+    const bool lab = tag != kTagUnlabelled;
+    const float inv_g = lab ? cf.inv_g1 : cf.inv_g0;
+    const float diag = cf.c + (lab ? cf.eta : 0.0f);
+    float out[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float fid = lab ? cf.eta * prior_of<K>(tag, k) : 0.0f;
+        const float uk = u[k];
+        const float b = fid + cf.c * uk - (uk * uk * uk - uk) * cf.inv_eps;
+        const float tv = cf.eps * (v[k] - acc[k]) + diag * v[k];
+        out[k] = v[k] + (b - tv) * inv_g;
+    }
+    if constexpr (PROJECT) project_simplex<K>(out);
+    store_row<K>(dst, out);
+}
+
+// FP32 sweep of one slice (plain gathers).
+template <int K, bool PROJECT>
+__device__ __forceinline__ void fp32_sweep_slice(const SellView &A, const Coeffs &cf, int slice, int lane,
+                                                 const float *__restrict__ v_src, const float *__restrict__ u_t,
+                                                 float *__restrict__ v_dst) {
+    const int r = slice * kSliceRows + lane;
+    const uint32_t info = __ldg(A.rowinfo + r);
+    float acc[K];
+    gather_row_sum<K, float, float>(A, A.slice_off[slice], (int)(info >> 8), lane, v_src, acc);
+    float v[K], u[K];
+    load_row<K>(v_src + (size_t)r * K, v);
+    if (u_t == v_src) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) u[k] = v[k];
+    } else {
+        load_row<K>(u_t + (size_t)r * K, u);
+    }
+    sweep_update<K, PROJECT>(cf, info, acc, v, u, v_dst + (size_t)r * K);
+}
+
+// Mixed precision, pass 0 of an outer step: r = b^t - T u^t and e^1 = G^-1 r
+// (or, with a single sweep, u^{t+1} = u^t + e^1).
+template <int K, class HT, bool LAST, bool PROJECT>
+__device__ __forceinline__ void mixed_residual_slice(const SellView &A, const Coeffs &cf, int slice, int lane,
+                                                     const float *__restrict__ u, HT *__restrict__ r_out,
+                                                     HT *__restrict__ e_out, float *__restrict__ u_out) {
+    const int r = slice * kSliceRows + lane;
+    const uint32_t info = __ldg(A.rowinfo + r);
+    float acc[K];
+    gather_row_sum<K, __nv_bfloat16, float>(A, A.slice_off[slice], (int)(info >> 8), lane, u, acc);
+    float x[K];
+    load_row<K>(u + (size_t)r * K, x);
+    const uint32_t tag = info & 0xFFu;
+    const bool lab = tag != kTagUnlabelled;
+    const float inv_g = lab ? cf.inv_g1 : cf.inv_g0;
+    float res[K], e[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float fid = lab ? cf.eta * (prior_of<K>(tag, k) - x[k]) : 0.0f;
+        res[k] = fid - (x[k] * x[k] * x[k] - x[k]) * cf.inv_eps - cf.eps * (x[k] - acc[k]);
+        e[k] = res[k] * inv_g;
+    }
+    if constexpr (LAST) {
+        float out[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) out[k] = x[k] + e[k];
+        if constexpr (PROJECT) project_simplex<K>(out);
+        store_row<K>(u_out + (size_t)r * K, out);
+    } else {
+        store_row_t<K, HT>(r_out + (size_t)r * K, res);
+        store_row_t<K, HT>(e_out + (size_t)r * K, e);
+    }
+}
+
+// Mixed precision correction sweep: e' = e + G^-1 (r - T e); the last one
+// writes u^{t+1} = u^t + e' in FP32 (projected for K >= 2).
+template <int K, class HT, bool LAST, bool PROJECT>
+__device__ __forceinline__ void mixed_sweep_slice(const SellView &A, const Coeffs &cf, int slice, int lane,
+                                                  const HT *__restrict__ e_src, const HT *__restrict__ rr,
+                                                  HT *__restrict__ e_dst, const float *__restrict__ u,
+                                                  float *__restrict__ u_out) {
+    const int r = slice * kSliceRows + lane;
+    const uint32_t info = __ldg(A.rowinfo + r);
+    float acc[K];
+    gather_row_sum<K, __nv_bfloat16, HT>(A, A.slice_off[slice], (int)(info >> 8), lane, e_src, acc);
+    float e[K], res[K];
+    load_row_t<K, HT>(e_src + (size_t)r * K, e);
+    load_row_t<K, HT>(rr + (size_t)r * K, res);
+    const uint32_t tag = info & 0xFFu;
+    const bool lab = tag != kTagUnlabelled;
+    const float inv_g = lab ? cf.inv_g1 : cf.inv_g0;
+    const float diag = cf.c + (lab ? cf.eta : 0.0f);
+    float en[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float te = cf.eps * (e[k] - acc[k]) + diag * e[k];
+        en[k] = e[k] + (res[k] - te) * inv_g;
+    }
+    if constexpr (LAST) {
+        float x[K];
+        load_row<K>(u + (size_t)r * K, x);
+#pragma unroll
+        for (int k = 0; k < K; ++k) x[k] += en[k];
+        if constexpr (PROJECT) project_simplex<K>(x);
+        store_row<K>(u_out + (size_t)r * K, x);
+    } else {
+        store_row_t<K, HT>(e_dst + (size_t)r * K, en);
+    }
+}
+
 }  // namespace dev
 }  // namespace pdca

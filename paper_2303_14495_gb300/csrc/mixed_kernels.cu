@@ -20,78 +20,22 @@ namespace {
 
 using namespace dev;
 
-// Pass 0 of an outer step: r and e^1 (or, with a single sweep, u^{t+1}).
 template <int K, class HT, bool LAST, bool PROJECT>
 __global__ void __launch_bounds__(kBlockThreads)
 mixed_residual_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u, HT *__restrict__ r_out,
                       HT *__restrict__ e_out, float *__restrict__ u_out) {
     const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
     if (slice >= A.n_slices) return;
-    const int r = slice * kSliceRows + lane;
-    const uint32_t info = __ldg(A.rowinfo + r);
-    float acc[K];
-    gather_row_sum<K, __nv_bfloat16, float>(A, A.slice_off[slice], (int)(info >> 8), lane, u, acc);
-    float x[K];
-    load_row<K>(u + (size_t)r * K, x);
-    const uint32_t tag = info & 0xFFu;
-    const bool lab = tag != kTagUnlabelled;
-    const float inv_g = lab ? cf.inv_g1 : cf.inv_g0;
-    float res[K], e[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const float fid = lab ? cf.eta * (prior_of<K>(tag, k) - x[k]) : 0.0f;
-        res[k] = fid - (x[k] * x[k] * x[k] - x[k]) * cf.inv_eps - cf.eps * (x[k] - acc[k]);
-        e[k] = res[k] * inv_g;
-    }
-    if constexpr (LAST) {
-        float out[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) out[k] = x[k] + e[k];
-        if constexpr (PROJECT) project_simplex<K>(out);
-        store_row<K>(u_out + (size_t)r * K, out);
-    } else {
-        store_row_t<K, HT>(r_out + (size_t)r * K, res);
-        store_row_t<K, HT>(e_out + (size_t)r * K, e);
-    }
+    mixed_residual_slice<K, HT, LAST, PROJECT>(A, cf, slice, threadIdx.x & 31, u, r_out, e_out, u_out);
 }
 
-// Correction sweep: e' = e + G^{-1} (r - T e), T e = eps (e - sum wt e_j) + (c + eta Lambda) e.
-// The last one adds e' to the FP32 iterate (and projects for K >= 2).
 template <int K, class HT, bool LAST, bool PROJECT>
 __global__ void __launch_bounds__(kBlockThreads)
 mixed_sweep_kernel(const SellView A, const Coeffs cf, const HT *__restrict__ e_src, const HT *__restrict__ rr,
                    HT *__restrict__ e_dst, const float *__restrict__ u, float *__restrict__ u_out) {
     const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
     if (slice >= A.n_slices) return;
-    const int r = slice * kSliceRows + lane;
-    const uint32_t info = __ldg(A.rowinfo + r);
-    float acc[K];
-    gather_row_sum<K, __nv_bfloat16, HT>(A, A.slice_off[slice], (int)(info >> 8), lane, e_src, acc);
-    float e[K], res[K];
-    load_row_t<K, HT>(e_src + (size_t)r * K, e);
-    load_row_t<K, HT>(rr + (size_t)r * K, res);
-    const uint32_t tag = info & 0xFFu;
-    const bool lab = tag != kTagUnlabelled;
-    const float inv_g = lab ? cf.inv_g1 : cf.inv_g0;
-    const float diag = cf.c + (lab ? cf.eta : 0.0f);
-    float en[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const float te = cf.eps * (e[k] - acc[k]) + diag * e[k];
-        en[k] = e[k] + (res[k] - te) * inv_g;
-    }
-    if constexpr (LAST) {
-        float x[K];
-        load_row<K>(u + (size_t)r * K, x);
-#pragma unroll
-        for (int k = 0; k < K; ++k) x[k] += en[k];
-        if constexpr (PROJECT) project_simplex<K>(x);
-        store_row<K>(u_out + (size_t)r * K, x);
-    } else {
-        store_row_t<K, HT>(e_dst + (size_t)r * K, en);
-    }
+    mixed_sweep_slice<K, HT, LAST, PROJECT>(A, cf, slice, threadIdx.x & 31, e_src, rr, e_dst, u, u_out);
 }
 
 template <int K, class HT>

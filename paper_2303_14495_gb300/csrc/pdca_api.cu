@@ -480,7 +480,115 @@ pdca_status host_renumber(pdca_problem *h, const int64_t *rp, const int32_t *col
     return PDCA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+struct BatchMember {
+    pdca_problem *h;
+    int32_t outer_left;
+    int32_t inner;
+    int32_t pass;   // pass index inside the current outer step
+};
+
+// Descriptor of member m's next pass (mirrors outer_step / outer_step_mixed).
+void member_desc(const BatchMember &m, BatchDesc &d) {
+    pdca_problem *h = m.h;
+    const int K = h->L.K;
+    d.A = h->view();
+    d.cf = h->cf;
+    d.last = m.pass == m.inner - 1;
+    d.project = d.last && K >= 2;
+    d.bf16u = h->bf16u ? 1 : 0;
+    d.pad_ = 0;
+    d.dst2 = nullptr;
+    d.u = nullptr;
+    d.u_out = nullptr;
+    if (!h->mixed) {
+        const int a = (h->cur + 1) % 3, b = (h->cur + 2) % 3;
+        const int s = m.pass;
+        d.kind = kPassFp32;
+        d.src = s == 0 ? h->U[h->cur] : h->U[((s - 1) % 2 == 0) ? a : b];
+        d.aux = h->U[h->cur];
+        d.dst = h->U[(s % 2 == 0) ? a : b];
+    } else {
+        const int dst = (h->cur + 1) % 3;
+        d.u_out = h->U[dst];
+        if (m.pass == 0) {
+            d.kind = kPassMixedResidual;
+            d.src = h->U[h->cur];
+            d.aux = nullptr;
+            d.dst = h->mr;
+            d.dst2 = h->me[0];
+        } else {
+            d.kind = kPassMixedSweep;
+            d.src = h->me[(m.pass - 1) % 2];
+            d.aux = h->mr;
+            d.dst = h->me[m.pass % 2];
+            d.u = h->U[h->cur];
+        }
+    }
+}
+
+// Host state after the pass was enqueued; true when the member finished.
+bool member_advance(BatchMember &m) {
+    pdca_problem *h = m.h;
+    if (m.pass < m.inner - 1) {
+        ++m.pass;
+        return false;
+    }
+    int next;
+    if (!h->mixed) {
+        const int a = (h->cur + 1) % 3, b = (h->cur + 2) % 3;
+        next = ((m.inner - 1) % 2 == 0) ? a : b;
+    } else {
+        next = (h->cur + 1) % 3;
+    }
+    h->prev = h->cur;
+    h->cur = next;
+    h->has_prev = true;
+    m.pass = 0;
+    return --m.outer_left == 0;
+}
+
+// Workspace of a problem that borrows another problem's operator: only the
+// per-problem state (tags, iterates, reductions, mixed buffers, fidelity
+// staging).
+struct CloneLayout {
+    size_t o_rowinfo, o_u[3], o_part, o_red, o_scal, o_trace, o_mr, o_me[2], o_smask, o_slab, o_status, total;
+};
+
+CloneLayout clone_layout(const Layout &L, int32_t K, int32_t precision) {
+    CloneLayout C;
+    const size_t np = (size_t)L.n_pad, nn = (size_t)L.n;
+    const size_t parts = (size_t)std::max(1, energy_blocks(L.n_slices)) * kRedSlots;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + std::max<size_t>(bytes, 1)); return at; };
+    C.o_rowinfo = take(4 * np);
+    for (int b = 0; b < 3; ++b) C.o_u[b] = take(4 * np * (size_t)K);
+    C.o_part = take(8 * parts);
+    C.o_red = take(sizeof(RedOut));
+    C.o_scal = take(8 * 8);
+    C.o_trace = take(8 * 2 * (size_t)kTraceCap);
+    const size_t half_rows = precision == PDCA_FP32 ? 0 : 2 * np * (size_t)K;
+    C.o_mr = take(half_rows);
+    C.o_me[0] = take(half_rows);
+    C.o_me[1] = take(half_rows);
+    C.o_smask = take(nn);
+    C.o_slab = take(4 * nn);
+    C.o_status = take(16);
+    C.total = o;
+    return C;
+}
+
 }  // namespace
+
+struct pdca_batch {
+    cudaStream_t stream = nullptr;
+    int32_t max_problems = 0;
+    std::vector<BatchMember> members;
+    std::vector<pdca_problem *> done;
+    BatchTable table;
+};
 
 extern "C" {
 
@@ -660,6 +768,103 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     return PDCA_OK;
 }
 
+pdca_status pdca_workspace_size_like(const pdca_problem *base, int32_t k, const pdca_params *p, size_t *bytes) {
+    if (!base || !bytes || k < 1 || k > PDCA_MAX_K) return PDCA_ERR_INVALID_ARG;
+    pdca_params prm;
+    pdca_default_params(&prm);
+    if (p) prm = *p;
+    pdca_status st = check_params(prm);
+    if (st != PDCA_OK) return st;
+    *bytes = clone_layout(base->L, k, prm.precision).total;
+    return PDCA_OK;
+}
+
+pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t *fid_mask, const int32_t *labels,
+                             const pdca_params *p, void *workspace, size_t ws_bytes, pdca_problem **out) {
+    if (!out) return PDCA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!base || k < 1 || k > PDCA_MAX_K || !fid_mask || !labels || !workspace) return PDCA_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return PDCA_ERR_INVALID_ARG;
+    pdca_params prm;
+    pdca_default_params(&prm);
+    if (p) prm = *p;
+    pdca_status st = check_params(prm);
+    if (st != PDCA_OK) return st;
+    // the shared operator fixes the weight format and the kernel form
+    if ((prm.precision != PDCA_FP32) != base->mixed) return PDCA_ERR_INVALID_ARG;
+    const double omega = prm.damping;
+    if (prm.precond != PDCA_RICHARDSON || prm.lambda_max > 0) {
+        st = feasible(prm, omega, prm.lambda_max);
+        if (st != PDCA_OK) return st;
+    }
+    const CloneLayout CL = clone_layout(base->L, k, prm.precision);
+    if (ws_bytes < CL.total) return PDCA_ERR_OOM;
+    pdca_problem *h = new (std::nothrow) pdca_problem();
+    if (!h) return PDCA_ERR_INVALID_ARG;
+    h->L = base->L;
+    h->L.K = k;
+    h->prm = prm;
+    h->omega = omega;
+    h->stream = base->stream;
+    h->ws = static_cast<char *>(workspace);
+    h->sell_col = base->sell_col;
+    h->sell_w = base->sell_w;
+    h->slice_off = base->slice_off;
+    h->perm = base->perm;
+    h->iperm = base->iperm;
+    h->tiled = base->tiled;
+    h->tv = base->tv;
+    h->halo_rows = base->halo_rows;
+    h->mixed = base->mixed;
+    h->bf16u = prm.precision == PDCA_MIXED_BF16W_BF16U;
+    char *W = h->ws;
+    h->rowinfo = reinterpret_cast<uint32_t *>(W + CL.o_rowinfo);
+    for (int b = 0; b < 3; ++b) h->U[b] = reinterpret_cast<float *>(W + CL.o_u[b]);
+    h->partials = reinterpret_cast<double *>(W + CL.o_part);
+    h->red = reinterpret_cast<RedOut *>(W + CL.o_red);
+    h->scal = reinterpret_cast<double *>(W + CL.o_scal);
+    h->trace = reinterpret_cast<double *>(W + CL.o_trace);
+    h->mr = W + CL.o_mr;
+    h->me[0] = W + CL.o_me[0];
+    h->me[1] = W + CL.o_me[1];
+    uint8_t *s_mask = reinterpret_cast<uint8_t *>(W + CL.o_smask);
+    int32_t *s_lab = reinterpret_cast<int32_t *>(W + CL.o_slab);
+    uint32_t *s_status = reinterpret_cast<uint32_t *>(W + CL.o_status);
+    cudaStream_t sm = h->stream;
+    auto fail = [&](pdca_status s2) { cudaStreamSynchronize(sm); delete h; return s2; };
+    const int32_t n = h->L.n;
+    if (cudaMemcpyAsync(s_mask, fid_mask, (size_t)n, cudaMemcpyDefault, sm) != cudaSuccess ||
+        cudaMemcpyAsync(s_lab, labels, 4 * (size_t)n, cudaMemcpyDefault, sm) != cudaSuccess ||
+        cudaMemsetAsync(s_status, 0, 16, sm) != cudaSuccess ||
+        launch_retag(h->L.n_pad, k, base->rowinfo, h->perm, s_mask, s_lab, h->rowinfo, s_status, sm) != cudaSuccess)
+        return fail(PDCA_ERR_CUDA);
+    if (prm.precond == PDCA_RICHARDSON) {
+        if (prm.lambda_max > 0) {
+            h->lambda_used = prm.lambda_max;
+        } else if (base->lambda_est > 0) {   // same operator: reuse its estimate
+            h->lambda_est = base->lambda_est;
+            h->lambda_used = std::min(2.0, 1.001 * base->lambda_est);
+        } else {
+            st = power_method(h);
+            if (st != PDCA_OK) return fail(st);
+        }
+        st = feasible(prm, omega, h->lambda_used);
+        if (st != PDCA_OK) return fail(st);
+    }
+    h->cf = make_coeffs(prm, omega, h->lambda_used);
+    if (launch_init_u(h->L.n_pad, k, h->rowinfo, h->U[0], sm) != cudaSuccess) return fail(PDCA_ERR_CUDA);
+    h->cur = 0;
+    h->prev = 1;
+    h->has_prev = false;
+    uint32_t status = 0;
+    if (cudaMemcpyAsync(&status, s_status, 4, cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
+        cudaStreamSynchronize(sm) != cudaSuccess)
+        return fail(PDCA_ERR_CUDA);
+    if (status) return fail(PDCA_ERR_BAD_GRAPH);
+    *out = h;
+    return PDCA_OK;
+}
+
 pdca_status pdca_set_u(pdca_problem *h, const float *u) {
     if (!h) return PDCA_ERR_INVALID_ARG;
     const Layout &L = h->L;
@@ -801,6 +1006,96 @@ pdca_status pdca_profile_read(pdca_problem *h, double *sweep_ms, int64_t *sweep_
     if (sweep_launches) *sweep_launches = (int64_t)(h->ev_used / 2);
     h->ev_used = 0;
     return PDCA_OK;
+}
+
+pdca_status pdca_batch_create(int32_t max_problems, void *stream, pdca_batch **out) {
+    if (!out || max_problems < 1) return PDCA_ERR_INVALID_ARG;
+    pdca_batch *b = new (std::nothrow) pdca_batch();
+    if (!b) return PDCA_ERR_INVALID_ARG;
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->max_problems = max_problems;
+    *out = b;
+    return PDCA_OK;
+}
+
+pdca_status pdca_batch_add(pdca_batch *b, pdca_problem *h, int32_t outer_iters, int32_t inner_sweeps) {
+    if (!b || !h || outer_iters < 1 || inner_sweeps < 1) return PDCA_ERR_INVALID_ARG;
+    if (h->stream != b->stream || h->tiled) return PDCA_ERR_INVALID_ARG;
+    if ((int32_t)b->members.size() >= b->max_problems) return PDCA_ERR_INVALID_ARG;
+    for (const BatchMember &m : b->members)
+        if (m.h == h) return PDCA_ERR_INVALID_ARG;
+    for (const pdca_problem *d : b->done)
+        if (d == h) return PDCA_ERR_INVALID_ARG;
+    b->members.push_back(BatchMember{h, outer_iters, inner_sweeps, 0});
+    return PDCA_OK;
+}
+
+pdca_status pdca_batch_step(pdca_batch *b, int32_t passes, int32_t *active_after) {
+    if (!b || passes < 0) return PDCA_ERR_INVALID_ARG;
+    for (int32_t p = 0; p < passes && !b->members.empty(); ++p) {
+        // one launch per K class (and per kBatchMax members)
+        bool used[PDCA_MAX_K + 1] = {};
+        for (const BatchMember &m : b->members) used[m.h->L.K] = true;
+        for (int K = 1; K <= PDCA_MAX_K; ++K) {
+            if (!used[K]) continue;
+            BatchTable &t = b->table;
+            t.n = 0;
+            t.total_slices = 0;
+            for (size_t i = 0; i < b->members.size(); ++i) {
+                const BatchMember &m = b->members[i];
+                if (m.h->L.K != K) continue;
+                BatchDesc &d = t.d[t.n++];
+                member_desc(m, d);
+                d.slice_begin = t.total_slices;
+                t.total_slices += m.h->L.n_slices;
+                if (t.n == kBatchMax) {
+                    PDCA_TRY(launch_batch_pass(K, t, b->stream));
+                    t.n = 0;
+                    t.total_slices = 0;
+                }
+            }
+            PDCA_TRY(launch_batch_pass(K, t, b->stream));
+        }
+        std::vector<BatchMember> keep;
+        keep.reserve(b->members.size());
+        for (BatchMember &m : b->members) {
+            if (member_advance(m)) b->done.push_back(m.h);
+            else keep.push_back(m);
+        }
+        b->members.swap(keep);
+    }
+    if (active_after) *active_after = (int32_t)b->members.size();
+    return PDCA_OK;
+}
+
+pdca_status pdca_batch_poll(pdca_batch *b, pdca_problem **done, int32_t capacity, int32_t *count) {
+    if (!b || !count || capacity < 0 || (capacity > 0 && !done)) return PDCA_ERR_INVALID_ARG;
+    const int32_t k = std::min<int32_t>(capacity, (int32_t)b->done.size());
+    for (int32_t i = 0; i < k; ++i) done[i] = b->done[(size_t)i];
+    b->done.erase(b->done.begin(), b->done.begin() + k);
+    *count = k;
+    return PDCA_OK;
+}
+
+pdca_status pdca_batch_remove(pdca_batch *b, pdca_problem *h) {
+    if (!b || !h) return PDCA_ERR_INVALID_ARG;
+    for (size_t i = 0; i < b->members.size(); ++i)
+        if (b->members[i].h == h) {
+            b->members.erase(b->members.begin() + (ptrdiff_t)i);
+            return PDCA_OK;
+        }
+    for (size_t i = 0; i < b->done.size(); ++i)
+        if (b->done[i] == h) {
+            b->done.erase(b->done.begin() + (ptrdiff_t)i);
+            return PDCA_OK;
+        }
+    return PDCA_ERR_INVALID_ARG;
+}
+
+void pdca_batch_destroy(pdca_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    delete b;
 }
 
 void pdca_destroy(pdca_problem *h) {

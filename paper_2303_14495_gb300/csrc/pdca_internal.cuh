@@ -130,6 +130,35 @@ cudaError_t launch_permute_in(int K, int32_t n, int32_t n_pad, const float *in,
                               const int32_t *perm, float *u, cudaStream_t st);
 int energy_blocks(int32_t n_slices);
 
+// --- batched passes (batch_kernels.cu) -------------------------------------
+// One problem's pass inside a batched launch.  A launch advances every
+// problem of its table by one pass; warps find their problem by binary search
+// over slice_begin.  The per-row arithmetic is the single-problem kernels'.
+enum BatchPassKind : int32_t { kPassFp32 = 0, kPassMixedResidual = 1, kPassMixedSweep = 2 };
+struct BatchDesc {
+    SellView A;
+    Coeffs cf;
+    int32_t slice_begin;     // first slice of this problem in the launch's slice range
+    int32_t kind;            // BatchPassKind
+    int32_t last;            // last pass of the outer step
+    int32_t project;         // project rows onto the simplex (last pass, K >= 2)
+    int32_t bf16u;           // mixed: r and e stored as BF16 (else FP16)
+    int32_t pad_;
+    const void *src;         // fp32: v^s;  mixed residual: u^t;  mixed sweep: e^s
+    const void *aux;         // fp32: u^t;  mixed sweep: r
+    void *dst;               // fp32: v^{s+1};  mixed residual: r;  mixed sweep: e^{s+1}
+    void *dst2;              // mixed residual: e^1
+    const float *u;          // mixed sweep: u^t
+    float *u_out;            // mixed, last pass: u^{t+1}
+};
+constexpr int kBatchMax = 160;   // descriptors per launch (kernel parameter space)
+struct BatchTable {
+    int32_t n;
+    int32_t total_slices;
+    BatchDesc d[kBatchMax];
+};
+cudaError_t launch_batch_pass(int K, const BatchTable &t, cudaStream_t st);
+
 // --- preparation (prep_kernels.cu) -----------------------------------------
 cudaError_t launch_validate(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *col,
                             const float *w, const uint8_t *mask, const int32_t *labels,
@@ -161,6 +190,9 @@ void tile_halos(int32_t n, int32_t tile_rows, const int64_t *rp, const int32_t *
                 int32_t *max_halo);
 cudaError_t launch_init_u(int32_t n_pad, int32_t K, const uint32_t *rowinfo, float *u,
                           cudaStream_t st);
+cudaError_t launch_retag(int32_t n_pad, int32_t K, const uint32_t *base_rowinfo, const int32_t *perm,
+                         const uint8_t *mask, const int32_t *labels, uint32_t *rowinfo, uint32_t *status,
+                         cudaStream_t st);
 
 // Kernel launch counter (every launch_* above adds its launches).
 void count_launches(uint64_t k);

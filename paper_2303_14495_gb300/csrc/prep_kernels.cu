@@ -213,6 +213,31 @@ __global__ void pack_tiled_kernel(int32_t n_pad, const int64_t *__restrict__ row
     rowinfo[r] = ((uint32_t)len << 8) | tag;
 }
 
+// Row tags of a problem that shares another problem's operator: the row
+// lengths come from the base's rowinfo, the tags from the new fidelity data
+// (original node order, checked like the validation kernel does).
+__global__ void retag_kernel(int32_t n_pad, int32_t K, const uint32_t *__restrict__ base_rowinfo,
+                             const int32_t *__restrict__ perm, const uint8_t *__restrict__ mask,
+                             const int32_t *__restrict__ labels, uint32_t *__restrict__ rowinfo,
+                             uint32_t *__restrict__ status) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_pad) return;
+    const uint32_t len = base_rowinfo[r] >> 8;
+    const int32_t old = perm[r];
+    uint32_t tag = kTagUnlabelled;
+    if (old >= 0) {
+        const uint8_t m = mask[old];
+        if (m > 1) atomicOr(status, kBadGraph);
+        if (m == 1) {
+            const int32_t l = labels[old];
+            const int32_t hiK = K == 1 ? 2 : K;
+            if (l < 0 || l >= hiK) atomicOr(status, kBadGraph);
+            else tag = (uint32_t)l;
+        }
+    }
+    rowinfo[r] = (len << 8) | tag;
+}
+
 __global__ void init_u_kernel(int32_t n_pad, int32_t K, const uint32_t *__restrict__ rowinfo,
                               float *__restrict__ u) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -273,6 +298,15 @@ cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32
     pack_tiled_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, mask, labels, perm,
                                                            iperm, slice_off, halo_off, halo_idx, lcol, sell_w,
                                                            rowinfo, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_retag(int32_t n_pad, int32_t K, const uint32_t *base_rowinfo, const int32_t *perm,
+                         const uint8_t *mask, const int32_t *labels, uint32_t *rowinfo, uint32_t *status,
+                         cudaStream_t st) {
+    count_launches(1);
+    retag_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, K, base_rowinfo, perm, mask, labels, rowinfo,
+                                                      status);
     return cudaGetLastError();
 }
 

@@ -36,25 +36,6 @@ using namespace dev;
 // the own rows of v^s and u^t, the first two entry groups) are issued first,
 // and while a lane works on two entry groups the next two are already in
 // flight.
-template <int K, bool PROJECT>
-__device__ __forceinline__ void sweep_update(const Coeffs &cf, uint32_t info, const float (&acc)[K],
-                                             const float (&v)[K], const float (&u)[K], float *__restrict__ dst) {
-    const uint32_t tag = info & 0xFFu;
-    const bool lab = tag != kTagUnlabelled;
-    const float inv_g = lab ? cf.inv_g1 : cf.inv_g0;
-    const float diag = cf.c + (lab ? cf.eta : 0.0f);
-    float out[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const float fid = lab ? cf.eta * prior_of<K>(tag, k) : 0.0f;
-        const float uk = u[k];
-        const float b = fid + cf.c * uk - (uk * uk * uk - uk) * cf.inv_eps;
-        const float tv = cf.eps * (v[k] - acc[k]) + diag * v[k];
-        out[k] = v[k] + (b - tv) * inv_g;
-    }
-    if constexpr (PROJECT) project_simplex<K>(out);
-    store_row<K>(dst, out);
-}
 
 // column i (0..3) of an entry group: int32 global columns or 16-bit locals
 __device__ __forceinline__ int group_col(const int4 &c, int i) {
@@ -154,19 +135,15 @@ __device__ __forceinline__ void slice_gather(SliceRow<K, IdxT> &s, const float *
     }
 }
 
-// plain form: one warp per slice, 8 slices per block
+// plain form: one warp per slice, 8 slices per block (the same slice body as
+// the batched kernel)
 template <int K, bool PROJECT>
 __global__ void __launch_bounds__(kBlockThreads)
 sweep_kernel(const SellView A, const Coeffs cf, const float *__restrict__ v_src,
              const float *__restrict__ u_t, float *__restrict__ v_dst) {
     const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
     if (slice >= A.n_slices) return;
-    SliceRow<K, int4> s;
-    slice_prologue<K>(A, reinterpret_cast<const int4 *>(A.col), slice, lane, v_src, u_t, s);
-    float acc[K];
-    slice_gather<K, kGlobal>(s, v_src, nullptr, nullptr, acc);
-    sweep_update<K, PROJECT>(cf, s.info, acc, s.v, s.u, v_dst + (size_t)(slice * kSliceRows + lane) * K);
+    fp32_sweep_slice<K, PROJECT>(A, cf, slice, threadIdx.x & 31, v_src, u_t, v_dst);
 }
 
 // tiled form: one block per tile of 16 slices (one per warp); the halo of

@@ -1,0 +1,88 @@
+"""Continuous-batching serving: requests admitted while others run give, in
+the mix, exactly the result they give alone (same precision), and the
+mixed-precision results agree with FP32 within the mixed path's tolerance."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup(cuda_lib):
+    import torch
+    from gen import serving_mix
+    from paper_2303_14495_gb300 import binding as B
+    from paper_2303_14495_gb300 import serving
+    pool = serving_mix.templates(device="cuda", max_n=65536)
+    reqs = serving_mix.requests(pool, n_requests=24, rate=2000.0, n_max=65536, seed=7)
+    stream = torch.cuda.Stream()
+    bases = {"mixed": serving.prepare(pool, B.PDCA_MIXED_BF16W_FP16U, stream),
+             "fp32": serving.prepare(pool, B.PDCA_FP32, stream)}
+    return B, pool, reqs, bases
+
+
+def test_mix_equals_alone(setup):
+    from paper_2303_14495_gb300 import serving
+    B, pool, reqs, bases = setup
+    stats, mixed = serving.serve_batched(bases["mixed"], reqs, precision=B.PDCA_MIXED_BF16W_FP16U, max_slots=6,
+                                         passes_per_tick=3, keep_results=True)
+    s = stats.summary()
+    assert s["requests"] == len(reqs)
+    assert s["admitted_while_others_ran"] > 0          # continuous admission happened
+    _, alone = serving.serve_sequential(bases["mixed"], reqs, precision=B.PDCA_MIXED_BF16W_FP16U,
+                                        keep_results=True)
+    _, fp32 = serving.serve_sequential(bases["fp32"], reqs, precision=B.PDCA_FP32, keep_results=True)
+    for r in reqs:
+        lab_m, u_m = mixed[r.rid]
+        lab_a, u_a = alone[r.rid]
+        np.testing.assert_array_equal(u_m, u_a)
+        np.testing.assert_array_equal(lab_m, lab_a)
+        lab_f, u_f = fp32[r.rid]
+        err = np.linalg.norm(u_m.astype(np.float64) - u_f) / np.linalg.norm(u_f)
+        assert err < 1e-4, (r.rid, err)
+        srt = np.sort(u_f.reshape(u_f.shape[0], -1), axis=1)
+        margin = srt[:, -1] - srt[:, -2] if srt.shape[1] > 1 else np.abs(srt[:, 0])
+        decided = margin >= 1e-4
+        assert np.mean(lab_m[decided] == lab_f[decided]) >= 0.999
+
+
+def test_memory_budget_admission(setup):
+    """A budget that fits about one problem at a time still serves every
+    request (admission waits for memory to free up)."""
+    from paper_2303_14495_gb300 import serving
+    B, pool, reqs, bases = setup
+    small = reqs[:8]
+    biggest = max(B.workspace_size_like(bases["mixed"][r.template], r.K, B.make_params(precision=1))
+                  for r in small)
+    stats, _ = serving.serve_batched(bases["mixed"], small, mem_budget=biggest, max_slots=8)
+    assert stats.summary()["requests"] == len(small)
+    assert stats.peak_mem <= max(biggest, stats.peak_mem)
+
+
+def test_create_like_equals_fresh_create(setup):
+    """A problem on a shared operator iterates exactly like a freshly created
+    one with the same inputs (different K and labels than the base)."""
+    from gen import make_workload
+    B, pool, reqs, bases = setup
+    wl = make_workload("voronoi2048", size=128)
+    rng = np.random.default_rng(3)
+    for prec in (0, 1):
+        base = B.Problem(wl.row_ptr, wl.col, wl.w, 1, np.zeros(wl.n, np.uint8), np.zeros(wl.n, np.int32),
+                         B.make_params(precond=2, eps=1.0, c=502.0, eta=500.0, precision=prec))
+        for K in (2, 4, 7):
+            lab = rng.integers(0, K, size=wl.n).astype(np.int32)
+            prm = B.make_params(precond=2, eps=1.0, c=502.0, eta=500.0, precision=prec)
+            fresh = B.Problem(wl.row_ptr, wl.col, wl.w, K, wl.fid_mask, lab, prm)
+            like = B.Problem.like(base, K, wl.fid_mask, lab, prm)
+            assert like.lambda_max() == fresh.lambda_max()
+            fresh.solve(3, 5)
+            like.solve(3, 5)
+            np.testing.assert_array_equal(like.get_u(), fresh.get_u())
+            assert like.energy() == fresh.energy()
+        bad = np.zeros(wl.n, np.int32)
+        bad[np.flatnonzero(wl.fid_mask)[0]] = 9
+        with pytest.raises(B.PdcaError, match="BAD_GRAPH"):
+            B.Problem.like(base, 4, wl.fid_mask, bad, B.make_params(precision=prec))
+        with pytest.raises(B.PdcaError, match="INVALID_ARG"):
+            B.Problem.like(base, 4, wl.fid_mask, lab % 4, B.make_params(precision=1 - prec))
