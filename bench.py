@@ -280,6 +280,33 @@ def run_reference(args, wl, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, local):
+    """Serving under mixed load: the same seeded request mix served by
+    continuous batching in mixed precision and by sequential per-problem
+    FP32 solves, on prepared (resident) graph operators."""
+    import torch
+    from gen import serving_mix
+    from paper_2303_14495_gb300 import binding as B, serving
+    t0 = time.perf_counter()
+    pool = serving_mix.templates(device=f"cuda:{local}")
+    reqs = serving_mix.requests(pool, n_requests=args.serving_requests, rate=args.serving_rate)
+    stream = torch.cuda.Stream()
+    bm = serving.prepare(pool, B.PDCA_MIXED_BF16W_FP16U, stream)
+    bf = serving.prepare(pool, B.PDCA_FP32, stream)
+    serving.serve_batched(bm, reqs[:32], max_slots=16)           # warm-up
+    serving.serve_sequential(bf, reqs[:8])
+    batched, _ = serving.serve_batched(bm, reqs, max_slots=args.serving_slots, passes_per_tick=4)
+    seq, _ = serving.serve_sequential(bf, reqs)
+    return {
+        "mix": (f"{len(reqs)} Poisson requests at {args.serving_rate:g}/s; image graphs (window k-NN, 3x3 "
+                f"patches) and Gaussian-mixture k-NN graphs alternating; N log-uniform in [4Ki, 1Mi] mapped "
+                f"to {len(pool)} resident graph templates; K in {{2, 5, 10}}"),
+        "batched_mixed": batched.summary(),
+        "sequential_fp32": seq.summary(),
+        "wall_s": time.perf_counter() - t0,
+    }
+
+
 def run_ours(args, wl, world, rank, local):
     import torch
     from paper_2303_14495_gb300 import binding as B
@@ -397,6 +424,10 @@ def run_ours(args, wl, world, rank, local):
             cpu["allcores"] = {"value": nb2 / dt2 / 1e9, "cores": thr2,
                                "sample": f"same work, OpenMP over rows, {dt2:.1f} s"}
 
+    serve = None
+    if rank == 0 and not args.no_serving:
+        serve = run_serving(args, local)
+
     if rank != 0:
         return
     line = {
@@ -427,6 +458,8 @@ def run_ours(args, wl, world, rank, local):
     }
     if e2e:
         line["e2e"] = e2e
+    if serve:
+        line["serving"] = serve
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -447,6 +480,10 @@ def main():
     ap.add_argument("--sort-window", type=int, default=0,
                     help="degree-sort window (power of two; 0 = library default)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=512)
+    ap.add_argument("--serving-rate", type=float, default=1000.0)
+    ap.add_argument("--serving-slots", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cpu-allcores", action="store_true")
     args = ap.parse_args()

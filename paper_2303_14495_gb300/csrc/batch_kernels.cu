@@ -33,7 +33,7 @@ __device__ __forceinline__ void mixed_pass(const BatchDesc &d, int slice, int la
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBlockThreads) batch_pass_kernel(const __grid_constant__ BatchTable t) {
+__global__ void __launch_bounds__(kBlockThreads, 4) batch_pass_kernel(const __grid_constant__ BatchTable t) {
     const int gs = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (gs >= t.total_slices) return;
     int lo = 0, hi = t.n - 1;

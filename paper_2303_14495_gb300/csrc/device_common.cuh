@@ -442,24 +442,116 @@ __device__ __forceinline__ void sweep_update(const Coeffs &cf, uint32_t info, co
     store_row<K>(dst, out);
 }
 
-// FP32 sweep of one slice (plain gathers).
+// column i (0..3) of an entry group: int32 global columns or 16-bit locals
+__device__ __forceinline__ int group_col(const int4 &c, int i) {
+    return i == 0 ? c.x : i == 1 ? c.y : i == 2 ? c.z : c.w;
+}
+__device__ __forceinline__ int group_col(const uint2 &c, int i) {
+    return (int)(i == 0 ? (c.x & 0xFFFFu) : i == 1 ? (c.x >> 16) : i == 2 ? (c.y & 0xFFFFu) : (c.y >> 16));
+}
+
+enum GatherMode { kGlobal = 0, kShared = 1, kIndirect = 2 };
+
+template <int K, int MODE>
+__device__ __forceinline__ void source_row(int c, const float *__restrict__ x, const float *hs,
+                                           const int32_t *__restrict__ hidx, float (&r)[K]) {
+    if constexpr (MODE == kGlobal) load_row<K>(x + (size_t)c * K, r);
+    else if constexpr (MODE == kShared) load_row_smem<K>(hs + c * K, r);
+    else load_row<K>(x + (size_t)__ldg(hidx + c) * K, r);
+}
+
+template <int K, int MODE, class IdxT>
+__device__ __forceinline__ void fma_group(float (&acc)[K], const IdxT &c, const float4 &w,
+                                          const float *__restrict__ x, const float *hs,
+                                          const int32_t *__restrict__ hidx) {
+    float r0[K], r1[K], r2[K], r3[K];
+    source_row<K, MODE>(group_col(c, 0), x, hs, hidx, r0);
+    source_row<K, MODE>(group_col(c, 1), x, hs, hidx, r1);
+    source_row<K, MODE>(group_col(c, 2), x, hs, hidx, r2);
+    source_row<K, MODE>(group_col(c, 3), x, hs, hidx, r3);
+    fma_row<K>(acc, w.x, r0);
+    fma_row<K>(acc, w.y, r1);
+    fma_row<K>(acc, w.z, r2);
+    fma_row<K>(acc, w.w, r3);
+}
+
+// Per-lane state of one slice row, loaded before the gather.
+template <int K, class IdxT>
+struct SliceRow {
+    uint32_t info;
+    int groups;
+    const IdxT *cp;
+    const float4 *wp;
+    float v[K], u[K];
+    IdxT c0, c1;
+    float4 w0, w1;
+};
+
+template <int K, class IdxT>
+__device__ __forceinline__ void slice_prologue(const SellView &A, const IdxT *cols, int slice, int lane,
+                                               const float *__restrict__ v_src, const float *__restrict__ u_t,
+                                               SliceRow<K, IdxT> &s) {
+    const int r = slice * kSliceRows + lane;
+    const int64_t base = A.slice_off[slice];
+    s.cp = cols + base / kVec + lane;
+    s.wp = reinterpret_cast<const float4 *>(A.w + base) + lane;
+    s.info = __ldg(A.rowinfo + r);
+    // every real row has an entry and every slice is at least kVec wide, so
+    // group 0 always exists; group 1 is loaded when the slice has it
+    const int width_groups = (int)((A.slice_off[slice + 1] - base) >> 5) / kVec;
+    s.c0 = __ldcs(s.cp);
+    s.w0 = __ldcs(s.wp);
+    if (width_groups > 1) {
+        s.c1 = __ldcs(s.cp + 32);
+        s.w1 = __ldcs(s.wp + 32);
+    }
+    load_row<K>(v_src + (size_t)r * K, s.v);
+    if (u_t == v_src) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) s.u[k] = s.v[k];
+    } else {
+        load_row<K>(u_t + (size_t)r * K, s.u);
+    }
+}
+
+template <int K, int MODE, class IdxT>
+__device__ __forceinline__ void slice_gather(SliceRow<K, IdxT> &s, const float *__restrict__ x, const float *hs,
+                                             const int32_t *__restrict__ hidx, float (&acc)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0f;
+    const int groups = (int)((s.info >> 8) + kVec - 1) / kVec;   // this lane's own groups
+    for (int g = 0; g < groups; g += 2) {
+        IdxT n0 = s.c0, n1 = s.c1;
+        float4 nw0 = s.w0, nw1 = s.w1;
+        if (g + 2 < groups) {
+            n0 = __ldcs(s.cp + 32 * (g + 2));
+            nw0 = __ldcs(s.wp + 32 * (g + 2));
+        }
+        if (g + 3 < groups) {
+            n1 = __ldcs(s.cp + 32 * (g + 3));
+            nw1 = __ldcs(s.wp + 32 * (g + 3));
+        }
+        fma_group<K, MODE>(acc, s.c0, s.w0, x, hs, hidx);
+        if (g + 1 < groups) fma_group<K, MODE>(acc, s.c1, s.w1, x, hs, hidx);
+        s.c0 = n0;
+        s.w0 = nw0;
+        s.c1 = n1;
+        s.w1 = nw1;
+    }
+}
+
+// FP32 sweep of one slice (plain gathers, pipelined: the independent loads
+// first, the next two entry groups in flight while two are processed; the
+// products are added in entry order, as in gather_row_sum).
 template <int K, bool PROJECT>
 __device__ __forceinline__ void fp32_sweep_slice(const SellView &A, const Coeffs &cf, int slice, int lane,
                                                  const float *__restrict__ v_src, const float *__restrict__ u_t,
                                                  float *__restrict__ v_dst) {
-    const int r = slice * kSliceRows + lane;
-    const uint32_t info = __ldg(A.rowinfo + r);
+    SliceRow<K, int4> s;
+    slice_prologue<K>(A, reinterpret_cast<const int4 *>(A.col), slice, lane, v_src, u_t, s);
     float acc[K];
-    gather_row_sum<K, float, float>(A, A.slice_off[slice], (int)(info >> 8), lane, v_src, acc);
-    float v[K], u[K];
-    load_row<K>(v_src + (size_t)r * K, v);
-    if (u_t == v_src) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) u[k] = v[k];
-    } else {
-        load_row<K>(u_t + (size_t)r * K, u);
-    }
-    sweep_update<K, PROJECT>(cf, info, acc, v, u, v_dst + (size_t)r * K);
+    slice_gather<K, kGlobal>(s, v_src, nullptr, nullptr, acc);
+    sweep_update<K, PROJECT>(cf, s.info, acc, s.v, s.u, v_dst + (size_t)(slice * kSliceRows + lane) * K);
 }
 
 // Mixed precision, pass 0 of an outer step: r = b^t - T u^t and e^1 = G^-1 r
