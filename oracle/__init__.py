@@ -60,6 +60,7 @@ class _Problem(C.Structure):
         ("d", C.c_void_p), ("mask", C.c_void_p), ("y", C.c_void_p),
         ("eps", C.c_double), ("eta", C.c_double), ("c", C.c_double),
         ("damping", C.c_double), ("delta0", C.c_double), ("lambda_max", C.c_double),
+        ("step_k", C.c_double),
     ]
 
 
@@ -75,6 +76,7 @@ def _lib(omp: bool = False):
                 "orc_apply_Ls": (None, [i64, i32, vp, vp, vp, vp, vp, vp]),
                 "orc_apply_L": (None, [i64, i32, vp, vp, vp, vp, vp, vp]),
                 "orc_apply_T": (None, [P, vp, vp]),
+                "orc_apply_system": (None, [P, vp, vp]),
                 "orc_prior": (None, [i64, i32, vp, vp, vp]),
                 "orc_init_u": (None, [i64, i32, vp, vp, vp]),
                 "orc_precond_diag": (None, [P, vp]),
@@ -157,7 +159,7 @@ class Problem:
 
     def __init__(self, row_ptr, col, w, K, fid_mask, fid_labels, eps, eta, c,
                  precond=JACOBI_DAMPED, damping=0.5, delta0=1e-6, lambda_max=0.0,
-                 laplacian=LAP_NORMALIZED, omp=False):
+                 laplacian=LAP_NORMALIZED, step_k=0.0, omp=False):
         self.omp = omp
         self.lib = _lib(omp)
         self.row_ptr = np.ascontiguousarray(row_ptr, np.int64)
@@ -180,6 +182,7 @@ class Problem:
         self.s.eps, self.s.eta, self.s.c = float(eps), float(eta), float(c)
         self.s.damping, self.s.delta0 = float(damping), float(delta0)
         self.s.lambda_max = float(lambda_max)
+        self.s.step_k = float(step_k)
 
     @property
     def ref(self):
@@ -213,6 +216,13 @@ class Problem:
         x = self._nk(x)
         y = self._nk()
         self.lib.orc_apply_T(self.ref, _p(x), _p(y))
+        return y
+
+    def apply_system(self, x):
+        """T x (infinite step size) or T_k x = x + k T x (step size k)."""
+        x = self._nk(x)
+        y = self._nk()
+        self.lib.orc_apply_system(self.ref, _p(x), _p(y))
         return y
 
     def precond_diag(self):

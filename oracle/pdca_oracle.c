@@ -15,6 +15,10 @@
  *   b^t = eta*Lambda*y + c*u^t - grad W(u^t),
  *   grad W(u) = (u^3 - u)/eps                           (W(u) = (u^2-1)^2/4)
  *   u <- u + G^{-1} (b - T u)                          (eq. general:diag:pre)
+ * With a finite step size k > 0 (Lemma preconditioned_DCA:stepsize) the linear
+ * system of an outer step is T_k u = b_k^t with T_k = I + k T and
+ * b_k^t = u^t + k b^t (eq. btk:utk), preconditioned by the G_k of eqs.
+ * pre:unnorm:jacob:richard:k and pre:norm:jacob:richard:k.
  * u is an n x K row-major array; K = 1 is the paper's binary +-1 model, K >= 2
  * runs the same scalar update on every column (one +-1 coding per class) and
  * projects each row onto the simplex after every outer step.
@@ -104,6 +108,18 @@ void orc_apply_T(const orc_problem *p, const double *x, double *y) {
     }
 }
 
+/* y = S x for the matrix S of the linear system of one outer step:
+ * S = T (infinite step size) or S = T_k = I + k T (step size k > 0). */
+void orc_apply_system(const orc_problem *p, const double *x, double *y) {
+    orc_apply_T(p, x, y);
+    if (p->step_k > 0.0) {
+        const int64_t nk = p->n * (int64_t)p->K;
+        const double k = p->step_k;
+#pragma omp parallel for schedule(static)
+        for (int64_t q = 0; q < nk; ++q) y[q] = x[q] + k * y[q];
+    }
+}
+
 /* Prior y in the +-1 coding.  K = 1: y_i = +1 for class 1, -1 for class 0.
  * K >= 2: y_ik = +1 if k is the node's class, -1 otherwise.  Rows with
  * Lambda_i = 0 get 0 (they never enter the equations). */
@@ -137,12 +153,32 @@ void orc_init_u(int64_t n, int32_t K, const uint8_t *mask, const int32_t *labels
  *   unnormalized L:   Jd: (eps*d_i + c + eta*Lambda_i)/omega
  *                     Jp: 2 eps d_i + c + delta0 + eta*Lambda_i
  *                     R : eps*lambda_max + c + delta0 + eta*Lambda_i
- * omega = 1/2 is the paper's G = 2 diag(T). */
+ * omega = 1/2 is the paper's G = 2 diag(T).
+ * Finite step size k (Sec. 3.1, G_{.,k} and G_{.,ks}), a_i = 1 (L_s) or d_i (L):
+ *                     Jd: (1 + k (eps*a_i + c + eta*Lambda_i))/omega   (= diag(T_k)/omega)
+ *                     Jp: 1 + k (2 eps a_i + c + eta*Lambda_i) + delta0
+ *                     R : 1 + k (eps*lambda_max + c + eta*Lambda_i) + delta0 */
 void orc_precond_diag(const orc_problem *p, double *g) {
     for (int64_t i = 0; i < p->n; ++i) {
         double lam = p->mask[i] ? 1.0 : 0.0;
         double dii = (p->laplacian == ORC_LAP_NORMALIZED) ? 1.0 : p->d[i];
         double gi;
+        if (p->step_k > 0.0) {
+            const double k = p->step_k;
+            switch (p->precond) {
+            case ORC_JACOBI_DAMPED:
+                gi = (1.0 + k * (p->eps * dii + p->c + p->eta * lam)) / p->damping;
+                break;
+            case ORC_JACOBI_PERTURBED:
+                gi = 1.0 + k * (2.0 * p->eps * dii + p->c + p->eta * lam) + p->delta0;
+                break;
+            default: /* ORC_RICHARDSON */
+                gi = 1.0 + k * (p->eps * p->lambda_max + p->c + p->eta * lam) + p->delta0;
+                break;
+            }
+            g[i] = gi;
+            continue;
+        }
         switch (p->precond) {
         case ORC_JACOBI_DAMPED:
             gi = (p->eps * dii + p->c + p->eta * lam) / p->damping;
@@ -158,7 +194,9 @@ void orc_precond_diag(const orc_problem *p, double *g) {
     }
 }
 
-/* b^t = eta*Lambda*y + c*u^t - (u^t^3 - u^t)/eps   (eq. bt:ut). */
+/* Right-hand side of one outer step's system:
+ *   b^t = eta*Lambda*y + c*u^t - (u^t^3 - u^t)/eps     (eq. bt:ut), infinite step;
+ *   b_k^t = u^t + k b^t                                 (eq. btk:utk), step size k. */
 void orc_rhs(const orc_problem *p, const double *u, double *b) {
     const int64_t nk = p->n * (int64_t)p->K;
 #pragma omp parallel for schedule(static)
@@ -167,15 +205,17 @@ void orc_rhs(const orc_problem *p, const double *u, double *b) {
         double lam = p->mask[i] ? 1.0 : 0.0;
         double grad_w = (u[q] * u[q] * u[q] - u[q]) / p->eps;
         b[q] = p->eta * lam * p->y[q] + p->c * u[q] - grad_w;
+        if (p->step_k > 0.0) b[q] = u[q] + p->step_k * b[q];
     }
 }
 
-/* One diagonal preconditioned sweep v_new = v + G^{-1}(b - T v)
- * (eq. dampedJacobi:richardson): every row reads the old v. tv is scratch. */
+/* One diagonal preconditioned sweep v_new = v + G^{-1}(b - S v)
+ * (eq. dampedJacobi:richardson), S = T or T_k: every row reads the old v.
+ * tv is scratch. */
 void orc_sweep(const orc_problem *p, const double *g, const double *b,
                const double *v, double *tv, double *v_new) {
     const int64_t nk = p->n * (int64_t)p->K;
-    orc_apply_T(p, v, tv);
+    orc_apply_system(p, v, tv);
 #pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < nk; ++q) {
         int64_t i = q / p->K;
@@ -232,10 +272,10 @@ double orc_energy(const orc_problem *p, const double *u, double *scratch_nk) {
     return 0.5 * p->eps * quad + well / (4.0 * p->eps) + 0.5 * p->eta * fid;
 }
 
-/* Relative residual ||b - T u|| / ||b|| of the DCA linear system. */
+/* Relative residual ||b - S u|| / ||b|| of the DCA linear system (S = T or T_k). */
 double orc_residual(const orc_problem *p, const double *b, const double *u, double *scratch_nk) {
     const int64_t nk = p->n * (int64_t)p->K;
-    orc_apply_T(p, u, scratch_nk);
+    orc_apply_system(p, u, scratch_nk);
     double rr = 0.0, bb = 0.0;
     for (int64_t q = 0; q < nk; ++q) {
         double r = b[q] - scratch_nk[q];
@@ -290,7 +330,9 @@ double orc_power_max_eig(const orc_problem *p, int32_t iters) {
     return num / den;
 }
 
-/* pDCA with the infinite step size (Prop. nopre): for t = 0..outer-1,
+/* pDCA with the infinite step size (Prop. nopre), or with step size k
+ * (Lemma preconditioned_DCA:stepsize, b_k^t, T_k, G_k in place of b^t, T, G):
+ * for t = 0..outer-1,
  *   b^t = eta Lambda y + c u^t - grad W(u^t);
  *   v^0 = u^t;  v^{s+1} = v^s + G^{-1}(b^t - T v^s), s < inner;
  *   K >= 2: project each row of v^inner onto the simplex;

@@ -33,6 +33,7 @@ typedef struct {
     double damping;         /* omega for ORC_JACOBI_DAMPED */
     double delta0;
     double lambda_max;      /* for ORC_RICHARDSON */
+    double step_k;          /* step size k of the DCA with step size; 0 = infinite */
 } orc_problem;
 
 int orc_num_threads(void);
@@ -42,6 +43,7 @@ void orc_apply_Ls(int64_t n, int32_t K, const int64_t *row_ptr, const int32_t *c
 void orc_apply_L(int64_t n, int32_t K, const int64_t *row_ptr, const int32_t *col,
                  const float *w, const double *d, const double *x, double *y);
 void orc_apply_T(const orc_problem *p, const double *x, double *y);
+void orc_apply_system(const orc_problem *p, const double *x, double *y);
 void orc_prior(int64_t n, int32_t K, const uint8_t *mask, const int32_t *labels, double *y);
 void orc_init_u(int64_t n, int32_t K, const uint8_t *mask, const int32_t *labels, double *u);
 void orc_precond_diag(const orc_problem *p, double *g);
