@@ -68,15 +68,23 @@ typedef enum {
     PDCA_ERR_TOO_LARGE = 10      /* n above PDCA_STATIC_MAX_N in pdca_energy_static    */
 } pdca_status;
 
-/* Laplacian (Sec. 2.2). */
+/* Laplacian (Sec. 2.2): L_s = I - D^{-1/2} W D^{-1/2} (normalized) or
+ * L = D - W (unnormalized), d_i = sum_j w_ij. */
 enum { PDCA_LAP_NORMALIZED = 0, PDCA_LAP_UNNORMALIZED = 1 };
 
-/* Diagonal preconditioner G (Sec. 3.1, eq. pre:norm:jacob:richard), normalized
- * Laplacian, infinite step size:
- *   PDCA_JACOBI_DAMPED    g_i = (eps + c + eta Lambda_i) / omega
- *                         (the paper's G_{Jd,s} = 2 diag(T) is omega = 1/2);
- *   PDCA_JACOBI_PERTURBED g_i = 2 eps + c + delta0 + eta Lambda_i   (G_{Jp,s});
- *   PDCA_RICHARDSON       g_i = eps lambda_max + c + delta0 + eta Lambda_i (G_{R,s}). */
+/* Diagonal preconditioner G (Sec. 3.1), infinite step size, with a_i = 1 for
+ * L_s (eq. pre:norm:jacob:richard) and a_i = d_i for L (eqs.
+ * pre:unnorm:jacob, pre:unnorm:richard):
+ *   PDCA_JACOBI_DAMPED    g_i = (eps a_i + c + eta Lambda_i) / omega
+ *                         (the paper's G_Jd = 2 diag(T) is omega = 1/2);
+ *   PDCA_JACOBI_PERTURBED g_i = 2 eps a_i + c + delta0 + eta Lambda_i    (G_Jp);
+ *   PDCA_RICHARDSON       g_i = eps lambda_max + c + delta0 + eta Lambda_i (G_R),
+ *                         lambda_max of L_s or L.
+ * With a finite step size k (Lemma preconditioned_DCA:stepsize) the system of
+ * an outer step is (I + kT) u = u^t + k b^t with the G_k of eqs.
+ * pre:unnorm:jacob:richard:k / pre:norm:jacob:richard:k; divided by k this is
+ * the system above with c + 1/k in place of c and delta0/k in place of
+ * delta0, which is how the library runs it. */
 enum { PDCA_JACOBI_DAMPED = 0, PDCA_JACOBI_PERTURBED = 1, PDCA_RICHARDSON = 2 };
 
 /* Node renumbering at create time (a layout choice; results are returned in
@@ -117,14 +125,20 @@ typedef struct {
     double eps;          /* diffuse interface parameter epsilon > 0                    */
     double c;            /* convex-split constant c > 0 (eq. dc:functional)           */
     double eta;          /* fidelity weight eta >= 0 (eq. functional:GL)              */
-    int32_t laplacian;   /* PDCA_LAP_*; only PDCA_LAP_NORMALIZED is implemented       */
+    int32_t laplacian;   /* PDCA_LAP_NORMALIZED (default) / PDCA_LAP_UNNORMALIZED     */
     int32_t precond;     /* PDCA_JACOBI_DAMPED / PDCA_JACOBI_PERTURBED / PDCA_RICHARDSON */
-    double damping;      /* omega in (0,1) for PDCA_JACOBI_DAMPED; feasible for every
-                            graph iff c > eps (2 omega - 1)/(1 - omega)               */
+    double damping;      /* omega in (0,1) for PDCA_JACOBI_DAMPED.  Checked at create
+                            with c' = c + 1/k (c' = c for the infinite step):
+                            L_s: feasible for every graph iff
+                            c' > eps (2 omega - 1)/(1 - omega);
+                            L:   required c' > eps max_i d_i (2 omega - 1)/(1 - omega),
+                            sufficient on every graph, attained on regular
+                            bipartite ones                                           */
     double delta0;       /* the small constant delta_0 > 0 of G_Jp and G_R (1e-6)     */
-    double lambda_max;   /* lambda_max(L_s) for PDCA_RICHARDSON; 0 = estimate it with
-                            the power method at create time, then use
-                            min(2, 1.001 * estimate) (2 bounds it, Prop. diagonal:pre) */
+    double lambda_max;   /* lambda_max of L_s (or L) for PDCA_RICHARDSON; 0 = estimate
+                            it with the power method at create time, then use
+                            min(B, 1.001 * estimate) with the bound B = 2 for L_s
+                            and B = 2 max_i d_i for L (Prop. diagonal:pre)           */
     int32_t power_iters; /* power-method iterations (150 in the paper's experiments)   */
     int32_t precision;   /* PDCA_FP32 / PDCA_MIXED_BF16W_FP16U / PDCA_MIXED_BF16W_BF16U */
     int32_t sort_window; /* rows are sorted by degree inside windows of this many rows
@@ -133,8 +147,11 @@ typedef struct {
                             PDCA_REORDER_BFS: windows of min(sort_window, 1024) rows
                             inside each 1024-node block, 0 = 1024                    */
     int32_t reorder;     /* PDCA_REORDER_BFS (default) / PDCA_REORDER_NONE             */
-    int32_t tiling;      /* PDCA_TILING_AUTO (default) / _OFF / _ON                    */
+    int32_t tiling;      /* PDCA_TILING_AUTO (default) / _OFF / _ON; _ON needs the
+                            normalized Laplacian                                     */
     int32_t reserved_;
+    double step_k;       /* step size k > 0 of the DCA with step size, or 0 for the
+                            infinite step size (Prop. nopre, the default)            */
 } pdca_params;
 
 typedef struct pdca_problem pdca_problem;
@@ -142,7 +159,7 @@ typedef struct pdca_problem pdca_problem;
 /* Fill *p with the defaults: eps = 1, c = 3, eta = 1, normalized Laplacian,
  * perturbed Jacobi, omega = 0.5, delta0 = 1e-6, lambda_max = 0 (estimate),
  * 150 power iterations, FP32, automatic sort window, BFS renumbering,
- * automatic tiling. */
+ * automatic tiling, infinite step size (step_k = 0). */
 void pdca_default_params(pdca_params *p);
 
 /* Device workspace, in bytes, that pdca_create needs for this graph.

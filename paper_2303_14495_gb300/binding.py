@@ -61,7 +61,7 @@ class pdca_params(C.Structure):
         ("damping", C.c_double), ("delta0", C.c_double), ("lambda_max", C.c_double),
         ("power_iters", C.c_int32), ("precision", C.c_int32),
         ("sort_window", C.c_int32), ("reorder", C.c_int32), ("tiling", C.c_int32),
-        ("reserved_", C.c_int32),
+        ("reserved_", C.c_int32), ("step_k", C.c_double),
     ]
 
 
@@ -138,14 +138,14 @@ def _ptr(a) -> Optional[int]:
 def make_params(eps=1.0, c=3.0, eta=1.0, precond=PDCA_JACOBI_PERTURBED, damping=0.5, delta0=1e-6,
                 lambda_max=0.0, power_iters=150, laplacian=PDCA_LAP_NORMALIZED,
                 precision=PDCA_FP32, sort_window=0, reorder=PDCA_REORDER_BFS,
-                tiling=PDCA_TILING_AUTO) -> pdca_params:
+                tiling=PDCA_TILING_AUTO, step_k=0.0) -> pdca_params:
     p = pdca_params()
     lib().pdca_default_params(C.byref(p))
     p.eps, p.c, p.eta = float(eps), float(c), float(eta)
     p.precond, p.damping, p.delta0 = int(precond), float(damping), float(delta0)
     p.lambda_max, p.power_iters = float(lambda_max), int(power_iters)
     p.laplacian, p.precision, p.sort_window = int(laplacian), int(precision), int(sort_window)
-    p.reorder, p.tiling = int(reorder), int(tiling)
+    p.reorder, p.tiling, p.step_k = int(reorder), int(tiling), float(step_k)
     return p
 
 

@@ -422,12 +422,26 @@ __device__ __forceinline__ void block_sum_store(float (&v)[S], double *__restric
 // One pass over one slice (lane = row), shared by the single-problem kernels
 // and the batched kernel.
 // ---------------------------------------------------------------------------
-template <int K, bool PROJECT>
-__device__ __forceinline__ void sweep_update(const Coeffs &cf, uint32_t info, const float (&acc)[K],
+// 1/g_i: precomputed per tag for L_s; alpha a_i + beta per row for L
+template <bool UN>
+__device__ __forceinline__ float inv_g_of(const Coeffs &cf, bool lab, float a) {
+    if constexpr (UN) return __frcp_rn(fmaf(cf.alpha, a, lab ? cf.beta1 : cf.beta0));
+    else return lab ? cf.inv_g1 : cf.inv_g0;
+}
+
+// (L x)_i = a_i x_i - acc with a_i = 1 for L_s
+template <bool UN>
+__device__ __forceinline__ float lap_row(float a, float x, float acc) {
+    if constexpr (UN) return a * x - acc;
+    else return x - acc;
+}
+
+template <int K, bool PROJECT, bool UN = false>
+__device__ __forceinline__ void sweep_update(const Coeffs &cf, uint32_t info, float a, const float (&acc)[K],
                                              const float (&v)[K], const float (&u)[K], float *__restrict__ dst) {
     const uint32_t tag = info & 0xFFu;
     const bool lab = tag != kTagUnlabelled;
-    const float inv_g = lab ? cf.inv_g1 : cf.inv_g0;
+    const float inv_g = inv_g_of<UN>(cf, lab, a);
     const float diag = cf.c + (lab ? cf.eta : 0.0f);
     float out[K];
 #pragma unroll
@@ -435,7 +449,7 @@ __device__ __forceinline__ void sweep_update(const Coeffs &cf, uint32_t info, co
         const float fid = lab ? cf.eta * prior_of<K>(tag, k) : 0.0f;
         const float uk = u[k];
         const float b = fid + cf.c * uk - (uk * uk * uk - uk) * cf.inv_eps;
-        const float tv = cf.eps * (v[k] - acc[k]) + diag * v[k];
+        const float tv = cf.eps * lap_row<UN>(a, v[k], acc[k]) + diag * v[k];
         out[k] = v[k] + (b - tv) * inv_g;
     }
     if constexpr (PROJECT) project_simplex<K>(out);
@@ -479,6 +493,7 @@ __device__ __forceinline__ void fma_group(float (&acc)[K], const IdxT &c, const 
 template <int K, class IdxT>
 struct SliceRow {
     uint32_t info;
+    float a;       // a_i (unnormalized L only)
     int groups;
     const IdxT *cp;
     const float4 *wp;
@@ -487,7 +502,7 @@ struct SliceRow {
     float4 w0, w1;
 };
 
-template <int K, class IdxT>
+template <int K, bool UN = false, class IdxT>
 __device__ __forceinline__ void slice_prologue(const SellView &A, const IdxT *cols, int slice, int lane,
                                                const float *__restrict__ v_src, const float *__restrict__ u_t,
                                                SliceRow<K, IdxT> &s) {
@@ -496,6 +511,7 @@ __device__ __forceinline__ void slice_prologue(const SellView &A, const IdxT *co
     s.cp = cols + base / kVec + lane;
     s.wp = reinterpret_cast<const float4 *>(A.w + base) + lane;
     s.info = __ldg(A.rowinfo + r);
+    s.a = UN ? __ldg(A.self + r) : 1.0f;
     // every real row has an entry and every slice is at least kVec wide, so
     // group 0 always exists; group 1 is loaded when the slice has it
     const int width_groups = (int)((A.slice_off[slice + 1] - base) >> 5) / kVec;
@@ -543,37 +559,39 @@ __device__ __forceinline__ void slice_gather(SliceRow<K, IdxT> &s, const float *
 // FP32 sweep of one slice (plain gathers, pipelined: the independent loads
 // first, the next two entry groups in flight while two are processed; the
 // products are added in entry order, as in gather_row_sum).
-template <int K, bool PROJECT>
+template <int K, bool PROJECT, bool UN>
 __device__ __forceinline__ void fp32_sweep_slice(const SellView &A, const Coeffs &cf, int slice, int lane,
                                                  const float *__restrict__ v_src, const float *__restrict__ u_t,
                                                  float *__restrict__ v_dst) {
     SliceRow<K, int4> s;
-    slice_prologue<K>(A, reinterpret_cast<const int4 *>(A.col), slice, lane, v_src, u_t, s);
+    slice_prologue<K, UN>(A, reinterpret_cast<const int4 *>(A.col), slice, lane, v_src, u_t, s);
     float acc[K];
     slice_gather<K, kGlobal>(s, v_src, nullptr, nullptr, acc);
-    sweep_update<K, PROJECT>(cf, s.info, acc, s.v, s.u, v_dst + (size_t)(slice * kSliceRows + lane) * K);
+    sweep_update<K, PROJECT, UN>(cf, s.info, s.a, acc, s.v, s.u,
+                                 v_dst + (size_t)(slice * kSliceRows + lane) * K);
 }
 
 // Mixed precision, pass 0 of an outer step: r = b^t - T u^t and e^1 = G^-1 r
 // (or, with a single sweep, u^{t+1} = u^t + e^1).
-template <int K, class HT, bool LAST, bool PROJECT>
+template <int K, class HT, bool LAST, bool PROJECT, bool UN>
 __device__ __forceinline__ void mixed_residual_slice(const SellView &A, const Coeffs &cf, int slice, int lane,
                                                      const float *__restrict__ u, HT *__restrict__ r_out,
                                                      HT *__restrict__ e_out, float *__restrict__ u_out) {
     const int r = slice * kSliceRows + lane;
     const uint32_t info = __ldg(A.rowinfo + r);
+    const float a = UN ? __ldg(A.self + r) : 1.0f;
     float acc[K];
     gather_row_sum<K, __nv_bfloat16, float>(A, A.slice_off[slice], (int)(info >> 8), lane, u, acc);
     float x[K];
     load_row<K>(u + (size_t)r * K, x);
     const uint32_t tag = info & 0xFFu;
     const bool lab = tag != kTagUnlabelled;
-    const float inv_g = lab ? cf.inv_g1 : cf.inv_g0;
+    const float inv_g = inv_g_of<UN>(cf, lab, a);
     float res[K], e[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const float fid = lab ? cf.eta * (prior_of<K>(tag, k) - x[k]) : 0.0f;
-        res[k] = fid - (x[k] * x[k] * x[k] - x[k]) * cf.inv_eps - cf.eps * (x[k] - acc[k]);
+        res[k] = fid - (x[k] * x[k] * x[k] - x[k]) * cf.inv_eps - cf.eps * lap_row<UN>(a, x[k], acc[k]);
         e[k] = res[k] * inv_g;
     }
     if constexpr (LAST) {
@@ -590,13 +608,14 @@ __device__ __forceinline__ void mixed_residual_slice(const SellView &A, const Co
 
 // Mixed precision correction sweep: e' = e + G^-1 (r - T e); the last one
 // writes u^{t+1} = u^t + e' in FP32 (projected for K >= 2).
-template <int K, class HT, bool LAST, bool PROJECT>
+template <int K, class HT, bool LAST, bool PROJECT, bool UN>
 __device__ __forceinline__ void mixed_sweep_slice(const SellView &A, const Coeffs &cf, int slice, int lane,
                                                   const HT *__restrict__ e_src, const HT *__restrict__ rr,
                                                   HT *__restrict__ e_dst, const float *__restrict__ u,
                                                   float *__restrict__ u_out) {
     const int r = slice * kSliceRows + lane;
     const uint32_t info = __ldg(A.rowinfo + r);
+    const float a = UN ? __ldg(A.self + r) : 1.0f;
     float acc[K];
     gather_row_sum<K, __nv_bfloat16, HT>(A, A.slice_off[slice], (int)(info >> 8), lane, e_src, acc);
     float e[K], res[K];
@@ -604,12 +623,12 @@ __device__ __forceinline__ void mixed_sweep_slice(const SellView &A, const Coeff
     load_row_t<K, HT>(rr + (size_t)r * K, res);
     const uint32_t tag = info & 0xFFu;
     const bool lab = tag != kTagUnlabelled;
-    const float inv_g = lab ? cf.inv_g1 : cf.inv_g0;
+    const float inv_g = inv_g_of<UN>(cf, lab, a);
     const float diag = cf.c + (lab ? cf.eta : 0.0f);
     float en[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const float te = cf.eps * (e[k] - acc[k]) + diag * e[k];
+        const float te = cf.eps * lap_row<UN>(a, e[k], acc[k]) + diag * e[k];
         en[k] = e[k] + (res[k] - te) * inv_g;
     }
     if constexpr (LAST) {

@@ -1,0 +1,100 @@
+// Kernels of the mixed-precision outer step, shared by mixed_kernels.cu
+// (L_s instances) and mixed_kernels_un.cu (L = D - W instances), which are
+// compiled separately so the two sets build in parallel.
+#pragma once
+#include "device_common.cuh"
+
+namespace pdca {
+namespace {
+
+using namespace dev;
+
+template <int K, class HT, bool LAST, bool PROJECT, bool UN>
+__global__ void __launch_bounds__(kBlockThreads)
+mixed_residual_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u, HT *__restrict__ r_out,
+                      HT *__restrict__ e_out, float *__restrict__ u_out) {
+    const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (slice >= A.n_slices) return;
+    mixed_residual_slice<K, HT, LAST, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, u, r_out, e_out, u_out);
+}
+
+template <int K, class HT, bool LAST, bool PROJECT, bool UN>
+__global__ void __launch_bounds__(kBlockThreads)
+mixed_sweep_kernel(const SellView A, const Coeffs cf, const HT *__restrict__ e_src, const HT *__restrict__ rr,
+                   HT *__restrict__ e_dst, const float *__restrict__ u, float *__restrict__ u_out) {
+    const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (slice >= A.n_slices) return;
+    mixed_sweep_slice<K, HT, LAST, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, e_src, rr, e_dst, u, u_out);
+}
+
+template <int K, class HT, bool UN>
+cudaError_t residual_ku(bool last, bool project, const SellView &A, const Coeffs &cf, const float *u, void *r,
+                        void *e, float *u_out, cudaStream_t st) {
+    const int blocks = (A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    HT *rh = static_cast<HT *>(r), *eh = static_cast<HT *>(e);
+    if (!last)
+        mixed_residual_kernel<K, HT, false, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, u, rh, eh, u_out);
+    else if (project && K >= 2)
+        mixed_residual_kernel<K, HT, true, (K >= 2), UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, u, rh, eh,
+                                                                                          u_out);
+    else
+        mixed_residual_kernel<K, HT, true, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, u, rh, eh, u_out);
+    return cudaGetLastError();
+}
+
+template <int K, class HT, bool UN>
+cudaError_t sweep_ku(bool last, bool project, const SellView &A, const Coeffs &cf, const void *e_src,
+                     const void *r, void *e_dst, const float *u, float *u_out, cudaStream_t st) {
+    const int blocks = (A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const HT *es = static_cast<const HT *>(e_src), *rh = static_cast<const HT *>(r);
+    HT *ed = static_cast<HT *>(e_dst);
+    if (!last)
+        mixed_sweep_kernel<K, HT, false, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, es, rh, ed, u, u_out);
+    else if (project && K >= 2)
+        mixed_sweep_kernel<K, HT, true, (K >= 2), UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, es, rh, ed, u,
+                                                                                       u_out);
+    else
+        mixed_sweep_kernel<K, HT, true, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, es, rh, ed, u, u_out);
+    return cudaGetLastError();
+}
+
+#define PDCA_DISPATCH_K(K, CALL)                                                      \
+    switch (K) {                                                                      \
+    case 1: return CALL(1); case 2: return CALL(2); case 3: return CALL(3);           \
+    case 4: return CALL(4); case 5: return CALL(5); case 6: return CALL(6);           \
+    case 7: return CALL(7); case 8: return CALL(8); case 9: return CALL(9);           \
+    case 10: return CALL(10); case 11: return CALL(11); case 12: return CALL(12);     \
+    case 13: return CALL(13); case 14: return CALL(14); case 15: return CALL(15);     \
+    case 16: return CALL(16);                                                         \
+    default: return cudaErrorInvalidValue;                                            \
+    }
+
+template <bool UN>
+cudaError_t mixed_residual_all(int K, bool bf16u, bool last, bool project, const SellView &A, const Coeffs &cf,
+                               const float *u, void *r, void *e, float *u_out, cudaStream_t st) {
+    if (bf16u) {
+#define CALL(KK) residual_ku<KK, __nv_bfloat16, UN>(last, project, A, cf, u, r, e, u_out, st)
+        PDCA_DISPATCH_K(K, CALL)
+#undef CALL
+    }
+#define CALL(KK) residual_ku<KK, __half, UN>(last, project, A, cf, u, r, e, u_out, st)
+    PDCA_DISPATCH_K(K, CALL)
+#undef CALL
+}
+
+template <bool UN>
+cudaError_t mixed_sweep_all(int K, bool bf16u, bool last, bool project, const SellView &A, const Coeffs &cf,
+                            const void *e_src, const void *r, void *e_dst, const float *u, float *u_out,
+                            cudaStream_t st) {
+    if (bf16u) {
+#define CALL(KK) sweep_ku<KK, __nv_bfloat16, UN>(last, project, A, cf, e_src, r, e_dst, u, u_out, st)
+        PDCA_DISPATCH_K(K, CALL)
+#undef CALL
+    }
+#define CALL(KK) sweep_ku<KK, __half, UN>(last, project, A, cf, e_src, r, e_dst, u, u_out, st)
+    PDCA_DISPATCH_K(K, CALL)
+#undef CALL
+}
+
+}  // namespace
+}  // namespace pdca

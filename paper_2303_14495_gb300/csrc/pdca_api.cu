@@ -40,7 +40,7 @@ struct Layout {
     bool host_order = false;           // renumbering computed on the host (BFS blocks)
     int64_t nnz = 0, sell_entries = 0, sell_cap = 0, halo_cap = 0;
     std::vector<int64_t> slice_off;    // n_slices + 1 (exact; filled at create for host order)
-    size_t o_col, o_w, o_slice, o_rowinfo, o_perm, o_iperm, o_u[3], o_part, o_red, o_scal, o_trace;
+    size_t o_col, o_w, o_slice, o_rowinfo, o_perm, o_iperm, o_self, o_u[3], o_part, o_red, o_scal, o_trace;
     size_t o_hoff, o_hidx;
     size_t o_mr, o_me[2];              // mixed precision: r and the two corrections (16-bit)
     size_t o_srp, o_scol, o_sw, o_sdeg, o_smask, o_slab, o_status;
@@ -51,17 +51,28 @@ struct Layout {
 // degree inside windows of `sigma` rows: inside a window sorted descending,
 // sum over slices of 32 * width <= (window nonzeros) + 32 * (window maximum),
 // and the window maxima sum to at most the sum of the largest
-// (number of windows) degrees.
-int64_t sell_bound(const int64_t *rp, int32_t n, int32_t sigma) {
+// (number of windows) degrees; rounding each slice width up to kVec adds at
+// most 32 (kVec - 1) per slice.  The top degrees are summed from a degree
+// histogram (one pass) unless the largest degree makes it too big.
+int64_t sell_bound(const int64_t *rp, int32_t n, int32_t sigma, int64_t max_deg) {
     const int64_t windows = ((int64_t)n + sigma - 1) / sigma;
-    std::vector<int32_t> d((size_t)n);
-    for (int32_t i = 0; i < n; ++i) d[(size_t)i] = (int32_t)(rp[i + 1] - rp[i]);
-    const int64_t top = std::min<int64_t>(windows, n);
-    std::nth_element(d.begin(), d.begin() + (top - 1), d.end(), std::greater<int32_t>());
-    int64_t s = 0;
-    for (int64_t i = 0; i < top; ++i) s += d[(size_t)i];
+    int64_t top = std::min<int64_t>(windows, n), s = 0;
+    if (max_deg <= (1 << 20)) {
+        std::vector<uint32_t> hist((size_t)max_deg + 1, 0u);
+        for (int32_t i = 0; i < n; ++i) ++hist[(size_t)(rp[i + 1] - rp[i])];
+        for (int64_t d = max_deg; d >= 0 && top > 0; --d) {
+            const int64_t take = std::min<int64_t>(top, hist[(size_t)d]);
+            s += take * d;
+            top -= take;
+        }
+    } else {
+        std::vector<int32_t> d((size_t)n);
+        for (int32_t i = 0; i < n; ++i) d[(size_t)i] = (int32_t)(rp[i + 1] - rp[i]);
+        std::nth_element(d.begin(), d.begin() + (top - 1), d.end(), std::greater<int32_t>());
+        for (int64_t i = 0; i < top; ++i) s += d[(size_t)i];
+    }
     const int64_t n_slices = ((int64_t)n + kSliceRows - 1) / kSliceRows;
-    return rp[n] + (int64_t)kSliceRows * s + n_slices * kSliceRows * (kVec - 1);   // + rounding to kVec
+    return rp[n] + (int64_t)kSliceRows * s + n_slices * kSliceRows * (kVec - 1);
 }
 
 // Slice widths for one sort window: the degrees of the window sorted
@@ -78,8 +89,12 @@ void window_widths(const int64_t *rp, int64_t base, int64_t end, std::vector<int
 int64_t sell_entries_for(const int64_t *rp, int32_t n, int32_t sigma, std::vector<int64_t> &widths) {
     const int32_t n_slices = (n + kSliceRows - 1) / kSliceRows;
     widths.assign((size_t)n_slices, 0);
-    std::vector<int32_t> scratch;
-    for (int64_t base = 0; base < n; base += sigma) window_widths(rp, base, std::min<int64_t>(n, base + sigma), scratch, widths);
+    const int64_t nwin = ((int64_t)n + sigma - 1) / sigma;
+    host_parallel_for(nwin, [&](int64_t wdx) {
+        std::vector<int32_t> scratch;
+        const int64_t base = wdx * sigma;
+        window_widths(rp, base, std::min<int64_t>(n, base + sigma), scratch, widths);
+    });
     int64_t tot = 0;
     for (int64_t w : widths) tot += w * kSliceRows;
     return tot;
@@ -89,7 +104,9 @@ pdca_status check_params(const pdca_params &p) {
     auto fin = [](double x) { return std::isfinite(x); };
     if (!(fin(p.eps) && p.eps > 0) || !(fin(p.c) && p.c > 0) || !(fin(p.eta) && p.eta >= 0))
         return PDCA_ERR_INVALID_ARG;
-    if (p.laplacian != PDCA_LAP_NORMALIZED) return PDCA_ERR_INVALID_ARG;
+    if (p.laplacian != PDCA_LAP_NORMALIZED && p.laplacian != PDCA_LAP_UNNORMALIZED) return PDCA_ERR_INVALID_ARG;
+    if (!(fin(p.step_k) && p.step_k >= 0)) return PDCA_ERR_INVALID_ARG;
+    if (p.laplacian == PDCA_LAP_UNNORMALIZED && p.tiling == PDCA_TILING_ON) return PDCA_ERR_INVALID_ARG;
     if (p.precision != PDCA_FP32 && p.precision != PDCA_MIXED_BF16W_FP16U && p.precision != PDCA_MIXED_BF16W_BF16U)
         return PDCA_ERR_INVALID_ARG;
     if (p.precision != PDCA_FP32 && p.tiling == PDCA_TILING_ON) return PDCA_ERR_INVALID_ARG;
@@ -112,11 +129,23 @@ pdca_status check_params(const pdca_params &p) {
 // c > eps (2 omega - 1)/(1 - omega) (the spectrum of L_s lies in [0, 2]);
 // perturbed Jacobi and Richardson need delta0 > 0 (Richardson also a
 // lambda_max that bounds the spectrum, which the caller vouches for).
-pdca_status feasible(const pdca_params &p, double omega, double lambda) {
+// c + 1/k: dividing the step-size-k system (I + kT, u^t + k b^t, G_k) by k
+// gives the infinite-step system with this c and delta0/k.
+double c_eff(const pdca_params &p) { return p.step_k > 0.0 ? p.c + 1.0 / p.step_k : p.c; }
+double delta0_eff(const pdca_params &p) { return p.step_k > 0.0 ? p.delta0 / p.step_k : p.delta0; }
+
+// Feasibility G > T (Sec. 3.1).  Damped Jacobi G = diag(T)/omega: for L_s the
+// bound on c is exact for every graph (eigenvalues of D^{-1/2} W D^{-1/2} lie
+// in [-1, 1]); for L, W >= -D gives G - T >= eps (1/omega - 2) D
+// + (1/omega - 1)(c + eta Lambda), so c > eps d_max (2 omega - 1)/(1 - omega)
+// suffices.  dmax = largest degree (used for L only).
+pdca_status feasible(const pdca_params &p, double omega, double lambda, double dmax) {
+    const double amax = p.laplacian == PDCA_LAP_UNNORMALIZED ? dmax : 1.0;
     switch (p.precond) {
     case PDCA_JACOBI_DAMPED:
         if (!(omega > 0.0 && omega < 1.0)) return PDCA_ERR_INFEASIBLE;
-        if (omega > 0.5 && !(p.c > p.eps * (2.0 * omega - 1.0) / (1.0 - omega))) return PDCA_ERR_INFEASIBLE;
+        if (omega > 0.5 && !(c_eff(p) > p.eps * amax * (2.0 * omega - 1.0) / (1.0 - omega)))
+            return PDCA_ERR_INFEASIBLE;
         return PDCA_OK;
     case PDCA_JACOBI_PERTURBED:
         return p.delta0 > 0.0 ? PDCA_OK : PDCA_ERR_INFEASIBLE;
@@ -125,36 +154,42 @@ pdca_status feasible(const pdca_params &p, double omega, double lambda) {
     }
 }
 
+// g_i = alpha a_i + beta_{Lambda_i} (a_i = 1 for L_s, d_i for L).
 Coeffs make_coeffs(const pdca_params &p, double omega, double lambda) {
-    double g0, g1;
+    const double c = c_eff(p), d0 = delta0_eff(p);
+    double alpha, beta0;
     switch (p.precond) {
     case PDCA_JACOBI_DAMPED:
-        g0 = (p.eps + p.c) / omega;
-        g1 = (p.eps + p.c + p.eta) / omega;
+        alpha = p.eps / omega;
+        beta0 = c / omega;
         break;
     case PDCA_JACOBI_PERTURBED:
-        g0 = 2.0 * p.eps + p.c + p.delta0;
-        g1 = g0 + p.eta;
+        alpha = 2.0 * p.eps;
+        beta0 = c + d0;
         break;
     default:
-        g0 = p.eps * lambda + p.c + p.delta0;
-        g1 = g0 + p.eta;
+        alpha = 0.0;
+        beta0 = p.eps * lambda + c + d0;
         break;
     }
+    const double beta1 = beta0 + (p.precond == PDCA_JACOBI_DAMPED ? p.eta / omega : p.eta);
     Coeffs cf;
     cf.eps = (float)p.eps;
     cf.inv_eps = (float)(1.0 / p.eps);
-    cf.c = (float)p.c;
+    cf.c = (float)c;
     cf.eta = (float)p.eta;
-    cf.inv_g0 = (float)(1.0 / g0);
-    cf.inv_g1 = (float)(1.0 / g1);
+    cf.inv_g0 = (float)(1.0 / (alpha + beta0));
+    cf.inv_g1 = (float)(1.0 / (alpha + beta1));
+    cf.alpha = (float)alpha;
+    cf.beta0 = (float)beta0;
+    cf.beta1 = (float)beta1;
     return cf;
 }
 
 // Host copy of row_ptr (copied from the device when it lives there) plus
 // its structural checks.
 pdca_status host_row_ptr(const int64_t *row_ptr, int32_t n, std::vector<int64_t> &keep,
-                         const int64_t **view) {
+                         const int64_t **view, int64_t *max_deg = nullptr) {
     if (!row_ptr || n < 1) return PDCA_ERR_INVALID_ARG;
     if (is_device_ptr(row_ptr)) {
         keep.resize((size_t)n + 1);
@@ -166,14 +201,18 @@ pdca_status host_row_ptr(const int64_t *row_ptr, int32_t n, std::vector<int64_t>
     }
     const int64_t *rp = *view;
     if (rp[0] != 0) return PDCA_ERR_INVALID_ARG;
+    int64_t mx = 0;
     for (int32_t i = 0; i < n; ++i) {
         const int64_t d = rp[i + 1] - rp[i];
         if (d < 0 || d >= (1 << 24)) return PDCA_ERR_INVALID_ARG;
+        mx = d > mx ? d : mx;
     }
+    if (max_deg) *max_deg = mx;
     return PDCA_OK;
 }
 
-pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_params &prm, Layout &L) {
+pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_params &prm, int64_t max_deg,
+                           Layout &L) {
     const int32_t sigma_req = prm.sort_window;
     L.n = n;
     L.K = K;
@@ -187,7 +226,7 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
         L.host_order = true;
         L.sigma = sigma_req && sigma_req <= kBfsBlock ? sigma_req : kBfsBlock;
         L.sell_entries = 0;
-        L.sell_cap = sell_bound(rp, n, L.sigma);
+        L.sell_cap = sell_bound(rp, n, L.sigma, max_deg);
         L.halo_cap = std::max<int64_t>(L.nnz, 1);
     } else if (sigma_req) {
         L.sigma = sigma_req;
@@ -217,6 +256,7 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     L.o_rowinfo = take(4 * np);
     L.o_perm = take(4 * np);
     L.o_iperm = take(4 * nn);
+    L.o_self = take(prm.laplacian == PDCA_LAP_UNNORMALIZED ? 4 * np : 0);
     for (int b = 0; b < 3; ++b) L.o_u[b] = take(4 * np * (size_t)K);
     L.o_part = take(8 * parts);
     L.o_red = take(sizeof(RedOut));
@@ -252,6 +292,8 @@ struct pdca_problem {
     pdca_params prm;
     double omega = 0.5;
     double lambda_used = 0.0, lambda_est = 0.0;
+    double dmax = 0.0;         // largest degree
+    float *self = nullptr;     // a_i = d_i per row (unnormalized L), else nullptr
     Coeffs cf;
     cudaStream_t stream = nullptr;
     char *ws = nullptr;
@@ -283,6 +325,7 @@ struct pdca_problem {
         A.wb = mixed ? reinterpret_cast<const __nv_bfloat16 *>(sell_w) : nullptr;
         A.slice_off = slice_off;
         A.rowinfo = rowinfo;
+        A.self = self;
         A.n_slices = L.n_slices;
         A.n = L.n;
         return A;
@@ -384,23 +427,29 @@ pdca_status reduce_energy(pdca_problem *h, double *trace_F, double *trace_r) {
     return PDCA_OK;
 }
 
+// Upper bound of lambda_max (Prop. diagonal:pre): 2 for L_s, 2 d_max for L.
+double lambda_bound(const pdca_problem *h) {
+    return h->prm.laplacian == PDCA_LAP_UNNORMALIZED ? 2.0 * h->dmax : 2.0;
+}
+
 pdca_status power_method(pdca_problem *h) {
     const SellView A = h->view();
-    const int parts = reduce_parts(A, h->tiles());
     float *x = h->U[1], *y = h->U[2];
     double *scale = h->scal, *lam = h->scal + 1;
+    unsigned *ticket = reinterpret_cast<unsigned *>(h->scal + 2);
+    PDCA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned), h->stream));
     PDCA_TRY(launch_power_init(A, h->perm, x, h->partials, h->stream));
     PDCA_TRY(launch_power_finalize(h->partials, energy_blocks(A.n_slices), scale, lam, h->stream));
     for (int it = 0; it <= h->prm.power_iters; ++it) {
-        PDCA_TRY(launch_power_spmv(A, h->tiles(), x, scale, y, h->partials, h->stream));
-        PDCA_TRY(launch_power_finalize(h->partials, parts, scale, lam, h->stream));
+        // the SpMV's last block reduces the partials and updates scale / lambda
+        PDCA_TRY(launch_power_spmv(A, h->tiles(), x, scale, y, h->partials, ticket, lam, h->stream));
         std::swap(x, y);
     }
     double lam_h = 0.0;
     PDCA_TRY(cudaMemcpyAsync(&lam_h, lam, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     PDCA_TRY(cudaStreamSynchronize(h->stream));
     h->lambda_est = lam_h;
-    h->lambda_used = std::min(2.0, 1.001 * lam_h);
+    h->lambda_used = std::min(lambda_bound(h), 1.001 * lam_h);
     return PDCA_OK;
 }
 
@@ -608,6 +657,8 @@ void pdca_default_params(pdca_params *p) {
     p->sort_window = 0;
     p->reorder = PDCA_REORDER_BFS;
     p->tiling = PDCA_TILING_AUTO;
+    p->reserved_ = 0;
+    p->step_k = 0.0;
 }
 
 const char *pdca_status_string(pdca_status s) {
@@ -639,10 +690,11 @@ pdca_status pdca_workspace_size(const int64_t *row_ptr, int32_t n, int32_t k, co
     if (st != PDCA_OK) return st;
     std::vector<int64_t> keep;
     const int64_t *rp = nullptr;
-    st = host_row_ptr(row_ptr, n, keep, &rp);
+    int64_t max_deg = 0;
+    st = host_row_ptr(row_ptr, n, keep, &rp, &max_deg);
     if (st != PDCA_OK) return st;
     Layout L;
-    st = compute_layout(rp, n, k, prm, L);
+    st = compute_layout(rp, n, k, prm, max_deg, L);
     if (st != PDCA_OK) return st;
     *bytes = L.total;
     return PDCA_OK;
@@ -661,20 +713,21 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     pdca_status st = check_params(prm);
     if (st != PDCA_OK) return st;
     const double omega = prm.damping;
-    if (prm.precond != PDCA_RICHARDSON || prm.lambda_max > 0) {
-        st = feasible(prm, omega, prm.lambda_max);
+    if (prm.laplacian == PDCA_LAP_NORMALIZED && (prm.precond != PDCA_RICHARDSON || prm.lambda_max > 0)) {
+        st = feasible(prm, omega, prm.lambda_max, 1.0);
         if (st != PDCA_OK) return st;
     }
     std::vector<int64_t> keep;
     const int64_t *rp = nullptr;
-    st = host_row_ptr(row_ptr, n, keep, &rp);
+    int64_t max_deg = 0;
+    st = host_row_ptr(row_ptr, n, keep, &rp, &max_deg);
     if (st != PDCA_OK) return st;
     const int64_t nnz = rp[n];
     if (nnz > 0 && (!col || !w)) return PDCA_ERR_INVALID_ARG;
 
     pdca_problem *h = new (std::nothrow) pdca_problem();
     if (!h) return PDCA_ERR_INVALID_ARG;
-    st = compute_layout(rp, n, k, prm, h->L);
+    st = compute_layout(rp, n, k, prm, max_deg, h->L);
     if (st != PDCA_OK) { delete h; return st; }
     if (ws_bytes < h->L.total) { delete h; return PDCA_ERR_OOM; }
     h->prm = prm;
@@ -689,6 +742,7 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     h->rowinfo = reinterpret_cast<uint32_t *>(W + L.o_rowinfo);
     h->perm = reinterpret_cast<int32_t *>(W + L.o_perm);
     h->iperm = reinterpret_cast<int32_t *>(W + L.o_iperm);
+    h->self = prm.laplacian == PDCA_LAP_UNNORMALIZED ? reinterpret_cast<float *>(W + L.o_self) : nullptr;
     for (int b = 0; b < 3; ++b) h->U[b] = reinterpret_cast<float *>(W + L.o_u[b]);
     h->mixed = prm.precision != PDCA_FP32;
     h->bf16u = prm.precision == PDCA_MIXED_BF16W_BF16U;
@@ -719,13 +773,19 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
         return fail(PDCA_ERR_CUDA);
     if (launch_validate(n, k, s_rp, s_col, s_w, s_mask, s_lab, s_deg, s_status, sm) != cudaSuccess)
         return fail(PDCA_ERR_CUDA);
-    uint32_t status = 0;
-    if (cudaMemcpyAsync(&status, s_status, 4, cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
+    uint32_t stat4[4] = {0, 0, 0, 0};
+    if (cudaMemcpyAsync(stat4, s_status, 16, cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
         cudaStreamSynchronize(sm) != cudaSuccess)
         return fail(PDCA_ERR_CUDA);
+    uint32_t status = stat4[0];
     if (status & kBadGraph) return fail(PDCA_ERR_BAD_GRAPH);
     if (status & kNotSymmetric) return fail(PDCA_ERR_NOT_SYMMETRIC);
     if (status & kIsolated) return fail(PDCA_ERR_ISOLATED_NODE);
+    std::memcpy(&h->dmax, stat4 + 2, sizeof(double));
+    if (prm.precond != PDCA_RICHARDSON || prm.lambda_max > 0) {
+        st = feasible(prm, omega, prm.lambda_max, h->dmax);
+        if (st != PDCA_OK) return fail(st);
+    }
 
     if (L.host_order) {
         st = host_renumber(h, rp, col, nnz);
@@ -742,8 +802,8 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     else
         pe = launch_pack(n, L.n_pad, k, s_rp, s_col, s_w, s_deg, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
                          h->sell_col, h->mixed ? nullptr : h->sell_w,
-                         h->mixed ? reinterpret_cast<__nv_bfloat16 *>(h->sell_w) : nullptr, h->rowinfo, s_status,
-                         sm);
+                         h->mixed ? reinterpret_cast<__nv_bfloat16 *>(h->sell_w) : nullptr, h->self, h->rowinfo,
+                         s_status, sm);
     if (pe != cudaSuccess) return fail(PDCA_ERR_CUDA);
     if (prm.precond == PDCA_RICHARDSON) {
         if (prm.lambda_max > 0) {
@@ -752,7 +812,7 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
             st = power_method(h);
             if (st != PDCA_OK) return fail(st);
         }
-        st = feasible(prm, omega, h->lambda_used);
+        st = feasible(prm, omega, h->lambda_used, h->dmax);
         if (st != PDCA_OK) return fail(st);
     }
     h->cf = make_coeffs(prm, omega, h->lambda_used);
@@ -790,11 +850,12 @@ pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t 
     if (p) prm = *p;
     pdca_status st = check_params(prm);
     if (st != PDCA_OK) return st;
-    // the shared operator fixes the weight format and the kernel form
+    // the shared operator fixes the weight format, the Laplacian and the kernel form
     if ((prm.precision != PDCA_FP32) != base->mixed) return PDCA_ERR_INVALID_ARG;
+    if (prm.laplacian != base->prm.laplacian) return PDCA_ERR_INVALID_ARG;
     const double omega = prm.damping;
     if (prm.precond != PDCA_RICHARDSON || prm.lambda_max > 0) {
-        st = feasible(prm, omega, prm.lambda_max);
+        st = feasible(prm, omega, prm.lambda_max, base->dmax);
         if (st != PDCA_OK) return st;
     }
     const CloneLayout CL = clone_layout(base->L, k, prm.precision);
@@ -812,6 +873,8 @@ pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t 
     h->slice_off = base->slice_off;
     h->perm = base->perm;
     h->iperm = base->iperm;
+    h->self = base->self;
+    h->dmax = base->dmax;
     h->tiled = base->tiled;
     h->tv = base->tv;
     h->halo_rows = base->halo_rows;
@@ -843,12 +906,12 @@ pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t 
             h->lambda_used = prm.lambda_max;
         } else if (base->lambda_est > 0) {   // same operator: reuse its estimate
             h->lambda_est = base->lambda_est;
-            h->lambda_used = std::min(2.0, 1.001 * base->lambda_est);
+            h->lambda_used = std::min(lambda_bound(h), 1.001 * base->lambda_est);
         } else {
             st = power_method(h);
             if (st != PDCA_OK) return fail(st);
         }
-        st = feasible(prm, omega, h->lambda_used);
+        st = feasible(prm, omega, h->lambda_used, h->dmax);
         if (st != PDCA_OK) return fail(st);
     }
     h->cf = make_coeffs(prm, omega, h->lambda_used);
@@ -895,7 +958,7 @@ pdca_status pdca_solve(pdca_problem *h, int32_t outer_iters, int32_t inner_sweep
                        double *energy_trace, double *residual_trace) {
     if (!h || outer_iters < 0 || inner_sweeps < 1 || !(damping >= 0.0)) return PDCA_ERR_INVALID_ARG;
     if (damping > 0.0 && h->prm.precond == PDCA_JACOBI_DAMPED && damping != h->omega) {
-        pdca_status st = feasible(h->prm, damping, h->lambda_used);
+        pdca_status st = feasible(h->prm, damping, h->lambda_used, h->dmax);
         if (st != PDCA_OK) return st;
         h->omega = damping;
         h->prm.damping = damping;
@@ -1033,29 +1096,30 @@ pdca_status pdca_batch_add(pdca_batch *b, pdca_problem *h, int32_t outer_iters, 
 pdca_status pdca_batch_step(pdca_batch *b, int32_t passes, int32_t *active_after) {
     if (!b || passes < 0) return PDCA_ERR_INVALID_ARG;
     for (int32_t p = 0; p < passes && !b->members.empty(); ++p) {
-        // one launch per K class (and per kBatchMax members)
-        bool used[PDCA_MAX_K + 1] = {};
-        for (const BatchMember &m : b->members) used[m.h->L.K] = true;
-        for (int K = 1; K <= PDCA_MAX_K; ++K) {
-            if (!used[K]) continue;
-            BatchTable &t = b->table;
-            t.n = 0;
-            t.total_slices = 0;
-            for (size_t i = 0; i < b->members.size(); ++i) {
-                const BatchMember &m = b->members[i];
-                if (m.h->L.K != K) continue;
-                BatchDesc &d = t.d[t.n++];
-                member_desc(m, d);
-                d.slice_begin = t.total_slices;
-                t.total_slices += m.h->L.n_slices;
-                if (t.n == kBatchMax) {
-                    PDCA_TRY(launch_batch_pass(K, t, b->stream));
-                    t.n = 0;
-                    t.total_slices = 0;
+        // one launch per class (K, Laplacian) and per kBatchMax members
+        bool used[2][PDCA_MAX_K + 1] = {};
+        for (const BatchMember &m : b->members) used[m.h->self ? 1 : 0][m.h->L.K] = true;
+        for (int un = 0; un < 2; ++un)
+            for (int K = 1; K <= PDCA_MAX_K; ++K) {
+                if (!used[un][K]) continue;
+                BatchTable &t = b->table;
+                t.n = 0;
+                t.total_slices = 0;
+                for (size_t i = 0; i < b->members.size(); ++i) {
+                    const BatchMember &m = b->members[i];
+                    if (m.h->L.K != K || (m.h->self ? 1 : 0) != un) continue;
+                    BatchDesc &d = t.d[t.n++];
+                    member_desc(m, d);
+                    d.slice_begin = t.total_slices;
+                    t.total_slices += m.h->L.n_slices;
+                    if (t.n == kBatchMax) {
+                        PDCA_TRY(launch_batch_pass(K, un == 1, t, b->stream));
+                        t.n = 0;
+                        t.total_slices = 0;
+                    }
                 }
+                PDCA_TRY(launch_batch_pass(K, un == 1, t, b->stream));
             }
-            PDCA_TRY(launch_batch_pass(K, t, b->stream));
-        }
         std::vector<BatchMember> keep;
         keep.reserve(b->members.size());
         for (BatchMember &m : b->members) {

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <vector>
 
 #include "pdca.h"
@@ -40,12 +41,15 @@ constexpr uint32_t kNotSymmetric = 2u;
 constexpr uint32_t kIsolated = 4u;
 constexpr uint32_t kLayoutMismatch = 8u;   // internal: packed row longer than its slice
 
+// The Laplacian as (L x)_i = a_i x_i - sum_j w'_ij x_j:  L_s has a_i = 1 and
+// w' = w_ij / sqrt(d_i d_j);  L = D - W has a_i = d_i and w' = w_ij.
 struct SellView {
     const int32_t *col;        // padded sliced-ELL column indices (new numbering)
-    const float *w;            // w_ij / sqrt(d_i d_j), FP32 (FP32 path)
+    const float *w;            // w'_ij, FP32 (FP32 path)
     const __nv_bfloat16 *wb;   // the same in BF16 (mixed-precision path)
     const int64_t *slice_off;  // n_slices + 1 entry offsets
     const uint32_t *rowinfo;   // (len << 8) | tag, n_pad
+    const float *self;         // a_i = d_i per row (n_pad) for L; nullptr for L_s
     int32_t n_slices;
     int32_t n;                 // real rows; rows >= n are padding
 };
@@ -77,10 +81,13 @@ struct TileView {
                                // through halo_idx from global memory instead
 };
 
-// Scalars of one sweep (Sec. 3): T = eps L_s + eta Lambda + c I and the two
-// values of 1/g_i (unlabelled, labelled rows).
+// Scalars of one sweep (Sec. 3): T = eps L + eta Lambda + c I (c already
+// holds c + 1/k for a finite step size k) and the preconditioner
+// g_i = alpha a_i + beta_{Lambda_i}; for L_s (a_i = 1) the two values of
+// 1/g_i (unlabelled, labelled rows) are precomputed.
 struct Coeffs {
     float eps, inv_eps, c, eta, inv_g0, inv_g1;
+    float alpha, beta0, beta1;
 };
 
 // Reduction results written by finalize kernels.
@@ -94,6 +101,7 @@ struct RedOut {
 // --- sweep / reductions (sweep_kernels.cu) ---------------------------------
 // T == nullptr selects the plain kernels (neighbour rows gathered from global
 // memory through L1/L2); otherwise the tiled kernels (halo in shared memory).
+// A.self != nullptr (unnormalized L) needs T == nullptr.
 cudaError_t launch_sweep(int K, bool project, const SellView &A, const TileView *T, const Coeffs &cf,
                          const float *v_src, const float *u_t, float *v_dst, cudaStream_t st);
 cudaError_t launch_energy(int K, const SellView &A, const TileView *T, const Coeffs &cf, const float *u,
@@ -109,8 +117,11 @@ cudaError_t launch_energy_finalize(const double *partials, int n_parts, double e
                                    double *trace_r, cudaStream_t st);
 cudaError_t launch_power_init(const SellView &A, const int32_t *perm, float *x,
                               double *partials, cudaStream_t st);
-cudaError_t launch_power_spmv(const SellView &A, const TileView *T, const float *x, const double *scale,
-                              float *y, double *partials, cudaStream_t st);
+// y = L_s (s x); the block that finishes last (ticket counter, reset to 0 by
+// it) sums the block partials in a fixed order and writes scale = 1/||y|| and
+// lambda = Rayleigh quotient of s x (no separate finalize launch).
+cudaError_t launch_power_spmv(const SellView &A, const TileView *T, const float *x, double *scale,
+                              float *y, double *partials, unsigned *ticket, double *lambda, cudaStream_t st);
 cudaError_t launch_power_finalize(const double *partials, int n_parts, double *scale,
                                   double *lambda, cudaStream_t st);
 cudaError_t launch_labels(int K, int32_t n, const float *u, const int32_t *perm,
@@ -124,6 +135,13 @@ cudaError_t launch_mixed_residual(int K, bool bf16u, bool last, bool project, co
 cudaError_t launch_mixed_sweep(int K, bool bf16u, bool last, bool project, const SellView &A, const Coeffs &cf,
                                const void *e_src, const void *r, void *e_dst, const float *u, float *u_out,
                                cudaStream_t st);
+// the instances for the unnormalized Laplacian (mixed_kernels_un.cu)
+cudaError_t launch_mixed_residual_un(int K, bool bf16u, bool last, bool project, const SellView &A,
+                                     const Coeffs &cf, const float *u, void *r, void *e, float *u_out,
+                                     cudaStream_t st);
+cudaError_t launch_mixed_sweep_un(int K, bool bf16u, bool last, bool project, const SellView &A,
+                                  const Coeffs &cf, const void *e_src, const void *r, void *e_dst, const float *u,
+                                  float *u_out, cudaStream_t st);
 cudaError_t launch_permute_out(int K, int32_t n, const float *u, const int32_t *perm,
                                float *out, cudaStream_t st);
 cudaError_t launch_permute_in(int K, int32_t n, int32_t n_pad, const float *in,
@@ -157,26 +175,36 @@ struct BatchTable {
     int32_t total_slices;
     BatchDesc d[kBatchMax];
 };
-cudaError_t launch_batch_pass(int K, const BatchTable &t, cudaStream_t st);
+// un: the table holds problems on the unnormalized Laplacian (A.self set).
+cudaError_t launch_batch_pass(int K, bool un, const BatchTable &t, cudaStream_t st);
+cudaError_t launch_batch_pass_un(int K, const BatchTable &t, cudaStream_t st);
 
 // --- preparation (prep_kernels.cu) -----------------------------------------
+// status[0]: kBadGraph | kNotSymmetric | kIsolated bits; status[2..3]: the
+// largest degree as the bits of a double (status must start zeroed).
 cudaError_t launch_validate(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *col,
                             const float *w, const uint8_t *mask, const int32_t *labels,
                             double *deg, uint32_t *status, cudaStream_t st);
 cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const int64_t *row_ptr,
                                int32_t *perm, int32_t *iperm, cudaStream_t st);
+// self == nullptr: L_s weights w_ij / sqrt(d_i d_j); else L weights w_ij and
+// self[r] = d_i (0 on padding rows).
 cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_ptr,
                         const int32_t *col, const float *w, const double *deg,
                         const uint8_t *mask, const int32_t *labels, const int32_t *perm,
                         const int32_t *iperm, const int64_t *slice_off, int32_t *sell_col,
-                        float *sell_w, __nv_bfloat16 *sell_wb, uint32_t *rowinfo, uint32_t *status,
-                        cudaStream_t st);
+                        float *sell_w, __nv_bfloat16 *sell_wb, float *self, uint32_t *rowinfo,
+                        uint32_t *status, cudaStream_t st);
 // tiled form: local 16-bit columns (position in the tile's halo) instead of int32
 cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32_t *col, const float *w,
                               const double *deg, const uint8_t *mask, const int32_t *labels,
                               const int32_t *perm, const int32_t *iperm, const int64_t *slice_off,
                               const int64_t *halo_off, const int32_t *halo_idx, uint16_t *lcol,
                               float *sell_w, uint32_t *rowinfo, uint32_t *status, cudaStream_t st);
+
+// f(0) .. f(count - 1) on the host's threads (index order per thread is
+// fixed, so results written per index do not depend on the thread count).
+void host_parallel_for(int64_t count, const std::function<void(int64_t)> &f);
 
 // --- host symbolic analysis (reorder.cpp) ------------------------------------
 // order[new] = old: BFS blocks of `block` nodes inside fixed chunks of `chunk`

@@ -3,7 +3,8 @@
 //                       columns, finite non-negative weights, w_ij == w_ji)
 //                       and the degrees d_i = sum_j w_ij (FP64, CSR order);
 //   window_sort_kernel  renumbering: rows sorted by degree inside windows;
-//   pack_kernel         sliced-ELL with w_ij / sqrt(d_i d_j) and the row tags;
+//   pack_kernel         sliced-ELL with w_ij / sqrt(d_i d_j) (L_s) or w_ij plus
+//                       the per-row d_i (L), and the row tags;
 //   init_u_kernel       u^0 (prior on labelled rows, centre elsewhere).
 #include "pdca_internal.cuh"
 
@@ -59,6 +60,8 @@ __global__ void validate_kernel(int32_t n, int32_t K, const int64_t *__restrict_
     }
     deg[i] = d;
     if (bad) atomicOr(status, bad);
+    // non-negative doubles order like their bit patterns
+    atomicMax(reinterpret_cast<unsigned long long *>(status + 2), (unsigned long long)__double_as_longlong(d));
 }
 
 // One block per window of `sigma` rows: bitonic sort of keys
@@ -115,8 +118,8 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
                             const int32_t *__restrict__ labels, const int32_t *__restrict__ perm,
                             const int32_t *__restrict__ iperm, const int64_t *__restrict__ slice_off,
                             int32_t *__restrict__ sell_col, float *__restrict__ sell_w,
-                            __nv_bfloat16 *__restrict__ sell_wb, uint32_t *__restrict__ rowinfo,
-                            uint32_t *__restrict__ status) {
+                            __nv_bfloat16 *__restrict__ sell_wb, float *__restrict__ self,
+                            uint32_t *__restrict__ rowinfo, uint32_t *__restrict__ status) {
     const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_pad) return;
     const int32_t s = r >> 5, lane = r & 31;
@@ -133,15 +136,18 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
             len = width;
         }
         const double di = deg[old];
+        if (self) self[r] = (float)di;
         for (int32_t j = 0; j < len; ++j) {
             const int32_t oj = col[e0 + j];
             const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
             sell_col[at] = iperm[oj];
-            const double wt = (double)w[e0 + j] / sqrt(di * deg[oj]);
+            const double wt = self ? (double)w[e0 + j] : (double)w[e0 + j] / sqrt(di * deg[oj]);
             if (sell_wb) sell_wb[at] = __double2bfloat16(wt);
             else sell_w[at] = (float)wt;
         }
         if (mask[old]) tag = (uint32_t)labels[old];
+    } else if (self) {
+        self[r] = 0.0f;
     }
     for (int32_t j = len; j < width; ++j) {
         const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
@@ -278,14 +284,14 @@ cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const in
 cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_ptr, const int32_t *col,
                         const float *w, const double *deg, const uint8_t *mask, const int32_t *labels,
                         const int32_t *perm, const int32_t *iperm, const int64_t *slice_off,
-                        int32_t *sell_col, float *sell_w, __nv_bfloat16 *sell_wb, uint32_t *rowinfo,
-                        uint32_t *status, cudaStream_t st) {
+                        int32_t *sell_col, float *sell_w, __nv_bfloat16 *sell_wb, float *self,
+                        uint32_t *rowinfo, uint32_t *status, cudaStream_t st) {
     (void)n;
     (void)K;
     count_launches(1);
     pack_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, mask, labels, perm,
-                                                     iperm, slice_off, sell_col, sell_w, sell_wb, rowinfo,
-                                                     status);
+                                                     iperm, slice_off, sell_col, sell_w, sell_wb, self,
+                                                     rowinfo, status);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@
 #include "pdca_internal.cuh"
 
 #include <algorithm>
+#include <functional>
 #include <thread>
 #include <vector>
 
@@ -87,6 +88,8 @@ void chunk_blocks(int64_t c0, int64_t c1, const int64_t *rp, const int32_t *col,
 }
 
 }  // namespace
+
+void host_parallel_for(int64_t count, const std::function<void(int64_t)> &f) { parallel_for(count, f); }
 
 void locality_order(int32_t n, const int64_t *rp, const int32_t *col, int32_t block, int32_t chunk,
                     int32_t sort_window, int32_t *order) {

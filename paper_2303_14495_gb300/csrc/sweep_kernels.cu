@@ -29,8 +29,10 @@ using namespace dev;
 // fused sweep
 // ---------------------------------------------------------------------------
 //   b    = eta Lambda_i y_i + c u_i - (u_i^3 - u_i)/eps          (u = u^t)
-//   Tv   = eps (v_i - sum_j wt_ij v_j) + (c + eta Lambda_i) v_i
-//   v'_i = v_i + (b - Tv) / g_i,   then projected if PROJECT.
+//   Tv   = eps (a_i v_i - sum_j w'_ij v_j) + (c + eta Lambda_i) v_i
+//   v'_i = v_i + (b - Tv) / g_i,   then projected if PROJECT
+// (a_i = 1 and w' = w / sqrt(d_i d_j) for L_s; a_i = d_i and w' = w for L,
+// the UN instances).
 //
 // Latency hiding: the loads that depend on nothing (the row tag and length,
 // the own rows of v^s and u^t, the first two entry groups) are issued first,
@@ -39,13 +41,13 @@ using namespace dev;
 
 // plain form: one warp per slice, 8 slices per block (the same slice body as
 // the batched kernel)
-template <int K, bool PROJECT>
+template <int K, bool PROJECT, bool UN>
 __global__ void __launch_bounds__(kBlockThreads, 4)
 sweep_kernel(const SellView A, const Coeffs cf, const float *__restrict__ v_src,
              const float *__restrict__ u_t, float *__restrict__ v_dst) {
     const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (slice >= A.n_slices) return;
-    fp32_sweep_slice<K, PROJECT>(A, cf, slice, threadIdx.x & 31, v_src, u_t, v_dst);
+    fp32_sweep_slice<K, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, v_src, u_t, v_dst);
 }
 
 // tiled form: one block per tile of 16 slices (one per warp); the halo of
@@ -70,20 +72,14 @@ sweep_tiled_kernel(const SellView A, const TileView T, const Coeffs cf, const fl
     float acc[K];
     if (staged) slice_gather<K, kShared>(s, v_src, hs, nullptr, acc);
     else slice_gather<K, kIndirect>(s, v_src, nullptr, T.halo_idx + h0, acc);
-    sweep_update<K, PROJECT>(cf, s.info, acc, s.v, s.u, v_dst + (size_t)(slice * kSliceRows + lane) * K);
+    sweep_update<K, PROJECT>(cf, s.info, 1.0f, acc, s.v, s.u, v_dst + (size_t)(slice * kSliceRows + lane) * K);
 }
 
 // ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
 // Per-row contributions (FP32 inside a row and a warp, FP64 across warps):
-//   quad += u_i . (L_s u)_i,  well += sum_k (u_ik^2 - 1)^2,
+//   quad += u_i . (L u)_i  (L_s or L: a_i u_i - sum_j w'_ij u_j),  well += sum_k (u_ik^2 - 1)^2,
 //   fid  += Lambda_i sum_k (u_ik - y_ik)^2,
 //   rr   += ||b_i - (T u)_i||^2 with b from u_prev, bb += ||b_i||^2.
 // b - T u is formed as c (u_prev - u) + eta Lambda (y - u)
@@ -96,6 +92,7 @@ __device__ __forceinline__ void energy_row(const SellView &A, const Coeffs &cf, 
     const int r = slice * kSliceRows + lane;
     if (r >= A.n) return;
     const uint32_t info = A.rowinfo[r];
+    const float a = A.self ? A.self[r] : 1.0f;
     float x[K];
     load_row<K>(u + (size_t)r * K, x);
     const uint32_t tag = info & 0xFFu;
@@ -105,7 +102,7 @@ __device__ __forceinline__ void energy_row(const SellView &A, const Coeffs &cf, 
     if (u_prev) load_row<K>(u_prev + (size_t)r * K, xp);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const float ls = x[k] - acc[k];
+        const float ls = a * x[k] - acc[k];
         q = fmaf(x[k], ls, q);
         const float s = x[k] * x[k] - 1.0f;
         wl = fmaf(s, s, wl);
@@ -194,6 +191,52 @@ energy_finalize_kernel(const double *__restrict__ partials, int n_parts, double 
     }
 }
 
+// scale <- 1/sqrt(sum y.y); lambda <- sum (s x).y / sum (s x).(s x).
+// Fixed-order sum over the partials by the NT threads of one block (a
+// 256-thread block: the finalize kernel, or the last block of an SpMV).
+template <int NT>
+__device__ __forceinline__ void power_reduce(const double *partials, int n_parts, double *scale, double *lambda) {
+    __shared__ double sm[NT][3];
+    double t[3] = {0, 0, 0};
+    for (int i = threadIdx.x; i < n_parts; i += NT)
+#pragma unroll
+        for (int s = 0; s < 3; ++s) t[s] += __ldcg(partials + (size_t)i * kRedSlots + s);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) sm[threadIdx.x][s] = t[s];
+    __syncthreads();
+    for (int h = NT / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+#pragma unroll
+            for (int s = 0; s < 3; ++s) sm[threadIdx.x][s] += sm[threadIdx.x + h][s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double yy = sm[0][0], xy = sm[0][1], xx = sm[0][2];
+        *scale = yy > 0.0 ? 1.0 / sqrt(yy) : 0.0;
+        *lambda = xx > 0.0 ? xy / xx : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+power_finalize_kernel(const double *__restrict__ partials, int n_parts, double *scale, double *lambda) {
+    power_reduce<256>(partials, n_parts, scale, lambda);
+}
+
+// After the block's partial is stored: the last block to arrive reduces.
+template <int NT>
+__device__ __forceinline__ void power_last_block(const double *partials, unsigned *ticket, double *scale,
+                                                 double *lambda) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    power_reduce<NT>(partials, gridDim.x, scale, lambda);
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
 // ---------------------------------------------------------------------------
 // power method for lambda_max(L_s)
 // ---------------------------------------------------------------------------
@@ -213,13 +256,14 @@ power_init_kernel(const SellView A, const int32_t *__restrict__ perm, float *__r
     block_sum_store<3>(red, partials + (size_t)blockIdx.x * kRedSlots);
 }
 
-// y = L_s (s x) with s = *scale; partial sums of y.y, (s x).y, (s x).(s x).
+// y = L (s x) with s = *scale (L_s, or L when A.self holds d_i); partial sums
+// of y.y, (s x).y, (s x).(s x).
 __device__ __forceinline__ void power_row(const SellView &A, int slice, int lane, float acc, float s,
                                           const float *__restrict__ x, float *__restrict__ y,
                                           float (&red)[3]) {
     const int r = slice * kSliceRows + lane;
     const float xs = s * __ldg(x + r);
-    const float yi = xs - s * acc;
+    const float yi = (A.self ? __ldg(A.self + r) : 1.0f) * xs - s * acc;
     y[r] = yi;
     if (r < A.n) {
         red[0] = fmaf(yi, yi, red[0]);
@@ -230,8 +274,8 @@ __device__ __forceinline__ void power_row(const SellView &A, int slice, int lane
 
 template <class WT>
 __global__ void __launch_bounds__(kBlockThreads)
-power_spmv_kernel(const SellView A, const float *__restrict__ x, const double *__restrict__ scale,
-                  float *__restrict__ y, double *__restrict__ partials) {
+power_spmv_kernel(const SellView A, const float *__restrict__ x, double *scale, float *__restrict__ y,
+                  double *__restrict__ partials, unsigned *ticket, double *lambda) {
     const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     float red[3] = {0.f, 0.f, 0.f};
@@ -239,14 +283,15 @@ power_spmv_kernel(const SellView A, const float *__restrict__ x, const double *_
         const int64_t base = A.slice_off[slice];
         float acc[1];
         gather_row_sum<1, WT, float>(A, base, row_len(A, slice, lane), lane, x, acc);
-        power_row(A, slice, lane, acc[0], (float)(*scale), x, y, red);
+        power_row(A, slice, lane, acc[0], (float)__ldcg(scale), x, y, red);
     }
     block_sum_store<3>(red, partials + (size_t)blockIdx.x * kRedSlots);
+    power_last_block<kBlockThreads>(partials, ticket, scale, lambda);
 }
 
 __global__ void __launch_bounds__(kTileThreads, PDCA_TILE_MIN_BLOCKS)
-power_spmv_tiled_kernel(const SellView A, const TileView T, const float *__restrict__ x,
-                        const double *__restrict__ scale, float *__restrict__ y, double *__restrict__ partials) {
+power_spmv_tiled_kernel(const SellView A, const TileView T, const float *__restrict__ x, double *scale,
+                        float *__restrict__ y, double *__restrict__ partials, unsigned *ticket, double *lambda) {
     extern __shared__ float4 smem_f4[];
     float *hs = reinterpret_cast<float *>(smem_f4);
     const int tile = blockIdx.x;
@@ -255,7 +300,7 @@ power_spmv_tiled_kernel(const SellView A, const TileView T, const float *__restr
     if (staged) load_halo<1>(T, tile, x, hs);
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const float s = (float)(*scale);
+    const float s = (float)__ldcg(scale);
     float red[3] = {0.f, 0.f, 0.f};
     for (int sl = threadIdx.x >> 5; sl < kTileSlices; sl += kTileThreads / 32) {
         const int slice = tile * kTileSlices + sl;
@@ -266,31 +311,7 @@ power_spmv_tiled_kernel(const SellView A, const TileView T, const float *__restr
         power_row(A, slice, lane, acc[0], s, x, y, red);
     }
     block_sum_store<3, kTileThreads / 32>(red, partials + (size_t)blockIdx.x * kRedSlots);
-}
-
-// scale <- 1/sqrt(sum y.y); lambda <- sum (s x).y / sum (s x).(s x)
-__global__ void __launch_bounds__(256)
-power_finalize_kernel(const double *__restrict__ partials, int n_parts, double *scale,
-                      double *lambda) {
-    __shared__ double sm[256][3];
-    double t[3] = {0, 0, 0};
-    for (int i = threadIdx.x; i < n_parts; i += 256)
-#pragma unroll
-        for (int s = 0; s < 3; ++s) t[s] += partials[(size_t)i * kRedSlots + s];
-#pragma unroll
-    for (int s = 0; s < 3; ++s) sm[threadIdx.x][s] = t[s];
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if (threadIdx.x < h)
-#pragma unroll
-            for (int s = 0; s < 3; ++s) sm[threadIdx.x][s] += sm[threadIdx.x + h][s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double yy = sm[0][0], xy = sm[0][1], xx = sm[0][2];
-        *scale = yy > 0.0 ? 1.0 / sqrt(yy) : 0.0;
-        *lambda = xx > 0.0 ? xy / xx : 0.0;
-    }
+    power_last_block<kTileThreads>(partials, ticket, scale, lambda);
 }
 
 // ---------------------------------------------------------------------------
@@ -349,6 +370,7 @@ cudaError_t sweep_k(bool project, const SellView &A, const TileView *T, const Co
                     const float *u_t, float *v_dst, cudaStream_t st) {
     constexpr bool P = K >= 2;
     if (T) {
+        if (A.self) return cudaErrorInvalidValue;   // the tiled kernels are L_s only
         const size_t sm = tile_smem_bytes(K, T->smem_rows);
         if (project && P) {
             cudaError_t e = allow_smem(sweep_tiled_kernel<K, P>, sm);
@@ -362,10 +384,13 @@ cudaError_t sweep_k(bool project, const SellView &A, const TileView *T, const Co
         return cudaGetLastError();
     }
     const int blocks = (A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (project && P)
-        sweep_kernel<K, P><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
-    else
-        sweep_kernel<K, false><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
+    if (A.self) {
+        if (project && P) sweep_kernel<K, P, true><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
+        else sweep_kernel<K, false, true><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
+    } else {
+        if (project && P) sweep_kernel<K, P, false><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
+        else sweep_kernel<K, false, false><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
+    }
     return cudaGetLastError();
 }
 
@@ -444,20 +469,22 @@ cudaError_t launch_power_init(const SellView &A, const int32_t *perm, float *x, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_power_spmv(const SellView &A, const TileView *T, const float *x, const double *scale,
-                              float *y, double *partials, cudaStream_t st) {
+cudaError_t launch_power_spmv(const SellView &A, const TileView *T, const float *x, double *scale, float *y,
+                              double *partials, unsigned *ticket, double *lambda, cudaStream_t st) {
     count_launches(1);
     if (T) {
         const size_t sm = tile_smem_bytes(1, T->smem_rows);
         cudaError_t e = allow_smem(power_spmv_tiled_kernel, sm);
         if (e != cudaSuccess) return e;
-        power_spmv_tiled_kernel<<<T->n_tiles, kTileThreads, sm, st>>>(A, *T, x, scale, y, partials);
+        power_spmv_tiled_kernel<<<T->n_tiles, kTileThreads, sm, st>>>(A, *T, x, scale, y, partials, ticket,
+                                                                        lambda);
     } else {
         if (A.wb)
-            power_spmv_kernel<__nv_bfloat16><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, x, scale, y,
-                                                                                                partials);
+            power_spmv_kernel<__nv_bfloat16><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(
+                A, x, scale, y, partials, ticket, lambda);
         else
-            power_spmv_kernel<float><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, x, scale, y, partials);
+            power_spmv_kernel<float><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, x, scale, y, partials,
+                                                                                        ticket, lambda);
     }
     return cudaGetLastError();
 }

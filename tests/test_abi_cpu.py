@@ -93,9 +93,12 @@ def test_create_rejects_before_device_work(B):
     st, h = B.pdca_create(rp, col, w, 64, 1, mask, lab,
                           P(precond=B.PDCA_JACOBI_PERTURBED, delta0=0.0), C.c_void_p(addr), 1 << 16, 0)
     assert st == 4
-    # unimplemented unnormalized Laplacian / negative eps / unaligned workspace
-    st, _ = B.pdca_create(rp, col, w, 64, 1, mask, lab, P(laplacian=1), C.c_void_p(addr), 1 << 16, 0)
-    assert st == 1
+    # unknown Laplacian, tiled unnormalized Laplacian, bad step size / negative
+    # eps / unaligned workspace
+    for bad in (P(laplacian=2), P(laplacian=1, tiling=B.PDCA_TILING_ON), P(step_k=-1.0),
+                P(step_k=float("nan")), P(step_k=float("inf"))):
+        st, _ = B.pdca_create(rp, col, w, 64, 1, mask, lab, bad, C.c_void_p(addr), 1 << 16, 0)
+        assert st == 1
     st, _ = B.pdca_create(rp, col, w, 64, 1, mask, lab, P(eps=-1.0), C.c_void_p(addr), 1 << 16, 0)
     assert st == 1
     st, _ = B.pdca_create(rp, col, w, 64, 1, mask, lab, P(), C.c_void_p(addr + 8), 1 << 16, 0)
