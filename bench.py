@@ -106,14 +106,23 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def sweep_source_sha1():
+    """Hash of the sources that define the fused sweep kernel."""
+    csrc = os.path.join(ROOT, "paper_2303_14495_gb300", "csrc")
+    sha = hashlib.sha1()
+    for name in ("sweep_kernels.cu", "device_common.cuh", "pdca_internal.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            sha.update(f.read())
+    return sha.hexdigest()[:12]
+
+
 def sweep_traffic_record():
     """DRAM bytes per sweep launch from the committed ncu summary, valid only
     while the kernel source is unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "sweep_voronoi2048_traffic.txt")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, "paper_2303_14495_gb300", "csrc", "sweep_kernels.cu")
-    h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    h = sweep_source_sha1()
     rec = {}
     for line in open(path):
         if ":" in line:

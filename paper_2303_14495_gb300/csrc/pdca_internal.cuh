@@ -54,6 +54,18 @@ struct SellView {
     int32_t n;                 // real rows; rows >= n are padding
 };
 
+// Resident blocks per SM the plain sweep is compiled for (registers per
+// thread <= 65536 / (256 x blocks)).
+#ifndef PDCA_SWEEP_MIN_BLOCKS
+#define PDCA_SWEEP_MIN_BLOCKS 4
+#endif
+// Consecutive groups of 8 slices one block of the plain sweep handles in
+// turn (neighbouring slices of the renumbering share most neighbour rows, so
+// later groups can find them in the same SM's L1).
+#ifndef PDCA_SWEEP_ITERS
+#define PDCA_SWEEP_ITERS 1
+#endif
+
 // Tiled form of the operator: tiles of kTileSlices slices; each tile lists
 // the distinct rows its entries reference (its halo, sorted), and every entry
 // stores the position of its column in that list (16 bits).  The tiled

@@ -20,6 +20,8 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 namespace pdca {
 namespace {
 
@@ -42,12 +44,16 @@ using namespace dev;
 // plain form: one warp per slice, 8 slices per block (the same slice body as
 // the batched kernel)
 template <int K, bool PROJECT, bool UN>
-__global__ void __launch_bounds__(kBlockThreads, 4)
+__global__ void __launch_bounds__(kBlockThreads, PDCA_SWEEP_MIN_BLOCKS)
 sweep_kernel(const SellView A, const Coeffs cf, const float *__restrict__ v_src,
              const float *__restrict__ u_t, float *__restrict__ v_dst) {
-    const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (slice >= A.n_slices) return;
-    fp32_sweep_slice<K, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, v_src, u_t, v_dst);
+    const int first = blockIdx.x * kWarpsPerBlock * PDCA_SWEEP_ITERS + (threadIdx.x >> 5);
+#pragma unroll 1
+    for (int it = 0; it < PDCA_SWEEP_ITERS; ++it) {
+        const int slice = first + it * kWarpsPerBlock;
+        if (slice >= A.n_slices) return;
+        fp32_sweep_slice<K, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, v_src, u_t, v_dst);
+    }
 }
 
 // tiled form: one block per tile of 16 slices (one per warp); the halo of
@@ -227,7 +233,9 @@ template <int NT>
 __device__ __forceinline__ void power_last_block(const double *partials, unsigned *ticket, double *scale,
                                                  double *lambda) {
     __shared__ bool last;
-    __threadfence();
+    // the partial was stored by threads of warp 0 (block_sum_store): only
+    // they fence, the other threads' stores of y need not drain first
+    if (threadIdx.x < 32) __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     __syncthreads();
@@ -280,9 +288,15 @@ power_spmv_kernel(const SellView A, const float *__restrict__ x, double *scale, 
     const int lane = threadIdx.x & 31;
     float red[3] = {0.f, 0.f, 0.f};
     if (slice < A.n_slices) {
-        const int64_t base = A.slice_off[slice];
         float acc[1];
-        gather_row_sum<1, WT, float>(A, base, row_len(A, slice, lane), lane, x, acc);
+        if constexpr (std::is_same<WT, float>::value) {
+            // the sweeps' pipelined slice body (same summation order)
+            SliceRow<1, int4> sr;
+            slice_prologue<1>(A, reinterpret_cast<const int4 *>(A.col), slice, lane, x, x, sr);
+            slice_gather<1, kGlobal>(sr, x, nullptr, nullptr, acc);
+        } else {
+            gather_row_sum<1, WT, float>(A, A.slice_off[slice], row_len(A, slice, lane), lane, x, acc);
+        }
         power_row(A, slice, lane, acc[0], (float)__ldcg(scale), x, y, red);
     }
     block_sum_store<3>(red, partials + (size_t)blockIdx.x * kRedSlots);
@@ -383,7 +397,8 @@ cudaError_t sweep_k(bool project, const SellView &A, const TileView *T, const Co
         }
         return cudaGetLastError();
     }
-    const int blocks = (A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int per_block = kWarpsPerBlock * PDCA_SWEEP_ITERS;
+    const int blocks = (A.n_slices + per_block - 1) / per_block;
     if (A.self) {
         if (project && P) sweep_kernel<K, P, true><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
         else sweep_kernel<K, false, true><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
