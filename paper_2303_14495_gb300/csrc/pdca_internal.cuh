@@ -59,12 +59,20 @@ struct SellView {
 #ifndef PDCA_SWEEP_MIN_BLOCKS
 #define PDCA_SWEEP_MIN_BLOCKS 4
 #endif
-// Consecutive groups of 8 slices one block of the plain sweep handles in
-// turn (neighbouring slices of the renumbering share most neighbour rows, so
-// later groups can find them in the same SM's L1).
-#ifndef PDCA_SWEEP_ITERS
-#define PDCA_SWEEP_ITERS 1
+// A block of the plain sweep handles up to this many consecutive groups of 8
+// slices in turn (neighbouring slices of the renumbering share most neighbour
+// rows, so later groups find many of them in the same SM's L1); fewer when
+// the graph is too small to keep every SM busy for several waves.
+#ifndef PDCA_SWEEP_MAX_ITERS
+#define PDCA_SWEEP_MAX_ITERS 4
 #endif
+constexpr int kSmCount = 152;   // GB300
+// slice groups per block for a graph of n_slices slices (at least 4 waves)
+inline int sweep_iters(int32_t n_slices) {
+    const int groups = (n_slices + 7) / 8;
+    const int it = groups / (4 * kSmCount * PDCA_SWEEP_MIN_BLOCKS);
+    return it < 1 ? 1 : (it > PDCA_SWEEP_MAX_ITERS ? PDCA_SWEEP_MAX_ITERS : it);
+}
 
 // Tiled form of the operator: tiles of kTileSlices slices; each tile lists
 // the distinct rows its entries reference (its halo, sorted), and every entry

@@ -20,6 +20,7 @@
 
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 
 namespace pdca {
@@ -46,10 +47,10 @@ using namespace dev;
 template <int K, bool PROJECT, bool UN>
 __global__ void __launch_bounds__(kBlockThreads, PDCA_SWEEP_MIN_BLOCKS)
 sweep_kernel(const SellView A, const Coeffs cf, const float *__restrict__ v_src,
-             const float *__restrict__ u_t, float *__restrict__ v_dst) {
-    const int first = blockIdx.x * kWarpsPerBlock * PDCA_SWEEP_ITERS + (threadIdx.x >> 5);
+             const float *__restrict__ u_t, float *__restrict__ v_dst, int iters) {
+    const int first = blockIdx.x * kWarpsPerBlock * iters + (threadIdx.x >> 5);
 #pragma unroll 1
-    for (int it = 0; it < PDCA_SWEEP_ITERS; ++it) {
+    for (int it = 0; it < iters; ++it) {
         const int slice = first + it * kWarpsPerBlock;
         if (slice >= A.n_slices) return;
         fp32_sweep_slice<K, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, v_src, u_t, v_dst);
@@ -397,14 +398,16 @@ cudaError_t sweep_k(bool project, const SellView &A, const TileView *T, const Co
         }
         return cudaGetLastError();
     }
-    const int per_block = kWarpsPerBlock * PDCA_SWEEP_ITERS;
-    const int blocks = (A.n_slices + per_block - 1) / per_block;
+    // keep at least 4 waves of resident blocks
+    const int groups = (A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int iters = sweep_iters(A.n_slices);
+    const int blocks = (groups + iters - 1) / iters;
     if (A.self) {
-        if (project && P) sweep_kernel<K, P, true><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
-        else sweep_kernel<K, false, true><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
+        if (project && P) sweep_kernel<K, P, true><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst, iters);
+        else sweep_kernel<K, false, true><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst, iters);
     } else {
-        if (project && P) sweep_kernel<K, P, false><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
-        else sweep_kernel<K, false, false><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst);
+        if (project && P) sweep_kernel<K, P, false><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst, iters);
+        else sweep_kernel<K, false, false><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst, iters);
     }
     return cudaGetLastError();
 }
