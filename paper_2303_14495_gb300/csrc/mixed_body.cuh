@@ -12,59 +12,49 @@ using namespace dev;
 template <int K, class HT, bool LAST, bool PROJECT, bool UN>
 __global__ void __launch_bounds__(kBlockThreads)
 mixed_residual_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u, HT *__restrict__ r_out,
-                      HT *__restrict__ e_out, float *__restrict__ u_out, int iters) {
-    const int first = blockIdx.x * kWarpsPerBlock * iters + (threadIdx.x >> 5);
-#pragma unroll 1
-    for (int it = 0; it < iters; ++it) {
-        const int slice = first + it * kWarpsPerBlock;
-        if (slice >= A.n_slices) return;
-        mixed_residual_slice<K, HT, LAST, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, u, r_out, e_out, u_out);
-    }
+                      HT *__restrict__ e_out, float *__restrict__ u_out) {
+    const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (slice >= A.n_slices) return;
+    mixed_residual_slice<K, HT, LAST, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, u, r_out, e_out, u_out);
 }
 
 template <int K, class HT, bool LAST, bool PROJECT, bool UN>
 __global__ void __launch_bounds__(kBlockThreads)
 mixed_sweep_kernel(const SellView A, const Coeffs cf, const HT *__restrict__ e_src, const HT *__restrict__ rr,
-                   HT *__restrict__ e_dst, const float *__restrict__ u, float *__restrict__ u_out, int iters) {
-    const int first = blockIdx.x * kWarpsPerBlock * iters + (threadIdx.x >> 5);
-#pragma unroll 1
-    for (int it = 0; it < iters; ++it) {
-        const int slice = first + it * kWarpsPerBlock;
-        if (slice >= A.n_slices) return;
-        mixed_sweep_slice<K, HT, LAST, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, e_src, rr, e_dst, u, u_out);
-    }
+                   HT *__restrict__ e_dst, const float *__restrict__ u, float *__restrict__ u_out) {
+    const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (slice >= A.n_slices) return;
+    mixed_sweep_slice<K, HT, LAST, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, e_src, rr, e_dst, u, u_out);
 }
 
 template <int K, class HT, bool UN>
 cudaError_t residual_ku(bool last, bool project, const SellView &A, const Coeffs &cf, const float *u, void *r,
                         void *e, float *u_out, cudaStream_t st) {
-    const int iters = sweep_iters(A.n_slices);
-    const int blocks = ((A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock + iters - 1) / iters;
+    const int blocks = (A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
     HT *rh = static_cast<HT *>(r), *eh = static_cast<HT *>(e);
     if (!last)
-        mixed_residual_kernel<K, HT, false, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, u, rh, eh, u_out, iters);
+        mixed_residual_kernel<K, HT, false, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, u, rh, eh, u_out);
     else if (project && K >= 2)
         mixed_residual_kernel<K, HT, true, (K >= 2), UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, u, rh, eh,
-                                                                                          u_out, iters);
+                                                                                          u_out);
     else
-        mixed_residual_kernel<K, HT, true, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, u, rh, eh, u_out, iters);
+        mixed_residual_kernel<K, HT, true, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, u, rh, eh, u_out);
     return cudaGetLastError();
 }
 
 template <int K, class HT, bool UN>
 cudaError_t sweep_ku(bool last, bool project, const SellView &A, const Coeffs &cf, const void *e_src,
                      const void *r, void *e_dst, const float *u, float *u_out, cudaStream_t st) {
-    const int iters = sweep_iters(A.n_slices);
-    const int blocks = ((A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock + iters - 1) / iters;
+    const int blocks = (A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const HT *es = static_cast<const HT *>(e_src), *rh = static_cast<const HT *>(r);
     HT *ed = static_cast<HT *>(e_dst);
     if (!last)
-        mixed_sweep_kernel<K, HT, false, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, es, rh, ed, u, u_out, iters);
+        mixed_sweep_kernel<K, HT, false, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, es, rh, ed, u, u_out);
     else if (project && K >= 2)
         mixed_sweep_kernel<K, HT, true, (K >= 2), UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, es, rh, ed, u,
-                                                                                       u_out, iters);
+                                                                                       u_out);
     else
-        mixed_sweep_kernel<K, HT, true, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, es, rh, ed, u, u_out, iters);
+        mixed_sweep_kernel<K, HT, true, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, es, rh, ed, u, u_out);
     return cudaGetLastError();
 }
 
