@@ -489,6 +489,27 @@ __device__ __forceinline__ void fma_group(float (&acc)[K], const IdxT &c, const 
     fma_row<K>(acc, w.w, r3);
 }
 
+// Entry-stream loads that bypass L1 allocation: every column index and
+// weight is read exactly once per pass, so L1 keeps its capacity for the
+// gathered rows of the iterate.
+__device__ __forceinline__ int4 ld_stream(const int4 *p) {
+    int4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint2 ld_stream(const uint2 *p) {
+    uint2 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ float4 ld_stream(const float4 *p) {
+    float4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
+    return r;
+}
+
 // Per-lane state of one slice row, loaded before the gather.
 template <int K, class IdxT>
 struct SliceRow {
@@ -515,11 +536,11 @@ __device__ __forceinline__ void slice_prologue(const SellView &A, const IdxT *co
     // every real row has an entry and every slice is at least kVec wide, so
     // group 0 always exists; group 1 is loaded when the slice has it
     const int width_groups = (int)((A.slice_off[slice + 1] - base) >> 5) / kVec;
-    s.c0 = __ldcs(s.cp);
-    s.w0 = __ldcs(s.wp);
+    s.c0 = ld_stream(s.cp);
+    s.w0 = ld_stream(s.wp);
     if (width_groups > 1) {
-        s.c1 = __ldcs(s.cp + 32);
-        s.w1 = __ldcs(s.wp + 32);
+        s.c1 = ld_stream(s.cp + 32);
+        s.w1 = ld_stream(s.wp + 32);
     }
     load_row<K>(v_src + (size_t)r * K, s.v);
     if (u_t == v_src) {
@@ -540,12 +561,12 @@ __device__ __forceinline__ void slice_gather(SliceRow<K, IdxT> &s, const float *
         IdxT n0 = s.c0, n1 = s.c1;
         float4 nw0 = s.w0, nw1 = s.w1;
         if (g + 2 < groups) {
-            n0 = __ldcs(s.cp + 32 * (g + 2));
-            nw0 = __ldcs(s.wp + 32 * (g + 2));
+            n0 = ld_stream(s.cp + 32 * (g + 2));
+            nw0 = ld_stream(s.wp + 32 * (g + 2));
         }
         if (g + 3 < groups) {
-            n1 = __ldcs(s.cp + 32 * (g + 3));
-            nw1 = __ldcs(s.wp + 32 * (g + 3));
+            n1 = ld_stream(s.cp + 32 * (g + 3));
+            nw1 = ld_stream(s.wp + 32 * (g + 3));
         }
         fma_group<K, MODE>(acc, s.c0, s.w0, x, hs, hidx);
         if (g + 1 < groups) fma_group<K, MODE>(acc, s.c1, s.w1, x, hs, hidx);
