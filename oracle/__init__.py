@@ -276,6 +276,49 @@ class Problem:
         return u, e[:outer], r[:outer]
 
 
+def second_eigenpair(row_ptr, col, w, laplacian: int = LAP_NORMALIZED, tol: float = 1e-13):
+    """(lambda_2, v_2): the second-smallest eigenvalue of L_s (or L) and its
+    unit eigenvector, the vector the paper initialises the unsupervised model
+    with (Sec. 5.3, the unsupervised clustering experiments).
+
+    Definition written out: the two largest eigenpairs of B I - L, where B
+    bounds the spectrum (2 for L_s, 2 max d_i for L, Prop. diagonal:pre), by
+    scipy's Lanczos (ARPACK) on the oracle's own C operator.  The eigenvector
+    is normalised to unit length and its sign fixed so that its
+    largest-magnitude component (lowest index among equal ones) is positive.
+    """
+    from scipy.sparse.linalg import LinearOperator, eigsh
+    row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    w = np.ascontiguousarray(w, np.float32)
+    n = row_ptr.shape[0] - 1
+    d, bad = degrees(row_ptr, col, w)
+    if bad >= 0:
+        raise ValueError(f"isolated node {bad}")
+    if laplacian == LAP_NORMALIZED:
+        bound, apply = 2.0, lambda x: apply_Ls(row_ptr, col, w, d, x)
+    else:
+        bound, apply = 2.0 * float(d.max()), lambda x: apply_L(row_ptr, col, w, d, x)
+    op = LinearOperator((n, n), matvec=lambda x: bound * np.asarray(x, np.float64).ravel() -
+                        apply(np.asarray(x, np.float64).ravel()), dtype=np.float64)
+    v0 = 1.0 + 0.5 * np.sin(np.arange(1, n + 1, dtype=np.float64))
+    vals, vecs = eigsh(op, k=2, which="LA", tol=tol, v0=v0, maxiter=100000)
+    order = np.argsort(-vals)
+    lam2 = bound - float(vals[order[1]])
+    v = vecs[:, order[1]].astype(np.float64)
+    v /= np.linalg.norm(v)
+    if v[int(np.argmax(np.abs(v)))] < 0:
+        v = -v
+    return lam2, v
+
+
+def spectral_init(v2) -> np.ndarray:
+    """u^0 of the unsupervised model from the second eigenvector: v_2 scaled
+    to max |u_i| = 1 (values in [-1, 1], the sign pattern of v_2)."""
+    v2 = np.asarray(v2, np.float64)
+    return v2 / np.abs(v2).max()
+
+
 def safe_lambda(lam_est: float, laplacian: int = LAP_NORMALIZED, dmax: float = 0.0) -> float:
     """lambda-hat used by the Richardson preconditioner: the power-method
     estimate raised by 0.1 % and capped by the Prop. (diagonal:pre) bound
