@@ -277,15 +277,20 @@ class Problem:
 
 
 def second_eigenpair(row_ptr, col, w, laplacian: int = LAP_NORMALIZED, tol: float = 1e-13):
-    """(lambda_2, v_2): the second-smallest eigenvalue of L_s (or L) and its
-    unit eigenvector, the vector the paper initialises the unsupervised model
-    with (Sec. 5.3, the unsupervised clustering experiments).
+    """(lambda_2, v_2): the smallest eigenvalue of L_s (or L) on the
+    orthogonal complement of its null vector q = D^1/2 1 (or 1), and its unit
+    eigenvector: the second eigenvector the paper initialises the unsupervised
+    model with (Sec. 5.3, the unsupervised clustering experiments).  On a
+    connected graph it is the second-smallest eigenpair; on a graph with
+    several components (where 0 is a multiple eigenvalue) the restriction to
+    the complement of q is what makes the vector unique.
 
-    Definition written out: the two largest eigenpairs of B I - L, where B
-    bounds the spectrum (2 for L_s, 2 max d_i for L, Prop. diagonal:pre), by
-    scipy's Lanczos (ARPACK) on the oracle's own C operator.  The eigenvector
-    is normalised to unit length and its sign fixed so that its
-    largest-magnitude component (lowest index among equal ones) is positive.
+    Definition written out: the largest eigenpair of Q (B I - L) Q with
+    Q = I - q q^T / q^T q and B a bound of the spectrum (2 for L_s, 2 max d_i
+    for L, Prop. diagonal:pre), by scipy's Lanczos (ARPACK) on the oracle's own
+    C operator.  The eigenvector is normalised to unit length and its sign fixed
+    so that its largest-magnitude component (lowest index among equal ones) is
+    positive.
     """
     from scipy.sparse.linalg import LinearOperator, eigsh
     row_ptr = np.ascontiguousarray(row_ptr, np.int64)
@@ -296,16 +301,23 @@ def second_eigenpair(row_ptr, col, w, laplacian: int = LAP_NORMALIZED, tol: floa
     if bad >= 0:
         raise ValueError(f"isolated node {bad}")
     if laplacian == LAP_NORMALIZED:
-        bound, apply = 2.0, lambda x: apply_Ls(row_ptr, col, w, d, x)
+        bound, apply, q = 2.0, (lambda x: apply_Ls(row_ptr, col, w, d, x)), np.sqrt(d)
     else:
-        bound, apply = 2.0 * float(d.max()), lambda x: apply_L(row_ptr, col, w, d, x)
-    op = LinearOperator((n, n), matvec=lambda x: bound * np.asarray(x, np.float64).ravel() -
-                        apply(np.asarray(x, np.float64).ravel()), dtype=np.float64)
-    v0 = 1.0 + 0.5 * np.sin(np.arange(1, n + 1, dtype=np.float64))
-    vals, vecs = eigsh(op, k=2, which="LA", tol=tol, v0=v0, maxiter=100000)
-    order = np.argsort(-vals)
-    lam2 = bound - float(vals[order[1]])
-    v = vecs[:, order[1]].astype(np.float64)
+        bound, apply, q = 2.0 * float(d.max()), (lambda x: apply_L(row_ptr, col, w, d, x)), np.ones(n)
+    q = q / np.linalg.norm(q)
+
+    def proj(x):
+        return x - (q @ x) * q
+
+    def mv(x):
+        x = proj(np.asarray(x, np.float64).ravel())
+        return proj(bound * x - apply(x))
+
+    op = LinearOperator((n, n), matvec=mv, dtype=np.float64)
+    v0 = proj(1.0 + 0.5 * np.sin(np.arange(1, n + 1, dtype=np.float64)))
+    vals, vecs = eigsh(op, k=1, which="LA", tol=tol, v0=v0, maxiter=100000)
+    lam2 = bound - float(vals[0])
+    v = proj(vecs[:, 0].astype(np.float64))
     v /= np.linalg.norm(v)
     if v[int(np.argmax(np.abs(v)))] < 0:
         v = -v

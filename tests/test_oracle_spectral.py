@@ -83,3 +83,24 @@ def test_two_cliques_split():
     u0 = oracle.spectral_init(v)
     assert np.abs(u0).max() == 1.0 and u0[np.argmax(np.abs(u0))] == 1.0
     assert 0 < lam < 0.01
+
+
+@pytest.mark.parametrize("lap", [oracle.LAP_NORMALIZED, oracle.LAP_UNNORMALIZED])
+def test_disconnected_graph_closed_form(lap):
+    """Two components A, B: 0 is a double eigenvalue; in the complement of
+    the null vector the eigenvector is D^1/2 (vol_B 1_A - vol_A 1_B) for L_s
+    (vol = sum of degrees) and |B| 1_A - |A| 1_B for L."""
+    pairs = [(0, 1), (1, 2), (0, 2), (2, 3)] + [(4, 5), (5, 6), (6, 7), (7, 8), (4, 8)]
+    i, j = np.array(pairs).T
+    wt = np.array([1.0, 0.5, 2.0, 1.5, 1.0, 0.7, 1.2, 0.9, 1.1], np.float32)
+    rp, col, w = csr_from_pairs(9, i, j, wt)
+    d, _ = oracle.degrees(rp, col, w)
+    A, Bm = np.arange(9) < 4, np.arange(9) >= 4
+    if lap == oracle.LAP_NORMALIZED:
+        ref = np.sqrt(d) * np.where(A, d[Bm].sum(), -d[A].sum())
+    else:
+        ref = np.where(A, Bm.sum(), -A.sum()).astype(float)
+    ref /= np.linalg.norm(ref)
+    lam, v = oracle.second_eigenpair(rp, col, w, lap)
+    assert abs(lam) < 1e-10
+    assert abs(abs(v @ ref) - 1.0) < 1e-10
