@@ -65,7 +65,8 @@ typedef enum {
     PDCA_ERR_BAD_GRAPH = 9,      /* column out of range, self loop, columns not
                                     strictly increasing, weight < 0 or not finite,
                                     mask not 0/1, or prior label out of range           */
-    PDCA_ERR_TOO_LARGE = 10      /* n above PDCA_STATIC_MAX_N in pdca_energy_static    */
+    PDCA_ERR_TOO_LARGE = 10,     /* n above PDCA_STATIC_MAX_N in pdca_energy_static    */
+    PDCA_ERR_NOT_CONVERGED = 11  /* pdca_spectral_init reached max_iters before tol    */
 } pdca_status;
 
 /* Laplacian (Sec. 2.2): L_s = I - D^{-1/2} W D^{-1/2} (normalized) or
@@ -263,6 +264,35 @@ pdca_status pdca_layout(pdca_problem *h, int64_t *sell_entries, int64_t *n_slice
  * resets both (synchronises). */
 pdca_status pdca_profile_enable(pdca_problem *h, int32_t on);
 pdca_status pdca_profile_read(pdca_problem *h, double *sweep_ms, int64_t *sweep_launches);
+
+/* Spectral initial iterate for the unsupervised model (no labelled nodes,
+ * K = 1): the paper initialises its unsupervised clustering runs with the
+ * eigenvector of the second-smallest eigenvalue of the normalized graph
+ * Laplacian (Sec. 5.3, Table of the clustering data sets).  This computes that
+ * eigenpair (lambda_2, v_2) of the handle's Laplacian (L_s, or L for
+ * PDCA_LAP_UNNORMALIZED): the smallest eigenpair on the orthogonal complement
+ * of the null vector D^1/2 1 (or 1), which is the second-smallest one on a
+ * connected graph and stays unique on a graph with several components.  It
+ * runs a block LOBPCG on the handle's operator and sets
+ * u^0 = v_2 / max_i |v_2,i|, signed so that its largest-magnitude entry
+ * (lowest node index among equal ones) is +1.  Where the handle stores BF16
+ * weights (mixed precision) the eigenpair is that of the BF16 operator.
+ *   workspace: DEVICE scratch of at least pdca_spectral_workspace_size bytes,
+ *     256-byte aligned, owned by the caller (free to reuse after the call);
+ *   max_iters >= 0: LOBPCG iterations; tol > 0: stop when the residual norm
+ *     ||L x - theta x|| of the unit Ritz vector is <= tol B, with B = 2 for
+ *     L_s and 2 max_i d_i for L (the bound of the spectrum); FP32 arithmetic
+ *     makes values below about 1e-6 unreachable;
+ *   lambda2 (nullable, host): the Ritz value of the second-smallest eigenpair;
+ *   u0_out (nullable, host or device, n floats): the u^0 that was set;
+ *   iters_done (nullable, host): iterations run.
+ * Synchronises the handle's stream.  Errors: INVALID_ARG (K != 1, a handle
+ * with PDCA_TILING_ON, bad arguments), OOM (workspace too small), NONFINITE,
+ * CUDA; NOT_CONVERGED when max_iters ran out first (u^0 is still set, from
+ * the last Ritz vector). */
+pdca_status pdca_spectral_workspace_size(const pdca_problem *h, size_t *bytes);
+pdca_status pdca_spectral_init(pdca_problem *h, void *workspace, size_t ws_bytes, int32_t max_iters, double tol,
+                               double *lambda2, float *u0_out, int32_t *iters_done);
 
 /* Number of kernels this library has launched in the process so far. */
 uint64_t pdca_kernel_launches(void);

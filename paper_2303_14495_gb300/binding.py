@@ -28,7 +28,7 @@ STATUS_NAMES = {
     0: "PDCA_OK", 1: "PDCA_ERR_INVALID_ARG", 2: "PDCA_ERR_NOT_SYMMETRIC",
     3: "PDCA_ERR_ISOLATED_NODE", 4: "PDCA_ERR_INFEASIBLE", 5: "PDCA_ERR_NONFINITE",
     6: "PDCA_ERR_OOM", 7: "PDCA_ERR_CUDA", 8: "PDCA_ERR_TIMEOUT", 9: "PDCA_ERR_BAD_GRAPH",
-    10: "PDCA_ERR_TOO_LARGE",
+    10: "PDCA_ERR_TOO_LARGE", 11: "PDCA_ERR_NOT_CONVERGED",
 }
 PDCA_STATIC_MAX_N = 1 << 20
 PDCA_LAP_NORMALIZED, PDCA_LAP_UNNORMALIZED = 0, 1
@@ -45,6 +45,7 @@ EXPORTS = [
     "pdca_status_string", "pdca_energy_static",
     "pdca_batch_create", "pdca_batch_add", "pdca_batch_step", "pdca_batch_poll", "pdca_batch_remove",
     "pdca_batch_destroy", "pdca_workspace_size_like", "pdca_create_like",
+    "pdca_spectral_workspace_size", "pdca_spectral_init",
 ]
 
 
@@ -108,6 +109,9 @@ def lib():
                 "pdca_batch_destroy": (None, [vp]),
                 "pdca_workspace_size_like": (C.c_int, [vp, i32, P, C.POINTER(C.c_size_t)]),
                 "pdca_create_like": (C.c_int, [vp, i32, vp, vp, P, vp, C.c_size_t, C.POINTER(vp)]),
+                "pdca_spectral_workspace_size": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
+                "pdca_spectral_init": (C.c_int, [vp, vp, C.c_size_t, i32, dbl, C.POINTER(dbl), vp,
+                                                 C.POINTER(i32)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -343,6 +347,24 @@ class Problem:
             out = np.empty(self.n, np.int32)
         _check(pdca_labels(self.h, out), "pdca_labels")
         return out
+
+    def spectral_init(self, max_iters: int = 500, tol: float = 1e-5, strict: bool = True):
+        """u^0 from the second eigenvector of the Laplacian (pdca_spectral_init).
+
+        Returns (lambda_2, u0 as a numpy array in node order, iterations).  The
+        scratch is a PyTorch tensor freed on return.  strict=False accepts
+        PDCA_ERR_NOT_CONVERGED (u^0 is then set from the last Ritz vector)."""
+        out = C.c_size_t(0)
+        _check(lib().pdca_spectral_workspace_size(self.h, C.byref(out)), "pdca_spectral_workspace_size")
+        ws = self.torch.empty(int(out.value), dtype=self.torch.uint8, device=self.device)
+        lam = C.c_double(0.0)
+        its = C.c_int32(0)
+        u0 = np.empty(self.n, np.float32)
+        st = lib().pdca_spectral_init(self.h, _ptr(ws), int(out.value), int(max_iters), float(tol), C.byref(lam),
+                                      _ptr(u0), C.byref(its))
+        if not (st == PDCA_OK or (st == 11 and not strict)):
+            _check(st, "pdca_spectral_init")
+        return float(lam.value), u0, int(its.value)
 
     def lambda_max(self):
         st, used, est = pdca_lambda_max(self.h)

@@ -40,7 +40,7 @@ struct Layout {
     bool host_order = false;           // renumbering computed on the host (BFS blocks)
     int64_t nnz = 0, sell_entries = 0, sell_cap = 0, halo_cap = 0;
     std::vector<int64_t> slice_off;    // n_slices + 1 (exact; filled at create for host order)
-    size_t o_col, o_w, o_slice, o_rowinfo, o_perm, o_iperm, o_self, o_u[3], o_part, o_red, o_scal, o_trace;
+    size_t o_col, o_w, o_slice, o_rowinfo, o_perm, o_iperm, o_self, o_dsq, o_u[3], o_part, o_red, o_scal, o_trace;
     size_t o_hoff, o_hidx;
     size_t o_mr, o_me[2];              // mixed precision: r and the two corrections (16-bit)
     size_t o_srp, o_scol, o_sw, o_sdeg, o_smask, o_slab, o_status;
@@ -257,6 +257,7 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     L.o_perm = take(4 * np);
     L.o_iperm = take(4 * nn);
     L.o_self = take(prm.laplacian == PDCA_LAP_UNNORMALIZED ? 4 * np : 0);
+    L.o_dsq = take(prm.laplacian == PDCA_LAP_NORMALIZED ? 4 * np : 0);
     for (int b = 0; b < 3; ++b) L.o_u[b] = take(4 * np * (size_t)K);
     L.o_part = take(8 * parts);
     L.o_red = take(sizeof(RedOut));
@@ -294,6 +295,7 @@ struct pdca_problem {
     double lambda_used = 0.0, lambda_est = 0.0;
     double dmax = 0.0;         // largest degree
     float *self = nullptr;     // a_i = d_i per row (unnormalized L), else nullptr
+    float *dsq = nullptr;      // sqrt(d_i) per row (normalized L_s: its null vector), else nullptr
     Coeffs cf;
     cudaStream_t stream = nullptr;
     char *ws = nullptr;
@@ -674,6 +676,7 @@ const char *pdca_status_string(pdca_status s) {
     case PDCA_ERR_TIMEOUT: return "bounded device wait ran out";
     case PDCA_ERR_BAD_GRAPH: return "malformed graph or fidelity input";
     case PDCA_ERR_TOO_LARGE: return "graph larger than the fixed scratch of pdca_energy_static";
+    case PDCA_ERR_NOT_CONVERGED: return "iteration limit reached before the tolerance";
     }
     return "unknown status";
 }
@@ -743,6 +746,7 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     h->perm = reinterpret_cast<int32_t *>(W + L.o_perm);
     h->iperm = reinterpret_cast<int32_t *>(W + L.o_iperm);
     h->self = prm.laplacian == PDCA_LAP_UNNORMALIZED ? reinterpret_cast<float *>(W + L.o_self) : nullptr;
+    h->dsq = prm.laplacian == PDCA_LAP_NORMALIZED ? reinterpret_cast<float *>(W + L.o_dsq) : nullptr;
     for (int b = 0; b < 3; ++b) h->U[b] = reinterpret_cast<float *>(W + L.o_u[b]);
     h->mixed = prm.precision != PDCA_FP32;
     h->bf16u = prm.precision == PDCA_MIXED_BF16W_BF16U;
@@ -802,8 +806,8 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     else
         pe = launch_pack(n, L.n_pad, k, s_rp, s_col, s_w, s_deg, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
                          h->sell_col, h->mixed ? nullptr : h->sell_w,
-                         h->mixed ? reinterpret_cast<__nv_bfloat16 *>(h->sell_w) : nullptr, h->self, h->rowinfo,
-                         s_status, sm);
+                         h->mixed ? reinterpret_cast<__nv_bfloat16 *>(h->sell_w) : nullptr, h->self,
+                         h->tiled ? nullptr : h->dsq, h->rowinfo, s_status, sm);
     if (pe != cudaSuccess) return fail(PDCA_ERR_CUDA);
     if (prm.precond == PDCA_RICHARDSON) {
         if (prm.lambda_max > 0) {
@@ -874,6 +878,7 @@ pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t 
     h->perm = base->perm;
     h->iperm = base->iperm;
     h->self = base->self;
+    h->dsq = base->dsq;
     h->dmax = base->dmax;
     h->tiled = base->tiled;
     h->tv = base->tv;
@@ -947,6 +952,34 @@ pdca_status pdca_set_u(pdca_problem *h, const float *u) {
     h->prev = stage;
     h->has_prev = false;
     return PDCA_OK;
+}
+
+pdca_status pdca_spectral_workspace_size(const pdca_problem *h, size_t *bytes) {
+    if (!h || !bytes) return PDCA_ERR_INVALID_ARG;
+    *bytes = align_up(spectral_workspace_bytes(h->L.n_pad)) + align_up(sizeof(float) * (size_t)h->L.n);
+    return PDCA_OK;
+}
+
+pdca_status pdca_spectral_init(pdca_problem *h, void *workspace, size_t ws_bytes, int32_t max_iters, double tol,
+                               double *lambda2, float *u0_out, int32_t *iters_done) {
+    if (!h || !workspace || max_iters < 0 || !(tol > 0.0) || !std::isfinite(tol)) return PDCA_ERR_INVALID_ARG;
+    if (h->L.K != 1 || h->tiled) return PDCA_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return PDCA_ERR_INVALID_ARG;
+    size_t need = 0;
+    pdca_spectral_workspace_size(h, &need);
+    if (ws_bytes < need) return PDCA_ERR_OOM;
+    float *vec = reinterpret_cast<float *>(static_cast<char *>(workspace) + align_up(spectral_workspace_bytes(h->L.n_pad)));
+    // the tolerance is relative to the bound of the spectrum
+    const double bound = h->self ? 2.0 * h->dmax : 2.0;
+    const pdca_status st = spectral_eigvec(h->view(), h->self != nullptr, h->self ? nullptr : h->dsq, h->perm,
+                                           h->L.n, h->L.n_pad, h->stream, workspace, max_iters, tol * bound,
+                                           lambda2, vec, iters_done);
+    if (st != PDCA_OK && st != PDCA_ERR_NOT_CONVERGED) return st;
+    pdca_status s2 = pdca_set_u(h, vec);
+    if (s2 != PDCA_OK) return s2;
+    if (u0_out) PDCA_TRY(cudaMemcpyAsync(u0_out, vec, sizeof(float) * (size_t)h->L.n, cudaMemcpyDefault, h->stream));
+    PDCA_TRY(cudaStreamSynchronize(h->stream));
+    return st;
 }
 
 pdca_status pdca_step(pdca_problem *h, int32_t inner_sweeps) {

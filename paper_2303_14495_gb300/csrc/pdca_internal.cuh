@@ -208,12 +208,12 @@ cudaError_t launch_validate(int32_t n, int32_t K, const int64_t *row_ptr, const 
 cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const int64_t *row_ptr,
                                int32_t *perm, int32_t *iperm, cudaStream_t st);
 // self == nullptr: L_s weights w_ij / sqrt(d_i d_j); else L weights w_ij and
-// self[r] = d_i (0 on padding rows).
+// self[r] = d_i (0 on padding rows).  dsq (nullable): sqrt(d_i) per row.
 cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_ptr,
                         const int32_t *col, const float *w, const double *deg,
                         const uint8_t *mask, const int32_t *labels, const int32_t *perm,
                         const int32_t *iperm, const int64_t *slice_off, int32_t *sell_col,
-                        float *sell_w, __nv_bfloat16 *sell_wb, float *self, uint32_t *rowinfo,
+                        float *sell_w, __nv_bfloat16 *sell_wb, float *self, float *dsq, uint32_t *rowinfo,
                         uint32_t *status, cudaStream_t st);
 // tiled form: local 16-bit columns (position in the tile's halo) instead of int32
 cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32_t *col, const float *w,
@@ -241,6 +241,18 @@ cudaError_t launch_init_u(int32_t n_pad, int32_t K, const uint32_t *rowinfo, flo
 cudaError_t launch_retag(int32_t n_pad, int32_t K, const uint32_t *base_rowinfo, const int32_t *perm,
                          const uint8_t *mask, const int32_t *labels, uint32_t *rowinfo, uint32_t *status,
                          cudaStream_t st);
+
+// --- spectral initial iterate (spectral.cu) -----------------------------------
+size_t spectral_workspace_bytes(int32_t n_pad);
+// Smallest eigenpair of the operator A (L_s, or L when un) on the orthogonal
+// complement of its null vector q (q = sqrt(d_i) per renumbered row for L_s;
+// the constant vector for L, q == nullptr); writes u0 = v2 / max|v2| (sign:
+// largest-magnitude entry positive) in the caller's node order to
+// out_caller_order (device, n floats).  PDCA_ERR_NOT_CONVERGED when
+// max_iters ran out (the output is still written).
+pdca_status spectral_eigvec(const SellView &A, bool un, const float *q, const int32_t *perm, int32_t n,
+                            int32_t n_pad, cudaStream_t st, void *workspace, int32_t max_iters, double tol,
+                            double *lambda2, float *out_caller_order, int32_t *iters_done);
 
 // Kernel launch counter (every launch_* above adds its launches).
 void count_launches(uint64_t k);

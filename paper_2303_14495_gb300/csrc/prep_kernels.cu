@@ -119,7 +119,8 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
                             const int32_t *__restrict__ iperm, const int64_t *__restrict__ slice_off,
                             int32_t *__restrict__ sell_col, float *__restrict__ sell_w,
                             __nv_bfloat16 *__restrict__ sell_wb, float *__restrict__ self,
-                            uint32_t *__restrict__ rowinfo, uint32_t *__restrict__ status) {
+                            float *__restrict__ dsq, uint32_t *__restrict__ rowinfo,
+                            uint32_t *__restrict__ status) {
     const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_pad) return;
     const int32_t s = r >> 5, lane = r & 31;
@@ -137,6 +138,7 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
         }
         const double di = deg[old];
         if (self) self[r] = (float)di;
+        if (dsq) dsq[r] = (float)sqrt(di);
         for (int32_t j = 0; j < len; ++j) {
             const int32_t oj = col[e0 + j];
             const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
@@ -146,8 +148,9 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
             else sell_w[at] = (float)wt;
         }
         if (mask[old]) tag = (uint32_t)labels[old];
-    } else if (self) {
-        self[r] = 0.0f;
+    } else {
+        if (self) self[r] = 0.0f;
+        if (dsq) dsq[r] = 0.0f;
     }
     for (int32_t j = len; j < width; ++j) {
         const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
@@ -284,13 +287,13 @@ cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const in
 cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_ptr, const int32_t *col,
                         const float *w, const double *deg, const uint8_t *mask, const int32_t *labels,
                         const int32_t *perm, const int32_t *iperm, const int64_t *slice_off,
-                        int32_t *sell_col, float *sell_w, __nv_bfloat16 *sell_wb, float *self,
+                        int32_t *sell_col, float *sell_w, __nv_bfloat16 *sell_wb, float *self, float *dsq,
                         uint32_t *rowinfo, uint32_t *status, cudaStream_t st) {
     (void)n;
     (void)K;
     count_launches(1);
     pack_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, mask, labels, perm,
-                                                     iperm, slice_off, sell_col, sell_w, sell_wb, self,
+                                                     iperm, slice_off, sell_col, sell_w, sell_wb, self, dsq,
                                                      rowinfo, status);
     return cudaGetLastError();
 }
