@@ -1,0 +1,161 @@
+"""Oracle of the nonlocal image graph (TEST INFRASTRUCTURE ONLY).
+
+Follows Sec. 2.3 of the paper (the weight of pixels i, j is the Gaussian
+kernel K(i,j) of eq. kij times the window indicator N_s(i,j)), with the
+window k-NN restriction the image workloads use: each pixel keeps the k
+window pixels with the smallest patch distance, and the graph is the union of
+those directed edges (symmetrised), weighted by K.
+
+Definition, spelled out so that every floating-point decision is the same as
+the CUDA builder's (the kept neighbours are decided by comparing distances,
+so both sides take that decision in the same precision, FP32):
+  * patch distance d2(i, j) = sum over patch offsets (oy, ox) in raster order
+    (oy, then ox, from -p to p) and channels c of (A - B)^2, where A and B are
+    the replicate-padded pixel values at i + (oy, ox) and j + (oy, ox); each
+    square and each addition rounded to float32 in that order (no fused
+    multiply-add);  alpha_n = 1;
+  * candidates of i: the pixels j != i with max(|dy|, |dx|) <= r inside the
+    image;  the k kept are the smallest (d2, j) in lexicographic order
+    (ties of d2 go to the lower index j = y W + x);
+  * w_ij = float32(exp(-float64(d2) / sigma^2)) for every edge of the union;
+    d2(i, j) == d2(j, i) exactly, so w is symmetric bit for bit.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+def _padded(img: np.ndarray, p: int) -> np.ndarray:
+    img = np.ascontiguousarray(img, np.float32)
+    return np.pad(img, ((p, p), (p, p), (0, 0)), mode="edge")
+
+
+def patch_d2(img: np.ndarray, p: int, i: int, j: int) -> np.float32:
+    """d2(i, j) for one pair, one term at a time (the definition above)."""
+    H, W, C = img.shape
+    P = _padded(img, p)
+    yi, xi = divmod(i, W)
+    yj, xj = divmod(j, W)
+    acc = np.float32(0.0)
+    for oy in range(-p, p + 1):
+        for ox in range(-p, p + 1):
+            for c in range(C):
+                a = P[yi + p + oy, xi + p + ox, c]
+                b = P[yj + p + oy, xj + p + ox, c]
+                t = np.float32(a - b)
+                acc = np.float32(acc + np.float32(t * t))
+    return acc
+
+
+def _d2_offset(P: np.ndarray, H: int, W: int, C: int, p: int, dy: int, dx: int) -> np.ndarray:
+    """d2(i, i + (dy, dx)) for every pixel i (H x W, float32, same order of
+    operations as patch_d2; +inf where the partner is outside the image)."""
+    acc = np.zeros((H, W), np.float32)
+    Hp, Wp = P.shape[:2]
+    for oy in range(-p, p + 1):
+        for ox in range(-p, p + 1):
+            for c in range(C):
+                ya, xa = p + oy, p + ox
+                A = P[ya:ya + H, xa:xa + W, c]
+                # partner rows / cols, clipped into the padded image (invalid ones masked below)
+                yb = np.clip(np.arange(H) + p + oy + dy, 0, Hp - 1)
+                xb = np.clip(np.arange(W) + p + ox + dx, 0, Wp - 1)
+                Bv = P[yb[:, None], xb[None, :], c]
+                t = (A - Bv).astype(np.float32)
+                acc = (acc + (t * t).astype(np.float32)).astype(np.float32)
+    ys, xs = np.arange(H)[:, None] + dy, np.arange(W)[None, :] + dx
+    bad = (ys < 0) | (ys >= H) | (xs < 0) | (xs >= W)
+    return np.where(bad, np.float32(np.inf), acc)
+
+
+def knn_lists(img: np.ndarray, p: int, r: int, k: int):
+    """(nbr, d2): for every pixel the k kept window neighbours (n x k, -1 and
+    +inf where fewer than k candidates exist) ordered by (d2, index)."""
+    img = np.ascontiguousarray(img, np.float32)
+    H, W, C = img.shape
+    n = H * W
+    P = _padded(img, p)
+    offs = [(dy, dx) for dy in range(-r, r + 1) for dx in range(-r, r + 1) if (dy, dx) != (0, 0)]
+    D = np.stack([_d2_offset(P, H, W, C, p, dy, dx).ravel() for dy, dx in offs], axis=1)   # n x m
+    idx = np.arange(n)[:, None] + np.array([dy * W + dx for dy, dx in offs])[None, :]
+    idx = np.where(np.isinf(D), np.int64(1) << 40, idx)
+    # lexicographic (d2, j): sort by j, then stable by d2
+    o1 = np.argsort(idx, axis=1, kind="stable")
+    D1 = np.take_along_axis(D, o1, 1)
+    J1 = np.take_along_axis(idx, o1, 1)
+    o2 = np.argsort(D1, axis=1, kind="stable")[:, :k]
+    d2 = np.take_along_axis(D1, o2, 1)
+    nbr = np.take_along_axis(J1, o2, 1)
+    nbr = np.where(np.isinf(d2), -1, nbr).astype(np.int64)
+    return nbr, d2
+
+
+def image_graph(img: np.ndarray, p: int, r: int, k: int, sigma: float):
+    """CSR (row_ptr int64, col int32 ascending, w float32) of the symmetrised
+    window k-NN patch graph."""
+    img = np.ascontiguousarray(img, np.float32)
+    H, W, _ = img.shape
+    n = H * W
+    nbr, d2 = knn_lists(img, p, r, k)
+    rows = np.repeat(np.arange(n), k)
+    cols = nbr.ravel()
+    vals = d2.ravel()
+    ok = cols >= 0
+    rows, cols, vals = rows[ok], cols[ok], vals[ok]
+    # union of (i, j) and (j, i); d2 is symmetric, so duplicates carry equal values
+    R = np.concatenate([rows, cols])
+    Cc = np.concatenate([cols, rows])
+    V = np.concatenate([vals, vals])
+    key = R * n + Cc
+    order = np.argsort(key, kind="stable")
+    key, R, Cc, V = key[order], R[order], Cc[order], V[order]
+    first = np.ones(key.size, bool)
+    first[1:] = key[1:] != key[:-1]
+    R, Cc, V = R[first], Cc[first], V[first]
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.add.at(row_ptr, R + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    w = np.exp(-V.astype(np.float64) / (float(sigma) ** 2)).astype(np.float32)
+    return row_ptr, Cc.astype(np.int32), w
+
+
+def image_graph_rows(img: np.ndarray, p: int, r: int, k: int, sigma: float, rows):
+    """The same graph restricted to the given pixels (for spot checks of large
+    images): {i: (sorted columns int32, weights float32)}, computed from the
+    k-NN lists of each pixel and of every pixel in its window, one pair at a
+    time through patch_d2."""
+    img = np.ascontiguousarray(img, np.float32)
+    H, W, _ = img.shape
+
+    def window(i):
+        y, x = divmod(i, W)
+        out = []
+        for yy in range(max(0, y - r), min(H, y + r + 1)):
+            for xx in range(max(0, x - r), min(W, x + r + 1)):
+                j = yy * W + xx
+                if j != i:
+                    out.append(j)
+        return out
+
+    cache = {}
+
+    def kept(i):
+        if i not in cache:
+            cand = sorted((patch_d2(img, p, i, j), j) for j in window(i))
+            cache[i] = {j: d for d, j in cand[:k]}
+        return cache[i]
+
+    out = {}
+    for i in rows:
+        i = int(i)
+        nb = {}
+        for j in window(i):
+            if j in kept(i):
+                nb[j] = kept(i)[j]
+            elif i in kept(j):
+                nb[j] = kept(j)[i]
+        cols = np.array(sorted(nb), np.int32)
+        w = np.array([np.exp(-float(nb[j]) / float(sigma) ** 2) for j in sorted(nb)], np.float32)
+        out[i] = (cols, w)
+    return out
