@@ -294,6 +294,35 @@ pdca_status pdca_spectral_workspace_size(const pdca_problem *h, size_t *bytes);
 pdca_status pdca_spectral_init(pdca_problem *h, void *workspace, size_t ws_bytes, int32_t max_iters, double tol,
                                double *lambda2, float *u0_out, int32_t *iters_done);
 
+/* Nonlocal image graph (Sec. 2.3): w_ij = K(i,j) N(i,j) with the Gaussian
+ * kernel of patch distances K (eq. kij, alpha_n = 1) and the window
+ * indicator N_s, restricted to each pixel's k window neighbours of smallest
+ * patch distance and symmetrised by union (an edge where either end keeps
+ * the other).  Pixel i = y W + x.
+ *   patch distance d2(i,j) = sum over the (2p+1)^2 patch offsets (raster
+ *     order) and the C channels of (a - b)^2, FP32 with every square and sum
+ *     rounded separately, patches replicate-padded at the border;
+ *   candidates: j != i with max(|y_i - y_j|, |x_i - x_j|) <= r inside the
+ *     image; the k smallest (d2, j) are kept (equal distances go to the lower
+ *     index);  w_ij = float(exp(-d2 / sigma^2)) (double exp), symmetric bit
+ *     for bit.
+ *   image: DEVICE, H x W x C float32, row-major (pixel-major, channels last);
+ *   1 <= C <= 16, 0 <= patch_radius p <= 4, window_radius r >= 1,
+ *   1 <= k <= 32 and (min(H, 2r+1) min(W, 2r+1) - 1) >= k; sigma > 0.
+ *   workspace: DEVICE scratch of pdca_image_graph_workspace_size bytes,
+ *     256-byte aligned.  row_ptr (H W + 1 int64), col (col_capacity int32)
+ *     and w (col_capacity float32): DEVICE outputs; 2 k H W always suffices.
+ *   *nnz (host): the number of entries; rows come out with strictly
+ *     increasing columns, ready for pdca_create.
+ * Synchronises the stream.  Errors: INVALID_ARG (sizes, a host pointer among
+ * image/workspace/outputs), OOM (workspace or col_capacity too small; *nnz
+ * then holds the size needed), CUDA. */
+pdca_status pdca_image_graph_workspace_size(int32_t H, int32_t W, int32_t k, size_t *bytes);
+pdca_status pdca_image_graph(const float *image, int32_t H, int32_t W, int32_t C, int32_t patch_radius,
+                             int32_t window_radius, int32_t k, double sigma, void *workspace, size_t ws_bytes,
+                             int64_t *row_ptr, int32_t *col, float *w, int64_t col_capacity, int64_t *nnz,
+                             void *stream);
+
 /* Number of kernels this library has launched in the process so far. */
 uint64_t pdca_kernel_launches(void);
 

@@ -159,3 +159,27 @@ def image_graph_rows(img: np.ndarray, p: int, r: int, k: int, sigma: float, rows
         w = np.array([np.exp(-float(nb[j]) / float(sigma) ** 2) for j in sorted(nb)], np.float32)
         out[i] = (cols, w)
     return out
+
+
+def image_graph_rows_crop(img: np.ndarray, p: int, r: int, k: int, sigma: float, rows):
+    """image_graph restricted to the given pixels of a large image, through
+    the full builder on a crop: the rows of pixel i depend only on the kept
+    lists of the pixels within r of i, and those only on pixels within
+    2r + p of i.  A crop of that radius (clipped to the image) keeps the
+    row-major order of the indices, so ties break as in the whole image."""
+    img = np.ascontiguousarray(img, np.float32)
+    H, W, _ = img.shape
+    R = 2 * r + p
+    out = {}
+    for i in rows:
+        i = int(i)
+        y, x = divmod(i, W)
+        y0, y1 = max(0, y - R), min(H, y + R + 1)
+        x0, x1 = max(0, x - R), min(W, x + R + 1)
+        Wc = x1 - x0
+        rp, col, w = image_graph(img[y0:y1, x0:x1], p, r, k, sigma)
+        ic = (y - y0) * Wc + (x - x0)
+        cc = col[rp[ic]:rp[ic + 1]].astype(np.int64)
+        gy, gx = cc // Wc + y0, cc % Wc + x0
+        out[i] = ((gy * W + gx).astype(np.int32), w[rp[ic]:rp[ic + 1]].copy())
+    return out

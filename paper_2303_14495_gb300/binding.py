@@ -46,6 +46,7 @@ EXPORTS = [
     "pdca_batch_create", "pdca_batch_add", "pdca_batch_step", "pdca_batch_poll", "pdca_batch_remove",
     "pdca_batch_destroy", "pdca_workspace_size_like", "pdca_create_like",
     "pdca_spectral_workspace_size", "pdca_spectral_init",
+    "pdca_image_graph_workspace_size", "pdca_image_graph",
 ]
 
 
@@ -112,6 +113,9 @@ def lib():
                 "pdca_spectral_workspace_size": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
                 "pdca_spectral_init": (C.c_int, [vp, vp, C.c_size_t, i32, dbl, C.POINTER(dbl), vp,
                                                  C.POINTER(i32)]),
+                "pdca_image_graph_workspace_size": (C.c_int, [i32, i32, i32, C.POINTER(C.c_size_t)]),
+                "pdca_image_graph": (C.c_int, [vp, i32, i32, i32, i32, i32, i32, dbl, vp, C.c_size_t, vp, vp,
+                                               vp, i64, C.POINTER(i64), vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -429,6 +433,31 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def image_graph(image, patch_radius: int, window_radius: int, k: int, sigma: float, stream=None):
+    """pdca_image_graph on a torch CUDA tensor image (H x W x C float32).
+
+    Returns (row_ptr int64, col int32, w float32) as CUDA tensors trimmed to
+    the graph's nnz; the scratch and the outputs are PyTorch allocations."""
+    import torch
+    img = image.contiguous()
+    assert img.is_cuda and img.dtype == torch.float32 and img.dim() == 3
+    H, W, Cc = (int(v) for v in img.shape)
+    st = stream if stream is not None else torch.cuda.current_stream(img.device)
+    out = C.c_size_t(0)
+    _check(lib().pdca_image_graph_workspace_size(H, W, int(k), C.byref(out)), "pdca_image_graph_workspace_size")
+    ws = torch.empty(int(out.value), dtype=torch.uint8, device=img.device)
+    cap = 2 * int(k) * H * W
+    rp = torch.empty(H * W + 1, dtype=torch.int64, device=img.device)
+    col = torch.empty(cap, dtype=torch.int32, device=img.device)
+    w = torch.empty(cap, dtype=torch.float32, device=img.device)
+    nnz = C.c_int64(0)
+    _check(lib().pdca_image_graph(_ptr(img), H, W, Cc, int(patch_radius), int(window_radius), int(k),
+                                  float(sigma), _ptr(ws), int(out.value), _ptr(rp), _ptr(col), _ptr(w), cap,
+                                  C.byref(nnz), C.c_void_p(st.cuda_stream)), "pdca_image_graph")
+    m = int(nnz.value)
+    return rp, col[:m], w[:m]
 
 
 def params_from_workload(p: dict, **over) -> pdca_params:

@@ -77,3 +77,15 @@ def test_structure():
     pos = {(i, int(j)): float(w[e]) for i in range(n) for e, j in zip(range(rp[i], rp[i + 1]), col[rp[i]:rp[i + 1]])}
     for (i, j), v in pos.items():
         assert pos[(j, i)] == v
+
+
+def test_crop_rows_equal_full():
+    rng = np.random.default_rng(5)
+    img = rng.uniform(size=(30, 34, 3)).astype(np.float32)
+    img[10:14, 5:9] = 0.25
+    rp, col, w = IG.image_graph(img, 1, 3, 6, 0.5)
+    rows = [0, 33, 34 * 12 + 7, 34 * 15 + 20, 30 * 34 - 1]
+    got = IG.image_graph_rows_crop(img, 1, 3, 6, 0.5, rows)
+    for i in rows:
+        np.testing.assert_array_equal(got[i][0], col[rp[i]:rp[i + 1]])
+        np.testing.assert_array_equal(got[i][1], w[rp[i]:rp[i + 1]])
