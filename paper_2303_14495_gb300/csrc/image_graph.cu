@@ -23,12 +23,12 @@
 #include <cmath>
 
 #include "pdca_internal.cuh"
+#include "scan.cuh"
 
 namespace pdca {
 namespace {
 
 constexpr int kMaxK = 32;
-constexpr int kScanBlock = 1024;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -131,79 +131,6 @@ image_union_kernel(int H, int W, int r, int k, const int32_t *__restrict__ nbr, 
     if (!FILL) count[i] = len;
 }
 
-// exclusive prefix sum of count into out (int64), per block of kScanBlock;
-// block totals to bsum
-__global__ void __launch_bounds__(kScanBlock)
-scan_block_kernel(int64_t n, const int32_t *__restrict__ count, int64_t *__restrict__ out, int64_t *__restrict__ bsum) {
-    __shared__ int64_t wsum[kScanBlock / 32];
-    const int64_t g = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    int64_t v = g < n ? count[g] : 0;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int64_t s = v;   // inclusive warp scan
-    for (int o = 1; o < 32; o <<= 1) {
-        const int64_t t = __shfl_up_sync(0xffffffffu, s, o);
-        if (lane >= o) s += t;
-    }
-    if (lane == 31) wsum[warp] = s;
-    __syncthreads();
-    if (warp == 0) {
-        int64_t t = wsum[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t u = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += u;
-        }
-        wsum[lane] = t;   // inclusive scan of warp totals
-    }
-    __syncthreads();
-    const int64_t before = warp > 0 ? wsum[warp - 1] : 0;
-    if (g < n) out[g] = before + s - v;
-    if (threadIdx.x == kScanBlock - 1) bsum[blockIdx.x] = wsum[31];
-}
-
-// exclusive scan of the block totals in place (one block, chunked), total to *total
-__global__ void __launch_bounds__(kScanBlock)
-scan_totals_kernel(int64_t nb, int64_t *__restrict__ bsum, int64_t *__restrict__ total) {
-    __shared__ int64_t wsum[kScanBlock / 32];
-    __shared__ int64_t carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t base = 0; base < nb; base += kScanBlock) {
-        const int64_t g = base + threadIdx.x;
-        const int64_t v = g < nb ? bsum[g] : 0;
-        int64_t s = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t t = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += t;
-        }
-        if (lane == 31) wsum[warp] = s;
-        __syncthreads();
-        if (warp == 0) {
-            int64_t t = wsum[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                const int64_t u = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t += u;
-            }
-            wsum[lane] = t;
-        }
-        __syncthreads();
-        const int64_t before = (warp > 0 ? wsum[warp - 1] : 0) + carry;
-        if (g < nb) bsum[g] = before + s - v;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += wsum[31];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *total = carry;
-}
-
-__global__ void __launch_bounds__(kScanBlock)
-scan_add_kernel(int64_t n, const int64_t *__restrict__ bsum, const int64_t *__restrict__ total,
-                int64_t *__restrict__ out) {
-    const int64_t g = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    if (g < n) out[g] += bsum[blockIdx.x];
-    if (g == 0) out[n] = *total;
-}
-
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct ImgWs {
@@ -280,11 +207,7 @@ extern "C" pdca_status pdca_image_graph(const float *image, int32_t H, int32_t W
     const double s2 = sigma * sigma;
     image_union_kernel<false><<<blocks, 128, 0, st>>>(H, W, window_radius, k, s.nbr, s.dist, s2, s.count,
                                                       nullptr, nullptr, nullptr);
-    const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
-    scan_block_kernel<<<(unsigned)nb, kScanBlock, 0, st>>>(n, s.count, row_ptr, s.bsum);
-    count_launches(2);
-    scan_totals_kernel<<<1, kScanBlock, 0, st>>>(nb, s.bsum, s.total);
-    scan_add_kernel<<<(unsigned)nb, kScanBlock, 0, st>>>(n, s.bsum, s.total, row_ptr);
+    exclusive_scan(n, s.count, row_ptr, s.bsum, s.total, st);
     int64_t tot = 0;
     if (cudaMemcpyAsync(&tot, s.total, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
