@@ -47,6 +47,7 @@ EXPORTS = [
     "pdca_batch_destroy", "pdca_workspace_size_like", "pdca_create_like",
     "pdca_spectral_workspace_size", "pdca_spectral_init",
     "pdca_image_graph_workspace_size", "pdca_image_graph",
+    "pdca_point_graph_workspace_size", "pdca_point_graph",
 ]
 
 
@@ -116,6 +117,9 @@ def lib():
                 "pdca_image_graph_workspace_size": (C.c_int, [i32, i32, i32, C.POINTER(C.c_size_t)]),
                 "pdca_image_graph": (C.c_int, [vp, i32, i32, i32, i32, i32, i32, dbl, vp, C.c_size_t, vp, vp,
                                                vp, i64, C.POINTER(i64), vp]),
+                "pdca_point_graph_workspace_size": (C.c_int, [i64, i32, C.POINTER(C.c_size_t)]),
+                "pdca_point_graph": (C.c_int, [vp, i64, i32, i32, i32, vp, C.c_size_t, vp, vp, vp, i64,
+                                               C.POINTER(i64), vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -456,6 +460,30 @@ def image_graph(image, patch_radius: int, window_radius: int, k: int, sigma: flo
     _check(lib().pdca_image_graph(_ptr(img), H, W, Cc, int(patch_radius), int(window_radius), int(k),
                                   float(sigma), _ptr(ws), int(out.value), _ptr(rp), _ptr(col), _ptr(w), cap,
                                   C.byref(nnz), C.c_void_p(st.cuda_stream)), "pdca_image_graph")
+    m = int(nnz.value)
+    return rp, col[:m], w[:m]
+
+
+def point_graph(X, k: int, scale_nn: int = 7, stream=None):
+    """pdca_point_graph on a torch CUDA tensor X (n x dim float32).
+
+    Returns (row_ptr int64, col int32, w float32) CUDA tensors trimmed to nnz."""
+    import torch
+    Xc = X.contiguous()
+    assert Xc.is_cuda and Xc.dtype == torch.float32 and Xc.dim() == 2
+    n, dim = (int(v) for v in Xc.shape)
+    st = stream if stream is not None else torch.cuda.current_stream(Xc.device)
+    out = C.c_size_t(0)
+    _check(lib().pdca_point_graph_workspace_size(n, int(k), C.byref(out)), "pdca_point_graph_workspace_size")
+    ws = torch.empty(int(out.value), dtype=torch.uint8, device=Xc.device)
+    cap = 2 * int(k) * n
+    rp = torch.empty(n + 1, dtype=torch.int64, device=Xc.device)
+    col = torch.empty(cap, dtype=torch.int32, device=Xc.device)
+    w = torch.empty(cap, dtype=torch.float32, device=Xc.device)
+    nnz = C.c_int64(0)
+    _check(lib().pdca_point_graph(_ptr(Xc), n, dim, int(k), int(scale_nn), _ptr(ws), int(out.value), _ptr(rp),
+                                  _ptr(col), _ptr(w), cap, C.byref(nnz), C.c_void_p(st.cuda_stream)),
+           "pdca_point_graph")
     m = int(nnz.value)
     return rp, col[:m], w[:m]
 
