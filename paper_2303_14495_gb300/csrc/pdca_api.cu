@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 using namespace pdca;
@@ -18,7 +19,7 @@ std::atomic<uint64_t> g_launches{0};
 constexpr size_t kAlign = 256;
 constexpr int kTraceCap = 1024;   // outer steps per trace chunk
 constexpr double kPadTarget = 1.10;
-constexpr int32_t kBfsChunk = 1 << 18;       // renumbering chunk (multiple of kBfsBlock)
+constexpr int32_t kBfsChunk = 1 << 16;       // renumbering chunk (multiple of kBfsBlock)
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -457,35 +458,66 @@ pdca_status power_method(pdca_problem *h) {
 
 // Host symbolic analysis (BFS-block renumbering, degree sort, halo lists),
 // then upload of perm / iperm / halo arrays and the exact slice offsets.
-pdca_status host_renumber(pdca_problem *h, const int64_t *rp, const int32_t *col, int64_t nnz) {
+// The renumbering order of BFS mode, computed on a host thread while the
+// device copies and validates the graph (the BFS reads only columns inside
+// its own chunk, so an invalid column cannot make it read out of bounds; the
+// order is used only once validation has passed).
+struct OrderJob {
+    std::vector<int32_t> col_keep, order;
+    const int32_t *hc = nullptr;
+    std::thread th;
+    pdca_status st = PDCA_OK;
+    ~OrderJob() {
+        if (th.joinable()) th.join();
+    }
+    pdca_status start(const int64_t *rp, const int32_t *col, int64_t nnz, int32_t n, int32_t sigma) {
+        hc = col;
+        if (nnz > 0 && is_device_ptr(col)) {
+            col_keep.resize((size_t)nnz);
+            if (cudaMemcpy(col_keep.data(), col, 4 * (size_t)nnz, cudaMemcpyDefault) != cudaSuccess)
+                return PDCA_ERR_CUDA;
+            hc = col_keep.data();
+        }
+        order.resize((size_t)n);
+        th = std::thread([this, rp, n, sigma] { locality_order(n, rp, hc, kBfsBlock, kBfsChunk, sigma, order.data()); });
+        return PDCA_OK;
+    }
+    void join() {
+        if (th.joinable()) th.join();
+    }
+};
+
+pdca_status host_renumber(pdca_problem *h, const int64_t *rp, OrderJob &job) {
     Layout &L = h->L;
     const int32_t n = L.n;
-    std::vector<int32_t> col_keep;
-    const int32_t *hc = col;
-    if (nnz > 0 && is_device_ptr(col)) {
-        col_keep.resize((size_t)nnz);
-        PDCA_TRY(cudaMemcpy(col_keep.data(), col, 4 * (size_t)nnz, cudaMemcpyDefault));
-        hc = col_keep.data();
-    }
-    // columns must be in range before the host walks them (the device check
-    // already passed, so this only guards against inconsistent input copies)
-    std::vector<int32_t> order((size_t)n);
-    locality_order(n, rp, hc, kBfsBlock, kBfsChunk, L.sigma, order.data());
+    job.join();
+    const int32_t *hc = job.hc;
+    const std::vector<int32_t> &order = job.order;
     std::vector<int32_t> perm((size_t)L.n_pad, -1), iperm((size_t)n);
-    for (int32_t r = 0; r < n; ++r) {
-        perm[(size_t)r] = order[(size_t)r];
-        iperm[(size_t)order[(size_t)r]] = r;
-    }
-    L.slice_off.assign((size_t)L.n_slices + 1, 0);
-    for (int32_t s = 0; s < L.n_slices; ++s) {
-        int64_t wmax = 0;
-        for (int32_t l = 0; l < kSliceRows; ++l) {
-            const int32_t r = s * kSliceRows + l;
-            if (r < n) wmax = std::max<int64_t>(wmax, rp[perm[(size_t)r] + 1] - rp[perm[(size_t)r]]);
+    const int64_t chunks = ((int64_t)n + 65535) / 65536;
+    host_parallel_for(chunks, [&](int64_t c) {
+        const int32_t r0 = (int32_t)(c * 65536), r1 = (int32_t)std::min<int64_t>(n, (c + 1) * 65536);
+        for (int32_t r = r0; r < r1; ++r) {
+            perm[(size_t)r] = order[(size_t)r];
+            iperm[(size_t)order[(size_t)r]] = r;
         }
-        wmax = (wmax + kVec - 1) / kVec * kVec;
-        L.slice_off[(size_t)s + 1] = L.slice_off[(size_t)s] + wmax * kSliceRows;
-    }
+    });
+    std::vector<int64_t> width((size_t)L.n_slices, 0);
+    const int64_t schunks = ((int64_t)L.n_slices + 2047) / 2048;
+    host_parallel_for(schunks, [&](int64_t c) {
+        const int32_t s0 = (int32_t)(c * 2048), s1 = (int32_t)std::min<int64_t>(L.n_slices, (c + 1) * 2048);
+        for (int32_t s = s0; s < s1; ++s) {
+            int64_t wmax = 0;
+            for (int32_t l = 0; l < kSliceRows; ++l) {
+                const int32_t r = s * kSliceRows + l;
+                if (r < n) wmax = std::max<int64_t>(wmax, rp[perm[(size_t)r] + 1] - rp[perm[(size_t)r]]);
+            }
+            width[(size_t)s] = (wmax + kVec - 1) / kVec * kVec;
+        }
+    });
+    L.slice_off.assign((size_t)L.n_slices + 1, 0);
+    for (int32_t s = 0; s < L.n_slices; ++s)
+        L.slice_off[(size_t)s + 1] = L.slice_off[(size_t)s] + width[(size_t)s] * kSliceRows;
     L.sell_entries = L.slice_off.back();
     if (L.sell_entries > L.sell_cap) return PDCA_ERR_CUDA;   // the bound is a theorem; never expected
     h->tiled = false;
@@ -766,6 +798,15 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     uint32_t *s_status = reinterpret_cast<uint32_t *>(W + L.o_status);
     cudaStream_t sm = h->stream;
 
+    // BFS renumbering on a host thread, overlapping the copies and validation
+    OrderJob job;
+    if (L.host_order) {
+        st = job.start(rp, col, nnz, n, L.sigma);
+        if (st != PDCA_OK) {
+            delete h;
+            return st;
+        }
+    }
     auto fail = [&](pdca_status s) { cudaStreamSynchronize(sm); delete h; return s; };
     auto cp = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, sm) : cudaSuccess;
@@ -792,7 +833,7 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     }
 
     if (L.host_order) {
-        st = host_renumber(h, rp, col, nnz);
+        st = host_renumber(h, rp, job);
         if (st != PDCA_OK) return fail(st);
     } else if (launch_window_sort(n, L.n_pad, L.sigma, s_rp, h->perm, h->iperm, sm) != cudaSuccess) {
         return fail(PDCA_ERR_CUDA);

@@ -67,6 +67,12 @@ void chunk_blocks(int64_t c0, int64_t c1, const int64_t *rp, const int32_t *col,
             touched.push_back((int32_t)seed);
             size_t qh = 0;
             while (qh < queue.size() && cnt < block) {
+                // the rows of queued nodes are scattered in memory: start
+                // fetching the edge list of a node a few places ahead
+                if (qh + 8 < queue.size()) {
+                    const int32_t a = queue[qh + 8];
+                    __builtin_prefetch(col + rp[a]);
+                }
                 const int32_t v = queue[qh++];
                 vis[(size_t)(v - c0)] = 1;
                 order[pos++] = v;
@@ -79,6 +85,7 @@ void chunk_blocks(int64_t c0, int64_t c1, const int64_t *rp, const int32_t *col,
                         inq[lj] = 1;
                         queue.push_back((int32_t)j);
                         touched.push_back((int32_t)j);
+                        __builtin_prefetch(rp + j);
                     }
                 }
             }
