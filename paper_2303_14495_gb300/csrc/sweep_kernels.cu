@@ -10,10 +10,10 @@
 //
 // All of them walk the sliced-ELL operator the same way: one warp per 32-row
 // slice, one lane per row, entry j of every lane read as one coalesced warp
-// load of column indices and one of weights (streamed with the evict-first
-// hint).  Neighbour rows of u come either from global memory through L1/L2
-// (plain form) or, in the tiled form, from shared memory: a block handles a
-// tile of 32 slices and first copies the tile's halo rows (the distinct rows
+// load of column indices and one of weights (streamed without L1
+// allocation).  Neighbour rows of u come either from global memory through
+// L1/L2 (plain form) or, in the tiled form, from shared memory: a block
+// handles a tile of 16 slices and first copies the tile's halo rows (the distinct rows
 // its entries reference) into shared memory, so every gather is a shared
 // memory load addressed by a 16-bit local column.
 #include "device_common.cuh"
@@ -136,9 +136,15 @@ energy_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u,
     const int lane = threadIdx.x & 31;
     float red[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (slice < A.n_slices) {
-        const int64_t base = A.slice_off[slice];
         float acc[K];
-        gather_row_sum<K, WT, float>(A, base, row_len(A, slice, lane), lane, u, acc);
+        if constexpr (std::is_same<WT, float>::value) {
+            // the sweeps' pipelined slice body (same summation order)
+            SliceRow<K, int4> sr;
+            slice_prologue<K>(A, reinterpret_cast<const int4 *>(A.col), slice, lane, u, u, sr);
+            slice_gather<K, kGlobal>(sr, u, nullptr, nullptr, acc);
+        } else {
+            gather_row_sum<K, WT, float>(A, A.slice_off[slice], row_len(A, slice, lane), lane, u, acc);
+        }
         energy_row<K>(A, cf, slice, lane, acc, u, u_prev, red);
     }
     block_sum_store<6>(red, partials + (size_t)blockIdx.x * kRedSlots);
