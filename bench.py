@@ -422,6 +422,38 @@ def run_ours(args, wl, world, rank, local):
                "includes": "pdca_create (H2D of the CSR, validation, degrees, reordering, "
                            "sliced-ELL packing, power method) + solve + energy + labels D2H"}
 
+    # the mixed-precision form of the same solve (informational; not the metric)
+    mixed = None
+    if not args.no_mixed and precision == 0:
+        mixed = {}
+        for name, prec in (("bf16w_bf16u", B.PDCA_MIXED_BF16W_BF16U), ("bf16w_fp16u", B.PDCA_MIXED_BF16W_FP16U)):
+            pm = B.params_from_workload(p, sort_window=args.sort_window, precision=prec,
+                                        **LAYOUT_PARAMS[args.layout])
+            mp = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, pm, device=dev)
+            for _ in range(2):
+                mp.set_u(None)
+                mp.solve(p["outer"], p["inner"])
+            torch.cuda.synchronize(dev)
+            mp.profile(True)
+            m0 = torch.cuda.Event(enable_timing=True)
+            m1 = torch.cuda.Event(enable_timing=True)
+            nm = max(3, args.steps // 4)
+            m0.record(stream)
+            for _ in range(nm):
+                mp.set_u(None)
+                mp.solve(p["outer"], p["inner"])
+                mp.energy()
+            m1.record(stream)
+            torch.cuda.synchronize(dev)
+            pm_ms, pm_n = mp.profile_read()
+            mp.profile(False)
+            passes = mixed_pass_bytes(wl.nnz, wl.n, wl.K, p["inner"])
+            mixed[name] = {"ms_per_solve": m0.elapsed_time(m1) / nm, "ms_per_pass": pm_ms / max(pm_n, 1),
+                           "algorithmic_gb_s_per_pass": (sum(passes) / len(passes)) / (pm_ms / max(pm_n, 1) * 1e-3) / 1e9,
+                           "solves": nm}
+            del mp
+        torch.cuda.synchronize(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, nb, thr = oracle_sample(wl, False, 2)
@@ -467,6 +499,8 @@ def run_ours(args, wl, world, rank, local):
     }
     if e2e:
         line["e2e"] = e2e
+    if mixed:
+        line["mixed_precision"] = mixed
     if serve:
         line["serving"] = serve
     if cpu:
@@ -490,6 +524,7 @@ def main():
                     help="degree-sort window (power of two; 0 = library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=512)
     ap.add_argument("--serving-rate", type=float, default=1000.0)
     ap.add_argument("--serving-slots", type=int, default=64)
