@@ -178,13 +178,34 @@ __device__ __forceinline__ void store_row_t(T *__restrict__ p, const float (&x)[
     }
 }
 
+// Entry-stream loads that bypass L1 allocation: every column index and
+// weight is read exactly once per pass, so L1 keeps its capacity for the
+// gathered rows of the iterate.
+__device__ __forceinline__ int4 ld_stream(const int4 *p) {
+    int4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint2 ld_stream(const uint2 *p) {
+    uint2 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ float4 ld_stream(const float4 *p) {
+    float4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
+    return r;
+}
+
 // the four weights of one entry group
 template <class WT>
 __device__ __forceinline__ float4 load_w_group(const WT *p) {
     if constexpr (std::is_same_v<WT, float>) {
-        return __ldcs(reinterpret_cast<const float4 *>(p));
+        return ld_stream(reinterpret_cast<const float4 *>(p));
     } else {
-        const uint2 t = __ldcs(reinterpret_cast<const uint2 *>(p));
+        const uint2 t = ld_stream(reinterpret_cast<const uint2 *>(p));
         const float2 a = unpack2<__nv_bfloat16>(t.x), b = unpack2<__nv_bfloat16>(t.y);
         return make_float4(a.x, a.y, b.x, b.y);
     }
@@ -205,24 +226,25 @@ __device__ __forceinline__ void gather_row_sum(const SellView &A, int64_t base, 
     const int groups = (len + kVec - 1) / kVec;   // this lane's groups only
     int g = 0;
     for (; g + 2 <= groups; g += 2) {
-        const int4 ca = __ldcs(cp + 32 * g), cb = __ldcs(cp + 32 * (g + 1));
+        const int4 ca = ld_stream(cp + 32 * g), cb = ld_stream(cp + 32 * (g + 1));
         const float4 wa = load_w_group<WT>(wp + 32 * kVec * g), wb = load_w_group<WT>(wp + 32 * kVec * (g + 1));
-        float x0[K], x1[K], x2[K], x3[K];
+        // all eight rows in flight before the first product
+        float x0[K], x1[K], x2[K], x3[K], y0[K], y1[K], y2[K], y3[K];
         load_row_t<K, XT>(x + (size_t)ca.x * K, x0);
         load_row_t<K, XT>(x + (size_t)ca.y * K, x1);
         load_row_t<K, XT>(x + (size_t)ca.z * K, x2);
         load_row_t<K, XT>(x + (size_t)ca.w * K, x3);
+        load_row_t<K, XT>(x + (size_t)cb.x * K, y0);
+        load_row_t<K, XT>(x + (size_t)cb.y * K, y1);
+        load_row_t<K, XT>(x + (size_t)cb.z * K, y2);
+        load_row_t<K, XT>(x + (size_t)cb.w * K, y3);
         fma_row<K>(acc, wa.x, x0); fma_row<K>(acc, wa.y, x1);
         fma_row<K>(acc, wa.z, x2); fma_row<K>(acc, wa.w, x3);
-        load_row_t<K, XT>(x + (size_t)cb.x * K, x0);
-        load_row_t<K, XT>(x + (size_t)cb.y * K, x1);
-        load_row_t<K, XT>(x + (size_t)cb.z * K, x2);
-        load_row_t<K, XT>(x + (size_t)cb.w * K, x3);
-        fma_row<K>(acc, wb.x, x0); fma_row<K>(acc, wb.y, x1);
-        fma_row<K>(acc, wb.z, x2); fma_row<K>(acc, wb.w, x3);
+        fma_row<K>(acc, wb.x, y0); fma_row<K>(acc, wb.y, y1);
+        fma_row<K>(acc, wb.z, y2); fma_row<K>(acc, wb.w, y3);
     }
     if (g < groups) {
-        const int4 ca = __ldcs(cp + 32 * g);
+        const int4 ca = ld_stream(cp + 32 * g);
         const float4 wa = load_w_group<WT>(wp + 32 * kVec * g);
         float x0[K], x1[K], x2[K], x3[K];
         load_row_t<K, XT>(x + (size_t)ca.x * K, x0);
@@ -487,27 +509,6 @@ __device__ __forceinline__ void fma_group(float (&acc)[K], const IdxT &c, const 
     fma_row<K>(acc, w.y, r1);
     fma_row<K>(acc, w.z, r2);
     fma_row<K>(acc, w.w, r3);
-}
-
-// Entry-stream loads that bypass L1 allocation: every column index and
-// weight is read exactly once per pass, so L1 keeps its capacity for the
-// gathered rows of the iterate.
-__device__ __forceinline__ int4 ld_stream(const int4 *p) {
-    int4 r;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
-    return r;
-}
-__device__ __forceinline__ uint2 ld_stream(const uint2 *p) {
-    uint2 r;
-    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
-    return r;
-}
-__device__ __forceinline__ float4 ld_stream(const float4 *p) {
-    float4 r;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
-    return r;
 }
 
 // Per-lane state of one slice row, loaded before the gather.
