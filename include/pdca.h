@@ -258,6 +258,18 @@ pdca_status pdca_lambda_max(pdca_problem *h, double *lambda_used, double *lambda
 pdca_status pdca_layout(pdca_problem *h, int64_t *sell_entries, int64_t *n_slices,
                         int32_t *sort_window, int32_t *tiled, int64_t *halo_rows, int32_t *max_halo);
 
+/* CUDA graph replay of pdca_solve: with on = 1, a call without traces (and
+ * with profiling off, a plain non-tiled handle and a non-default stream) is
+ * captured once into a CUDA graph per (outer, inner, starting buffers,
+ * coefficients) and replayed on later calls with the same key (at most 6 kept
+ * per handle, oldest dropped first).  The replay launches exactly the kernels
+ * and arguments of the direct path, so results are identical; it removes the
+ * per-launch host cost, which dominates for small graphs.  The graphs are
+ * CUDA driver objects (host and device resources the driver manages); on = 0
+ * or pdca_destroy releases them.  Default off.  When the caller's stream is
+ * itself being captured, pdca_solve launches directly into that capture. */
+pdca_status pdca_graph_enable(pdca_problem *h, int32_t on);
+
 /* Kernel timing for measurement: enable (1) / disable (0) CUDA-event timing
  * of every sweep launch of this handle; read returns the summed sweep time
  * in milliseconds and the number of timed launches since the last read, and

@@ -47,7 +47,7 @@ EXPORTS = [
     "pdca_batch_destroy", "pdca_workspace_size_like", "pdca_create_like",
     "pdca_spectral_workspace_size", "pdca_spectral_init",
     "pdca_image_graph_workspace_size", "pdca_image_graph",
-    "pdca_point_graph_workspace_size", "pdca_point_graph",
+    "pdca_point_graph_workspace_size", "pdca_point_graph", "pdca_graph_enable",
 ]
 
 
@@ -118,6 +118,7 @@ def lib():
                 "pdca_image_graph": (C.c_int, [vp, i32, i32, i32, i32, i32, i32, dbl, vp, C.c_size_t, vp, vp,
                                                vp, i64, C.POINTER(i64), vp]),
                 "pdca_point_graph_workspace_size": (C.c_int, [i64, i32, C.POINTER(C.c_size_t)]),
+                "pdca_graph_enable": (C.c_int, [vp, i32]),
                 "pdca_point_graph": (C.c_int, [vp, i64, i32, i32, i32, vp, C.c_size_t, vp, vp, vp, i64,
                                                C.POINTER(i64), vp]),
             }
@@ -383,6 +384,10 @@ class Problem:
         st, d = pdca_layout(self.h)
         _check(st, "pdca_layout")
         return d
+
+    def graphs(self, on: bool):
+        """pdca_graph_enable: replay pdca_solve through cached CUDA graphs."""
+        _check(lib().pdca_graph_enable(self.h, int(bool(on))), "pdca_graph_enable")
 
     def profile(self, on: bool):
         _check(pdca_profile_enable(self.h, on), "pdca_profile_enable")

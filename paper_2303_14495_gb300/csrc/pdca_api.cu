@@ -320,6 +320,22 @@ struct pdca_problem {
     void *mr = nullptr, *me[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
+    // pdca_solve replay cache (pdca_graph_enable): one instantiated CUDA graph
+    // per (outer, inner, starting buffers, coefficients)
+    struct SolveGraph {
+        int32_t outer, inner, cur, prev;
+        bool has_prev;
+        Coeffs cf;
+        int end_cur, end_prev;
+        uint64_t launches;
+        cudaGraphExec_t exec;
+    };
+    bool graphs_on = false;
+    std::vector<SolveGraph> graphs;
+    void drop_graphs() {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+        graphs.clear();
+    }
 
     SellView view() const {
         SellView A;
@@ -1028,6 +1044,61 @@ pdca_status pdca_step(pdca_problem *h, int32_t inner_sweeps) {
     return outer_step(h, inner_sweeps);
 }
 
+}  // extern "C"
+
+namespace {
+
+// pdca_solve through a cached CUDA graph: the launches of `outer` outer steps
+// are captured once per starting state (which of the three iterate buffers
+// hold u^t and u^{t-1}) and coefficient set, then replayed; the replay runs
+// exactly the kernels and arguments of the direct path.
+pdca_status solve_graph(pdca_problem *h, int32_t outer, int32_t inner) {
+    for (auto &g : h->graphs)
+        if (g.outer == outer && g.inner == inner && g.cur == h->cur && g.prev == h->prev &&
+            g.has_prev == h->has_prev && std::memcmp(&g.cf, &h->cf, sizeof(Coeffs)) == 0) {
+            PDCA_TRY(cudaGraphLaunch(g.exec, h->stream));
+            count_launches(g.launches);
+            h->cur = g.end_cur;
+            h->prev = g.end_prev;
+            h->has_prev = true;
+            return PDCA_OK;
+        }
+    pdca_problem::SolveGraph g{};
+    g.outer = outer;
+    g.inner = inner;
+    g.cur = h->cur;
+    g.prev = h->prev;
+    g.has_prev = h->has_prev;
+    g.cf = h->cf;
+    const uint64_t l0 = pdca_kernel_launches();
+    PDCA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    pdca_status st = PDCA_OK;
+    for (int32_t t = 0; t < outer && st == PDCA_OK; ++t) st = outer_step(h, inner);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+    if (st != PDCA_OK || ce != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        return st != PDCA_OK ? st : PDCA_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return PDCA_ERR_CUDA;
+    g.launches = pdca_kernel_launches() - l0;   // counted once at capture: they run at this first launch
+    g.end_cur = h->cur;
+    g.end_prev = h->prev;
+    if (h->graphs.size() >= 6) {
+        cudaGraphExecDestroy(h->graphs.front().exec);
+        h->graphs.erase(h->graphs.begin());
+    }
+    h->graphs.push_back(g);
+    PDCA_TRY(cudaGraphLaunch(g.exec, h->stream));
+    return PDCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 pdca_status pdca_solve(pdca_problem *h, int32_t outer_iters, int32_t inner_sweeps, double damping,
                        double *energy_trace, double *residual_trace) {
     if (!h || outer_iters < 0 || inner_sweeps < 1 || !(damping >= 0.0)) return PDCA_ERR_INVALID_ARG;
@@ -1039,6 +1110,11 @@ pdca_status pdca_solve(pdca_problem *h, int32_t outer_iters, int32_t inner_sweep
         h->cf = make_coeffs(h->prm, h->omega, h->lambda_used);
     }
     const bool tracing = energy_trace || residual_trace;
+    if (h->graphs_on && !tracing && !h->prof && !h->tiled && outer_iters > 0 && h->stream != nullptr) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        PDCA_TRY(cudaStreamIsCapturing(h->stream, &cs));
+        if (cs == cudaStreamCaptureStatusNone) return solve_graph(h, outer_iters, inner_sweeps);
+    }
     int chunk0 = 0;
     for (int32_t t = 0; t < outer_iters; ++t) {
         pdca_status st = outer_step(h, inner_sweeps);
@@ -1236,10 +1312,21 @@ void pdca_batch_destroy(pdca_batch *b) {
     delete b;
 }
 
+pdca_status pdca_graph_enable(pdca_problem *h, int32_t on) {
+    if (!h) return PDCA_ERR_INVALID_ARG;
+    if (!on) {
+        PDCA_TRY(cudaStreamSynchronize(h->stream));
+        h->drop_graphs();
+    }
+    h->graphs_on = on != 0;
+    return PDCA_OK;
+}
+
 void pdca_destroy(pdca_problem *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    h->drop_graphs();
     delete h;
 }
 
