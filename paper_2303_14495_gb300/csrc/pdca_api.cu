@@ -59,8 +59,16 @@ int64_t sell_bound(const int64_t *rp, int32_t n, int32_t sigma, int64_t max_deg)
     const int64_t windows = ((int64_t)n + sigma - 1) / sigma;
     int64_t top = std::min<int64_t>(windows, n), s = 0;
     if (max_deg <= (1 << 20)) {
-        std::vector<uint32_t> hist((size_t)max_deg + 1, 0u);
-        for (int32_t i = 0; i < n; ++i) ++hist[(size_t)(rp[i + 1] - rp[i])];
+        // per-chunk histograms in parallel (few chunks when the degree range is wide)
+        const int64_t nch = max_deg <= 4096 ? std::max<int64_t>(1, std::min<int64_t>(64, n / 65536)) : 1;
+        std::vector<std::vector<uint32_t>> part((size_t)nch, std::vector<uint32_t>((size_t)max_deg + 1, 0u));
+        host_parallel_for(nch, [&](int64_t c) {
+            const int64_t i0 = (int64_t)n * c / nch, i1 = (int64_t)n * (c + 1) / nch;
+            for (int64_t i = i0; i < i1; ++i) ++part[(size_t)c][(size_t)(rp[i + 1] - rp[i])];
+        });
+        std::vector<uint32_t> &hist = part[0];
+        for (int64_t c = 1; c < nch; ++c)
+            for (size_t d = 0; d < hist.size(); ++d) hist[d] += part[(size_t)c][d];
         for (int64_t d = max_deg; d >= 0 && top > 0; --d) {
             const int64_t take = std::min<int64_t>(top, hist[(size_t)d]);
             s += take * d;
@@ -202,11 +210,25 @@ pdca_status host_row_ptr(const int64_t *row_ptr, int32_t n, std::vector<int64_t>
     }
     const int64_t *rp = *view;
     if (rp[0] != 0) return PDCA_ERR_INVALID_ARG;
+    // row lengths in range, and the largest, over chunks in parallel
+    const int64_t chunk = 1 << 18, nch = ((int64_t)n + chunk - 1) / chunk;
+    std::vector<int64_t> cmax((size_t)nch, 0);
+    std::vector<uint8_t> cbad((size_t)nch, 0);
+    host_parallel_for(nch, [&](int64_t c) {
+        int64_t mx = 0;
+        bool bad = false;
+        for (int64_t i = c * chunk; i < std::min<int64_t>(n, (c + 1) * chunk); ++i) {
+            const int64_t d = rp[i + 1] - rp[i];
+            bad |= d < 0 || d >= (1 << 24);
+            mx = d > mx ? d : mx;
+        }
+        cmax[(size_t)c] = mx;
+        cbad[(size_t)c] = bad;
+    });
     int64_t mx = 0;
-    for (int32_t i = 0; i < n; ++i) {
-        const int64_t d = rp[i + 1] - rp[i];
-        if (d < 0 || d >= (1 << 24)) return PDCA_ERR_INVALID_ARG;
-        mx = d > mx ? d : mx;
+    for (int64_t c = 0; c < nch; ++c) {
+        if (cbad[(size_t)c]) return PDCA_ERR_INVALID_ARG;
+        mx = std::max(mx, cmax[(size_t)c]);
     }
     if (max_deg) *max_deg = mx;
     return PDCA_OK;
