@@ -341,7 +341,8 @@ pdca_status pdca_image_graph(const float *image, int32_t H, int32_t W, int32_t C
  *   w_ij = exp(-|x_i - x_j|^2 / (sigma_i sigma_j)),
  * sigma_i = distance of i to its scale_nn-th nearest neighbour (self
  * excluded), symmetrised by union (an edge where either end keeps the other).
- * Distances are screened in FP32 (a tiled product, |x|^2 + |y|^2 - 2 x.y) to
+ * Distances are screened in FP32 on the mean-centred points (a tiled product,
+ * |x|^2 + |y|^2 - 2 x.y) to
  * 3k + 8 candidates per point, then recomputed exactly in FP64 as sums of
  * squared coordinate differences; the k smallest (d2, j) are kept (equal
  * distances go to the lower index).  The weights are symmetric bit for bit.
@@ -349,12 +350,13 @@ pdca_status pdca_image_graph(const float *image, int32_t H, int32_t W, int32_t C
  *   k <= n - 1, 1 <= scale_nn <= k.
  *   workspace: DEVICE scratch of pdca_point_graph_workspace_size bytes,
  *     256-byte aligned (it holds a tile of min(4096, 2^26 / n) x n FP32
- *     distances).  row_ptr (n + 1 int64), col and w (col_capacity entries):
+ *     distances, and a centred copy of X).  row_ptr (n + 1 int64), col and w
+ *     (col_capacity entries):
  *     DEVICE outputs; 2 k n always suffices.  *nnz (host): the entries.
  * Synchronises the stream.  Errors: INVALID_ARG, OOM (workspace or
  * col_capacity; *nnz then holds the size needed), BAD_GRAPH (some sigma_i = 0:
  * i has scale_nn coincident points), CUDA. */
-pdca_status pdca_point_graph_workspace_size(int64_t n, int32_t k, size_t *bytes);
+pdca_status pdca_point_graph_workspace_size(int64_t n, int32_t dim, int32_t k, size_t *bytes);
 pdca_status pdca_point_graph(const float *X, int64_t n, int32_t dim, int32_t k, int32_t scale_nn, void *workspace,
                              size_t ws_bytes, int64_t *row_ptr, int32_t *col, float *w, int64_t col_capacity,
                              int64_t *nnz, void *stream);

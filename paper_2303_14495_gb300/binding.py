@@ -117,7 +117,7 @@ def lib():
                 "pdca_image_graph_workspace_size": (C.c_int, [i32, i32, i32, C.POINTER(C.c_size_t)]),
                 "pdca_image_graph": (C.c_int, [vp, i32, i32, i32, i32, i32, i32, dbl, vp, C.c_size_t, vp, vp,
                                                vp, i64, C.POINTER(i64), vp]),
-                "pdca_point_graph_workspace_size": (C.c_int, [i64, i32, C.POINTER(C.c_size_t)]),
+                "pdca_point_graph_workspace_size": (C.c_int, [i64, i32, i32, C.POINTER(C.c_size_t)]),
                 "pdca_graph_enable": (C.c_int, [vp, i32]),
                 "pdca_point_graph": (C.c_int, [vp, i64, i32, i32, i32, vp, C.c_size_t, vp, vp, vp, i64,
                                                C.POINTER(i64), vp]),
@@ -479,7 +479,7 @@ def point_graph(X, k: int, scale_nn: int = 7, stream=None):
     n, dim = (int(v) for v in Xc.shape)
     st = stream if stream is not None else torch.cuda.current_stream(Xc.device)
     out = C.c_size_t(0)
-    _check(lib().pdca_point_graph_workspace_size(n, int(k), C.byref(out)), "pdca_point_graph_workspace_size")
+    _check(lib().pdca_point_graph_workspace_size(n, dim, int(k), C.byref(out)), "pdca_point_graph_workspace_size")
     ws = torch.empty(int(out.value), dtype=torch.uint8, device=Xc.device)
     cap = 2 * int(k) * n
     rp = torch.empty(n + 1, dtype=torch.int64, device=Xc.device)

@@ -5,6 +5,9 @@
 //   to its m-th nearest neighbour.
 //
 // Query rows go in tiles of T rows:
+//   (the points are first centred on their mean, which leaves distances
+//   unchanged and keeps the screening product accurate for data far from
+//   the origin)
 //   dist_tile_kernel  FP32 tiled product of the query tile with all points
 //                     (64 x 64 outputs per block, 16-wide k-slabs staged in
 //                     shared memory), turned into approximate squared
@@ -32,6 +35,25 @@ namespace {
 constexpr int kPgMaxK = 32;
 constexpr int kPgMaxC = 3 * kPgMaxK + 8;
 constexpr int kTB = 64, kTK = 16;   // product tile: 64 x 64 outputs, 16-wide slabs
+
+// column means (FP64), one thread per coordinate (coalesced across threads)
+__global__ void __launch_bounds__(256)
+colmean_kernel(const float *__restrict__ X, int64_t n, int D, double *__restrict__ mean) {
+    const int d = blockIdx.x * 256 + threadIdx.x;
+    if (d >= D) return;
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += (double)__ldg(X + i * D + d);
+    mean[d] = s / (double)n;
+}
+
+// Xc = X - mean: distances are unchanged, and the screening product
+// |x|^2 + |y|^2 - 2 x.y no longer loses the distances to large norms
+__global__ void __launch_bounds__(256)
+center_kernel(const float *__restrict__ X, int64_t n, int D, const double *__restrict__ mean, float *__restrict__ Xc) {
+    const int64_t q = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (q >= n * D) return;
+    Xc[q] = (float)((double)X[q] - mean[q % D]);
+}
 
 __global__ void __launch_bounds__(256)
 sqnorm_kernel(const float *__restrict__ X, int64_t n, int D, float *__restrict__ sq) {
@@ -263,7 +285,8 @@ compact_kernel(int64_t n, const int64_t *__restrict__ off, const int32_t *__rest
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct PgWs {
-    float *sq, *dist;
+    float *sq, *dist, *xc;
+    double *mean;
     int32_t *cand, *nbr, *cnt, *fillc, *ecol, *len;
     double *nd2, *sigma, *ed2;
     int64_t *off, *bsum, *total;
@@ -273,7 +296,7 @@ struct PgWs {
 
 int tile_rows(int64_t n) { return (int)std::max<int64_t>(64, std::min<int64_t>(4096, ((int64_t)64 << 20) / n)); }
 
-PgWs pg_ws(int64_t n, int k, char *base) {
+PgWs pg_ws(int64_t n, int k, int dim, char *base) {
     PgWs s{};
     const int T = tile_rows(n), c = (int)std::min<int64_t>(n - 1, 3 * k + 8);
     size_t o = 0;
@@ -285,6 +308,7 @@ PgWs pg_ws(int64_t n, int k, char *base) {
     const size_t o_cnt = take(4 * (size_t)n), o_fill = take(4 * (size_t)n), o_len = take(4 * (size_t)n);
     const size_t o_off = take(8 * ((size_t)n + 1)), o_ecol = take(4 * cap), o_ed2 = take(8 * cap);
     const size_t o_bsum = take(8 * nb), o_tot = take(8), o_st = take(4);
+    const size_t o_xc = take(4 * (size_t)n * dim), o_mean = take(8 * (size_t)dim);
     s.bytes = o;
     if (base) {
         s.sq = reinterpret_cast<float *>(base + o_sq);
@@ -302,6 +326,8 @@ PgWs pg_ws(int64_t n, int k, char *base) {
         s.bsum = reinterpret_cast<int64_t *>(base + o_bsum);
         s.total = reinterpret_cast<int64_t *>(base + o_tot);
         s.status = reinterpret_cast<uint32_t *>(base + o_st);
+        s.xc = reinterpret_cast<float *>(base + o_xc);
+        s.mean = reinterpret_cast<double *>(base + o_mean);
     }
     return s;
 }
@@ -325,9 +351,10 @@ bool dev_ptr(const void *p) {
 
 using namespace pdca;
 
-extern "C" pdca_status pdca_point_graph_workspace_size(int64_t n, int32_t k, size_t *bytes) {
-    if (!bytes || n < 2 || n > 0x7fffffffLL || k < 1 || k > kPgMaxK || k > n - 1) return PDCA_ERR_INVALID_ARG;
-    *bytes = pg_ws(n, k, nullptr).bytes;
+extern "C" pdca_status pdca_point_graph_workspace_size(int64_t n, int32_t dim, int32_t k, size_t *bytes) {
+    if (!bytes || n < 2 || n > 0x7fffffffLL || dim < 1 || k < 1 || k > kPgMaxK || k > n - 1)
+        return PDCA_ERR_INVALID_ARG;
+    *bytes = pg_ws(n, k, dim, nullptr).bytes;
     return PDCA_OK;
 }
 
@@ -340,18 +367,20 @@ extern "C" pdca_status pdca_point_graph(const float *X, int64_t n, int32_t dim, 
     if ((reinterpret_cast<uintptr_t>(workspace) % 256) != 0) return PDCA_ERR_INVALID_ARG;
     if (!dev_ptr(X) || !dev_ptr(workspace) || !dev_ptr(row_ptr) || !dev_ptr(col) || !dev_ptr(w))
         return PDCA_ERR_INVALID_ARG;
-    const PgWs s = pg_ws(n, k, static_cast<char *>(workspace));
+    const PgWs s = pg_ws(n, k, dim, static_cast<char *>(workspace));
     if (ws_bytes < s.bytes) return PDCA_ERR_OOM;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int T = tile_rows(n), c = (int)std::min<int64_t>(n - 1, 3 * k + 8);
     const unsigned nblk = (unsigned)((n + 255) / 256);
-    count_launches(1);
-    sqnorm_kernel<<<nblk, 256, 0, st>>>(X, n, dim, s.sq);
+    count_launches(3);
+    colmean_kernel<<<(unsigned)((dim + 255) / 256), 256, 0, st>>>(X, n, dim, s.mean);
+    center_kernel<<<(unsigned)((n * dim + 255) / 256), 256, 0, st>>>(X, n, dim, s.mean, s.xc);
+    sqnorm_kernel<<<nblk, 256, 0, st>>>(s.xc, n, dim, s.sq);
     for (int64_t q0 = 0; q0 < n; q0 += T) {
         const int rows = (int)std::min<int64_t>(T, n - q0);
         const dim3 g((unsigned)((n + kTB - 1) / kTB), (unsigned)((rows + kTB - 1) / kTB));
         count_launches(3);
-        dist_tile_kernel<<<g, 256, 0, st>>>(X, n, dim, q0, rows, s.sq, s.dist);
+        dist_tile_kernel<<<g, 256, 0, st>>>(s.xc, n, dim, q0, rows, s.sq, s.dist);
         candidate_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(s.dist, n, rows, c, s.cand);
         rerank_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(X, n, dim, q0, rows, c, k, s.cand, s.nbr, s.nd2);
     }

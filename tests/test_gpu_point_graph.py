@@ -54,6 +54,16 @@ def test_random_clouds(B, n, d, k, m):
     assert_same(gpu_graph(B, X, k, m), (rp, col, w))
 
 
+def test_far_from_origin(B):
+    """Data offset by 1000 in every coordinate: the FP32 screen works on the
+    mean-centred points, so the candidates still contain the exact k nearest."""
+    rng = np.random.default_rng(77)
+    X = (rng.normal(size=(800, 20)) + 1000.0).astype(np.float32)
+    assert separated(X, 10)
+    rp, col, w, _ = PG.point_graph(X, 10, 7)
+    assert_same(gpu_graph(B, X, 10, 7), (rp, col, w))
+
+
 def test_lattice_ties(B):
     """Integer lattice in 2-D: many exact ties, broken by the lower index."""
     g = np.stack(np.meshgrid(np.arange(23), np.arange(19), indexing="ij"), -1).reshape(-1, 2).astype(np.float32)
