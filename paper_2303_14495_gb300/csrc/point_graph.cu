@@ -9,8 +9,8 @@
 //   unchanged and keeps the screening product accurate for data far from
 //   the origin)
 //   dist_tile_kernel  FP32 tiled product of the query tile with all points
-//                     (64 x 64 outputs per block, 16-wide k-slabs staged in
-//                     shared memory), turned into approximate squared
+//                     (128 x 128 outputs per block, 8 x 8 per thread, 8-wide
+//                     k-slabs staged in shared memory), turned into approximate squared
 //                     distances |x|^2 + |y|^2 - 2 x.y in the epilogue;
 //   candidate_kernel  one warp per query: each lane keeps its c smallest, a
 //                     c-round warp merge gives the query's c candidates
@@ -34,7 +34,7 @@ namespace {
 
 constexpr int kPgMaxK = 32;
 constexpr int kPgMaxC = 3 * kPgMaxK + 8;
-constexpr int kTB = 64, kTK = 16;   // product tile: 64 x 64 outputs, 16-wide slabs
+constexpr int kTB = 128, kTK = 8;   // product tile: 128 x 128 outputs, 8-wide slabs
 
 // column means (FP64), one thread per coordinate (coalesced across threads)
 __global__ void __launch_bounds__(256)
@@ -67,49 +67,69 @@ sqnorm_kernel(const float *__restrict__ X, int64_t n, int D, float *__restrict__
     sq[i] = s;
 }
 
-// out[t * n + j] = sq[q0 + t] + sq[j] - 2 x_{q0+t} . x_j  (+inf for j == q0 + t)
+// out[t * n + j] = sq[q0 + t] + sq[j] - 2 x_{q0+t} . x_j  (+inf for j == q0 + t).
+// Block: 128 query rows x 128 points, 256 threads with 8 x 8 outputs each;
+// 8-wide k-slabs of both operands staged in shared memory (transposed, so
+// each thread reads its 8 + 8 operands as float4 pairs), the next slab's
+// global loads issued before the current slab's products.
 __global__ void __launch_bounds__(256)
 dist_tile_kernel(const float *__restrict__ X, int64_t n, int D, int64_t q0, int T, const float *__restrict__ sq,
                  float *__restrict__ out) {
-    __shared__ float As[kTK][kTB + 4];
-    __shared__ float Bs[kTK][kTB + 4];
+    __shared__ __align__(16) float As[kTK][kTB];
+    __shared__ __align__(16) float Bs[kTK][kTB];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int64_t row0 = (int64_t)blockIdx.y * kTB, col0 = (int64_t)blockIdx.x * kTB;   // row: query t, col: point j
-    float acc[4][4] = {};
+    // loader mapping: 128 rows x 8 columns per operand = 1024 values, 4 per thread
+    const int lr = threadIdx.x / 2, lc = (threadIdx.x % 2) * 4;
+    const int64_t qa = q0 + row0 + lr, pb = col0 + lr;
+    const bool arow = row0 + lr < T, brow = pb < n;
+    float ra[4], rb[4];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int kk = k0 + lc + u;
+            ra[u] = (arow && kk < D) ? __ldg(X + qa * D + kk) : 0.0f;
+            rb[u] = (brow && kk < D) ? __ldg(X + pb * D + kk) : 0.0f;
+        }
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = 0.0f;
+    fetch(0);
     for (int k0 = 0; k0 < D; k0 += kTK) {
-        // 64 x 16 slabs, one element per thread per 4 passes
-        for (int e = threadIdx.x; e < kTB * kTK; e += 256) {
-            const int r = e / kTK, c = e % kTK;
-            const int64_t qa = q0 + row0 + r, pb = col0 + r;
-            As[c][r] = (row0 + r < T && k0 + c < D) ? __ldg(X + qa * D + k0 + c) : 0.0f;
-            Bs[c][r] = (pb < n && k0 + c < D) ? __ldg(X + pb * D + k0 + c) : 0.0f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            As[lc + u][lr] = ra[u];
+            Bs[lc + u][lr] = rb[u];
         }
         __syncthreads();
+        if (k0 + kTK < D) fetch(k0 + kTK);
 #pragma unroll
         for (int c = 0; c < kTK; ++c) {
-            float a[4], b[4];
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[c][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[c][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[c][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[c][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                a[u] = As[c][ty * 4 + u];
-                b[u] = Bs[c][tx * 4 + u];
-            }
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int64_t t = row0 + ty * 4 + u;
+    for (int u = 0; u < 8; ++u) {
+        const int64_t t = row0 + (u < 4 ? ty * 4 + u : 64 + ty * 4 + u - 4);
         if (t >= T) continue;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int64_t j = col0 + tx * 4 + v;
+        for (int v = 0; v < 8; ++v) {
+            const int64_t j = col0 + (v < 4 ? tx * 4 + v : 64 + tx * 4 + v - 4);
             if (j >= n) continue;
-            const float d = (q0 + t == j) ? INFINITY : sq[q0 + t] + sq[j] - 2.0f * acc[u][v];
-            out[t * n + j] = d;
+            out[t * n + j] = (q0 + t == j) ? INFINITY : sq[q0 + t] + sq[j] - 2.0f * acc[u][v];
         }
     }
 }
