@@ -349,7 +349,7 @@ pdca_status pdca_image_graph(const float *image, int32_t H, int32_t W, int32_t C
  *   X: DEVICE, n x dim float32, row-major; 2 <= n < 2^31, 1 <= k <= 32,
  *   k <= n - 1, 1 <= scale_nn <= k.
  *   workspace: DEVICE scratch of pdca_point_graph_workspace_size bytes,
- *     256-byte aligned (it holds a tile of min(4096, 2^26 / n) x n FP32
+ *     256-byte aligned (it holds a tile of min(8192, 2^28 / n) x n FP32
  *     distances, and a centred copy of X).  row_ptr (n + 1 int64), col and w
  *     (col_capacity entries):
  *     DEVICE outputs; 2 k n always suffices.  *nnz (host): the entries.

@@ -135,6 +135,7 @@ dist_tile_kernel(const float *__restrict__ X, int64_t n, int D, int64_t q0, int 
 }
 
 // one warp per query row of the tile: the c smallest approximate distances
+// (ties in order of the lanes' scans; the exact re-rank decides afterwards)
 __global__ void __launch_bounds__(256)
 candidate_kernel(const float *__restrict__ dist, int64_t n, int T, int c, int32_t *__restrict__ cand) {
     const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -143,10 +144,10 @@ candidate_kernel(const float *__restrict__ dist, int64_t n, int T, int c, int32_
     float bd[kPgMaxC];
     int32_t bj[kPgMaxC];
     int cnt = 0;
+    float thr = INFINITY;   // the lane's current c-th smallest (kept in a register)
     const float *row = dist + (int64_t)t * n;
-    for (int64_t j = lane; j < n; j += 32) {
-        const float d = row[j];
-        if (cnt == c && !(d < bd[c - 1])) continue;
+    auto consider = [&](float d, int64_t j) {
+        if (!(d < thr) && cnt == c) return;
         int pos = cnt < c ? cnt : c - 1;
         while (pos > 0 && bd[pos - 1] > d) {
             bd[pos] = bd[pos - 1];
@@ -156,7 +157,18 @@ candidate_kernel(const float *__restrict__ dist, int64_t n, int T, int c, int32_
         bd[pos] = d;
         bj[pos] = (int32_t)j;
         if (cnt < c) ++cnt;
+        if (cnt == c) thr = bd[c - 1];
+    };
+    int64_t j = lane;
+    // eight loads in flight per lane, then the (mostly rejecting) comparisons
+    for (; j + 7 * 32 < n; j += 8 * 32) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcs(row + j + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) consider(v[u], j + 32 * u);
     }
+    for (; j < n; j += 32) consider(row[j], j);
     // merge: c rounds, each takes the smallest head among the lanes
     int head = 0;
     for (int q = 0; q < c; ++q) {
@@ -314,7 +326,7 @@ struct PgWs {
     size_t bytes;
 };
 
-int tile_rows(int64_t n) { return (int)std::max<int64_t>(64, std::min<int64_t>(4096, ((int64_t)64 << 20) / n)); }
+int tile_rows(int64_t n) { return (int)std::max<int64_t>(64, std::min<int64_t>(8192, ((int64_t)1 << 28) / n)); }
 
 PgWs pg_ws(int64_t n, int k, int dim, char *base) {
     PgWs s{};
