@@ -108,6 +108,19 @@ enum { PDCA_REORDER_NONE = 0, PDCA_REORDER_BFS = 1 };
  *                    16-bit local columns. */
 enum { PDCA_TILING_AUTO = 0, PDCA_TILING_OFF = 1, PDCA_TILING_ON = 2 };
 
+/* Order of the entries inside each row of the sliced-ELL operator (a layout
+ * choice; the sum over a row's neighbours is the same up to FP32 rounding):
+ *   PDCA_ENTRIES_SPREAD (default) the entries of each quarter of a slice
+ *                       (8 rows: the rows one L1 wavefront serves when a
+ *                       neighbour row of the iterate takes 16 bytes) are
+ *                       ordered so that, at each position, their columns
+ *                       differ modulo 8 or fall in the same group of 8 rows
+ *                       (fewer bank conflicts in the gathers).  The order
+ *                       depends on the graph only, not on K or the precision,
+ *                       so problems sharing an operator see the same order;
+ *   PDCA_ENTRIES_CSR    the order of the caller's CSR columns. */
+enum { PDCA_ENTRIES_SPREAD = 0, PDCA_ENTRIES_CSR = 1 };
+
 /* Arithmetic of the sweeps.
  *   PDCA_FP32               FP32 pre-scaled weights and iterates, FP32
  *                           accumulation, FP64 accumulation across warps in the
@@ -150,7 +163,7 @@ typedef struct {
     int32_t reorder;     /* PDCA_REORDER_BFS (default) / PDCA_REORDER_NONE             */
     int32_t tiling;      /* PDCA_TILING_AUTO (default) / _OFF / _ON; _ON needs the
                             normalized Laplacian                                     */
-    int32_t reserved_;
+    int32_t entry_order; /* PDCA_ENTRIES_SPREAD (default) / PDCA_ENTRIES_CSR              */
     double step_k;       /* step size k > 0 of the DCA with step size, or 0 for the
                             infinite step size (Prop. nopre, the default)            */
 } pdca_params;

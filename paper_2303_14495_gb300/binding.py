@@ -36,6 +36,7 @@ PDCA_JACOBI_DAMPED, PDCA_JACOBI_PERTURBED, PDCA_RICHARDSON = 0, 1, 2
 PDCA_FP32, PDCA_MIXED_BF16W_FP16U, PDCA_MIXED_BF16W_BF16U = 0, 1, 2
 PDCA_REORDER_NONE, PDCA_REORDER_BFS = 0, 1
 PDCA_TILING_AUTO, PDCA_TILING_OFF, PDCA_TILING_ON = 0, 1, 2
+PDCA_ENTRIES_SPREAD, PDCA_ENTRIES_CSR = 0, 1
 
 # every symbol include/pdca.h declares
 EXPORTS = [
@@ -64,7 +65,7 @@ class pdca_params(C.Structure):
         ("damping", C.c_double), ("delta0", C.c_double), ("lambda_max", C.c_double),
         ("power_iters", C.c_int32), ("precision", C.c_int32),
         ("sort_window", C.c_int32), ("reorder", C.c_int32), ("tiling", C.c_int32),
-        ("reserved_", C.c_int32), ("step_k", C.c_double),
+        ("entry_order", C.c_int32), ("step_k", C.c_double),
     ]
 
 
@@ -151,7 +152,7 @@ def _ptr(a) -> Optional[int]:
 def make_params(eps=1.0, c=3.0, eta=1.0, precond=PDCA_JACOBI_PERTURBED, damping=0.5, delta0=1e-6,
                 lambda_max=0.0, power_iters=150, laplacian=PDCA_LAP_NORMALIZED,
                 precision=PDCA_FP32, sort_window=0, reorder=PDCA_REORDER_BFS,
-                tiling=PDCA_TILING_AUTO, step_k=0.0) -> pdca_params:
+                tiling=PDCA_TILING_AUTO, step_k=0.0, entry_order=PDCA_ENTRIES_SPREAD) -> pdca_params:
     p = pdca_params()
     lib().pdca_default_params(C.byref(p))
     p.eps, p.c, p.eta = float(eps), float(c), float(eta)
@@ -159,6 +160,7 @@ def make_params(eps=1.0, c=3.0, eta=1.0, precond=PDCA_JACOBI_PERTURBED, damping=
     p.lambda_max, p.power_iters = float(lambda_max), int(power_iters)
     p.laplacian, p.precision, p.sort_window = int(laplacian), int(precision), int(sort_window)
     p.reorder, p.tiling, p.step_k = int(reorder), int(tiling), float(step_k)
+    p.entry_order = int(entry_order)
     return p
 
 

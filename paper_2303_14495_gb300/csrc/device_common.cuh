@@ -511,6 +511,27 @@ __device__ __forceinline__ void fma_group(float (&acc)[K], const IdxT &c, const 
     fma_row<K>(acc, w.w, r3);
 }
 
+// Slices of a block's range, handed out to its warps in order: a warp takes
+// the next untaken slot when it finishes one (a shared-memory counter), so a
+// warp with short rows does not idle while another works on long ones, and
+// the block retires as soon as the range is done.  The first slot of warp w
+// is w; f(slice) runs for every slice of [first, first + count) that exists.
+template <class F>
+__device__ __forceinline__ void for_block_slices(int first, int count, int n_slices, int *next_slot, F &&f) {
+    if (threadIdx.x == 0) *next_slot = kWarpsPerBlock;
+    __syncthreads();
+    int slot = threadIdx.x >> 5;
+#pragma unroll 1
+    while (slot < count) {
+        const int slice = first + slot;
+        if (slice >= n_slices) return;
+        f(slice);
+        int nxt = 0;
+        if ((threadIdx.x & 31) == 0) nxt = atomicAdd(next_slot, 1);
+        slot = __shfl_sync(0xffffffffu, nxt, 0);
+    }
+}
+
 // Per-lane state of one slice row, loaded before the gather.
 template <int K, class IdxT>
 struct SliceRow {

@@ -130,6 +130,7 @@ pdca_status check_params(const pdca_params &p) {
     if (p.reorder != PDCA_REORDER_NONE && p.reorder != PDCA_REORDER_BFS) return PDCA_ERR_INVALID_ARG;
     if (p.tiling < PDCA_TILING_AUTO || p.tiling > PDCA_TILING_ON) return PDCA_ERR_INVALID_ARG;
     if (p.tiling == PDCA_TILING_ON && p.reorder != PDCA_REORDER_BFS) return PDCA_ERR_INVALID_ARG;
+    if (p.entry_order != PDCA_ENTRIES_SPREAD && p.entry_order != PDCA_ENTRIES_CSR) return PDCA_ERR_INVALID_ARG;
     return PDCA_OK;
 }
 
@@ -729,7 +730,7 @@ void pdca_default_params(pdca_params *p) {
     p->sort_window = 0;
     p->reorder = PDCA_REORDER_BFS;
     p->tiling = PDCA_TILING_AUTO;
-    p->reserved_ = 0;
+    p->entry_order = PDCA_ENTRIES_SPREAD;
     p->step_k = 0.0;
 }
 
@@ -888,6 +889,12 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
                          h->mixed ? reinterpret_cast<__nv_bfloat16 *>(h->sell_w) : nullptr, h->self,
                          h->tiled ? nullptr : h->dsq, h->rowinfo, s_status, sm);
     if (pe != cudaSuccess) return fail(PDCA_ERR_CUDA);
+    if (prm.entry_order == PDCA_ENTRIES_SPREAD &&
+        launch_spread(L.n_pad, h->slice_off, h->rowinfo, h->tiled ? nullptr : h->sell_col,
+                      h->tiled ? const_cast<uint16_t *>(h->tv.lcol) : nullptr, h->tv.halo_off, h->tv.halo_idx,
+                      h->mixed ? nullptr : h->sell_w, h->mixed ? reinterpret_cast<__nv_bfloat16 *>(h->sell_w) : nullptr,
+                      sm) != cudaSuccess)
+        return fail(PDCA_ERR_CUDA);
     if (prm.precond == PDCA_RICHARDSON) {
         if (prm.lambda_max > 0) {
             h->lambda_used = prm.lambda_max;

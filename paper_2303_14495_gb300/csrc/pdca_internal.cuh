@@ -222,6 +222,13 @@ cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32
                               const int64_t *halo_off, const int32_t *halo_idx, uint16_t *lcol,
                               float *sell_w, uint32_t *rowinfo, uint32_t *status, cudaStream_t st);
 
+// Entry order for the gathers (PDCA_ENTRIES_SPREAD), in place after the pack.
+// Exactly one of sell_col (plain form) and lcol (tiled form, with its halo
+// lists) is given, and exactly one of sell_w (FP32) and sell_wb (BF16).
+cudaError_t launch_spread(int32_t n_pad, const int64_t *slice_off, const uint32_t *rowinfo,
+                          int32_t *sell_col, uint16_t *lcol, const int64_t *halo_off, const int32_t *halo_idx,
+                          float *sell_w, __nv_bfloat16 *sell_wb, cudaStream_t st);
+
 // f(0) .. f(count - 1) on the host's threads (index order per thread is
 // fixed, so results written per index do not depend on the thread count).
 void host_parallel_for(int64_t count, const std::function<void(int64_t)> &f);

@@ -5,6 +5,7 @@
 //   window_sort_kernel  renumbering: rows sorted by degree inside windows;
 //   pack_kernel         sliced-ELL with w_ij / sqrt(d_i d_j) (L_s) or w_ij plus
 //                       the per-row d_i (L), and the row tags;
+//   spread_kernel       entry order inside rows for conflict-light gathers;
 //   init_u_kernel       u^0 (prior on labelled rows, centre elsewhere).
 #include "pdca_internal.cuh"
 
@@ -225,6 +226,89 @@ __global__ void pack_tiled_kernel(int32_t n_pad, const int64_t *__restrict__ row
 // Row tags of a problem that shares another problem's operator: the row
 // lengths come from the base's rowinfo, the tags from the new fidelity data
 // (original node order, checked like the validation kernel does).
+// One thread per quarter of a slice (S = 8 lanes: the rows whose 16-byte
+// neighbour rows one L1 wavefront serves).  Neighbour row c lies in group
+// c / S of S consecutive rows at slot c % S; two rows of the quarter read at
+// the same position conflict when they use the same slot of different groups.
+// Position by position, each row (in lane order) takes its first remaining
+// entry, looking at most kSpreadLook ahead, whose slot is free or holds the
+// same group; without one it keeps its entry.  Rows are permuted in place
+// (column and weight together); padding entries stay where they are.  The
+// choice reads global columns only, so the plain and tiled forms get the same
+// order, and it does not depend on K or the precision.
+constexpr int kSpreadLook = 64;
+constexpr int kSpreadLanes = 8;   // S
+
+__global__ void spread_kernel(int32_t n_slices, const int64_t *__restrict__ slice_off,
+                              const uint32_t *__restrict__ rowinfo, int32_t *__restrict__ sell_col,
+                              uint16_t *__restrict__ lcol, const int64_t *__restrict__ halo_off,
+                              const int32_t *__restrict__ halo_idx, float *__restrict__ sell_w,
+                              __nv_bfloat16 *__restrict__ sell_wb) {
+    constexpr int S = kSpreadLanes, groups = kSliceRows / kSpreadLanes;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_slices * groups) return;
+    const int64_t s = t / groups;
+    const int32_t lane0 = (int32_t)(t % groups) * S;
+    const int64_t base = slice_off[s];
+    const int64_t h0 = lcol ? halo_off[(s * kSliceRows) / kTileRows] : 0;
+    int32_t len[S];
+    int32_t maxlen = 0;
+#pragma unroll
+    for (int32_t l = 0; l < S; ++l) {
+        len[l] = (int32_t)(rowinfo[s * kSliceRows + lane0 + l] >> 8);
+        maxlen = max(maxlen, len[l]);
+    }
+    auto at = [&](int32_t lane, int32_t j) {
+        return base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
+    };
+    auto gcol = [&](int64_t a) { return lcol ? halo_idx[h0 + lcol[a]] : sell_col[a]; };
+    int32_t group_at[S];
+    for (int32_t p = 0; p < maxlen; ++p) {
+        uint32_t used = 0;
+#pragma unroll
+        for (int32_t l = 0; l < S; ++l) {
+            if (p >= len[l]) continue;
+            const int32_t lane = lane0 + l;
+            const int32_t lim = min(len[l], p + kSpreadLook);
+            int32_t pick = -1, slot = 0, grp = 0;
+            for (int32_t j = p; j < lim; ++j) {
+                const int32_t c = gcol(at(lane, j));
+                slot = c % S;
+                grp = c / S;
+                if (!((used >> slot) & 1u) || group_at[slot] == grp) {
+                    pick = j;
+                    break;
+                }
+            }
+            if (pick < 0) continue;   // every candidate conflicts: keep the entry at p
+            if (!((used >> slot) & 1u)) {
+                used |= 1u << slot;
+                group_at[slot] = grp;
+            }
+            if (pick == p) continue;
+            const int64_t a = at(lane, p), b = at(lane, pick);
+            if (lcol) {
+                const uint16_t x = lcol[a];
+                lcol[a] = lcol[b];
+                lcol[b] = x;
+            } else {
+                const int32_t x = sell_col[a];
+                sell_col[a] = sell_col[b];
+                sell_col[b] = x;
+            }
+            if (sell_wb) {
+                const __nv_bfloat16 x = sell_wb[a];
+                sell_wb[a] = sell_wb[b];
+                sell_wb[b] = x;
+            } else {
+                const float x = sell_w[a];
+                sell_w[a] = sell_w[b];
+                sell_w[b] = x;
+            }
+        }
+    }
+}
+
 __global__ void retag_kernel(int32_t n_pad, int32_t K, const uint32_t *__restrict__ base_rowinfo,
                              const int32_t *__restrict__ perm, const uint8_t *__restrict__ mask,
                              const int32_t *__restrict__ labels, uint32_t *__restrict__ rowinfo,
@@ -307,6 +391,18 @@ cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32
     pack_tiled_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, mask, labels, perm,
                                                            iperm, slice_off, halo_off, halo_idx, lcol, sell_w,
                                                            rowinfo, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spread(int32_t n_pad, const int64_t *slice_off, const uint32_t *rowinfo, int32_t *sell_col,
+                          uint16_t *lcol, const int64_t *halo_off, const int32_t *halo_idx, float *sell_w,
+                          __nv_bfloat16 *sell_wb, cudaStream_t st) {
+    const int32_t n_slices = n_pad / kSliceRows;
+    const int64_t threads = (int64_t)n_slices * (kSliceRows / kSpreadLanes);
+    if (threads == 0) return cudaSuccess;
+    count_launches(1);
+    spread_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n_slices, slice_off, rowinfo, sell_col, lcol,
+                                                                     halo_off, halo_idx, sell_w, sell_wb);
     return cudaGetLastError();
 }
 

@@ -42,19 +42,19 @@ using namespace dev;
 // and while a lane works on two entry groups the next two are already in
 // flight.
 
-// plain form: one warp per slice, 8 slices per block (the same slice body as
-// the batched kernel)
+// plain form: one warp per slice at a time; a block owns iters x 8
+// consecutive slices (32 = one renumbering block of 1024 rows at the usual
+// iters = 4) and its warps take them from a shared queue (the same slice
+// body as the batched kernel)
 template <int K, bool PROJECT, bool UN>
 __global__ void __launch_bounds__(kBlockThreads, PDCA_SWEEP_MIN_BLOCKS)
 sweep_kernel(const SellView A, const Coeffs cf, const float *__restrict__ v_src,
              const float *__restrict__ u_t, float *__restrict__ v_dst, int iters) {
-    const int first = blockIdx.x * kWarpsPerBlock * iters + (threadIdx.x >> 5);
-#pragma unroll 1
-    for (int it = 0; it < iters; ++it) {
-        const int slice = first + it * kWarpsPerBlock;
-        if (slice >= A.n_slices) return;
+    __shared__ int next_slot;
+    const int count = kWarpsPerBlock * iters;
+    for_block_slices(blockIdx.x * count, count, A.n_slices, &next_slot, [&](int slice) {
         fp32_sweep_slice<K, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, v_src, u_t, v_dst);
-    }
+    });
 }
 
 // tiled form: one block per tile of 16 slices (one per warp); the halo of

@@ -95,7 +95,7 @@ def test_create_rejects_before_device_work(B):
     assert st == 4
     # unknown Laplacian, tiled unnormalized Laplacian, bad step size / negative
     # eps / unaligned workspace
-    for bad in (P(laplacian=2), P(laplacian=1, tiling=B.PDCA_TILING_ON), P(step_k=-1.0),
+    for bad in (P(laplacian=2), P(laplacian=1, tiling=B.PDCA_TILING_ON), P(step_k=-1.0), P(entry_order=2),
                 P(step_k=float("nan")), P(step_k=float("inf"))):
         st, _ = B.pdca_create(rp, col, w, 64, 1, mask, lab, bad, C.c_void_p(addr), 1 << 16, 0)
         assert st == 1

@@ -85,6 +85,8 @@ LAYOUTS = {
     "tiled": dict(reorder=1, tiling=2),
     "bfs_plain": dict(reorder=1, tiling=0),
     "window_sort": dict(reorder=0, tiling=0),
+    "csr_entries": dict(reorder=1, tiling=0, entry_order=1),
+    "tiled_csr_entries": dict(reorder=1, tiling=2, entry_order=1),
 }
 
 
@@ -98,7 +100,7 @@ def test_random_graph_sizes(B, n, K, layout):
     lab = rng.integers(0, max(K, 2), size=n).astype(np.int32)
     gpu, ref = make_pair(B, rp, col, w, K, mask, lab, 1.0, 5.0, 4.0, B.PDCA_JACOBI_PERTURBED,
                          **LAYOUTS[layout])
-    assert gpu.layout()["tiled"] == (layout == "tiled")
+    assert gpu.layout()["tiled"] == layout.startswith("tiled")
     run_parity(gpu, ref, 4, 3)
 
 
@@ -145,23 +147,25 @@ def test_sort_windows(B, sw):
     run_parity(gpu, ref, 3, 3)
 
 
-@pytest.mark.parametrize("K", [1, 4, 10])
-def test_tiled_equals_plain_bitwise(B, K):
+@pytest.mark.parametrize("K,entries", [(1, 0), (4, 0), (10, 0), (4, 1)])
+def test_tiled_equals_plain_bitwise(B, K, entries):
     """The tiled and plain kernels add the same products in the same order, so
-    on the same renumbering their iterates agree bit for bit."""
+    on the same renumbering (and the same entry order) their iterates agree
+    bit for bit."""
     wl = make_workload("voronoi2048", size=192)
     rng = np.random.default_rng(K)
     lab = rng.integers(0, K if K > 1 else 2, size=wl.n).astype(np.int32)
     out = {}
-    for mode in ("tiled", "bfs_plain"):
+    for mode in (("tiled", "bfs_plain") if entries == 0 else ("tiled_csr_entries", "csr_entries")):
         prm = B.make_params(eps=1.0, eta=50.0, c=52.0, precond=B.PDCA_RICHARDSON, lambda_max=1.99,
                             **LAYOUTS[mode])
         g = B.Problem(wl.row_ptr, wl.col, wl.w, K, wl.fid_mask, lab, prm)
-        assert g.layout()["tiled"] == (mode == "tiled")
+        assert g.layout()["tiled"] == mode.startswith("tiled")
         g.solve(3, 4)
         out[mode] = (g.get_u(), g.energy())
-    np.testing.assert_array_equal(out["tiled"][0], out["bfs_plain"][0])
-    assert out["tiled"][1][0] == out["bfs_plain"][1][0]
+    (ut, ft), (up, fp) = out.values()
+    np.testing.assert_array_equal(ut, up)
+    assert ft[0] == fp[0]
 
 
 def test_tiling_with_oversized_halos(B):
