@@ -167,6 +167,9 @@ cudaError_t launch_permute_out(int K, int32_t n, const float *u, const int32_t *
 cudaError_t launch_permute_in(int K, int32_t n, int32_t n_pad, const float *in,
                               const int32_t *perm, float *u, cudaStream_t st);
 int energy_blocks(int32_t n_slices);
+// blocks of the kernels whose block takes sweep_iters() groups of 8 slices
+// from a queue (<= energy_blocks)
+int queue_blocks(int32_t n_slices);
 
 // --- batched passes (batch_kernels.cu) -------------------------------------
 // One problem's pass inside a batched launch.  A launch advances every

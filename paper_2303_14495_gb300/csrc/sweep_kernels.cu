@@ -131,11 +131,16 @@ __device__ __forceinline__ void energy_row(const SellView &A, const Coeffs &cf, 
 template <int K, class WT>
 __global__ void __launch_bounds__(kBlockThreads)
 energy_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u,
-              const float *__restrict__ u_prev, double *__restrict__ partials) {
-    const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+              const float *__restrict__ u_prev, double *__restrict__ partials, int iters) {
+    // slices from the block's queue, sums per slice slot, added in slot order
+    // (as in power_spmv_kernel)
+    __shared__ int next_slot;
+    __shared__ double slot_sum[kWarpsPerBlock * PDCA_SWEEP_MAX_ITERS][6];
+    const int count = kWarpsPerBlock * iters;
+    const int first = blockIdx.x * count;
     const int lane = threadIdx.x & 31;
-    float red[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (slice < A.n_slices) {
+    for (int i = threadIdx.x; i < count * 6; i += blockDim.x) slot_sum[i / 6][i % 6] = 0.0;
+    for_block_slices(first, count, A.n_slices, &next_slot, [&](int slice) {
         float acc[K];
         if constexpr (std::is_same<WT, float>::value) {
             // the sweeps' pipelined slice body (same summation order)
@@ -145,9 +150,20 @@ energy_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u,
         } else {
             gather_row_sum<K, WT, float>(A, A.slice_off[slice], row_len(A, slice, lane), lane, u, acc);
         }
+        float red[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         energy_row<K>(A, cf, slice, lane, acc, u, u_prev, red);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float t = warp_sum_f(red[k]);
+            if (lane == 0) slot_sum[slice - first][k] = (double)t;
+        }
+    });
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double t = 0.0;
+        for (int q = 0; q < count; ++q) t += slot_sum[q][threadIdx.x];
+        partials[(size_t)blockIdx.x * kRedSlots + threadIdx.x] = t;
     }
-    block_sum_store<6>(red, partials + (size_t)blockIdx.x * kRedSlots);
 }
 
 template <int K>
@@ -287,14 +303,23 @@ __device__ __forceinline__ void power_row(const SellView &A, int slice, int lane
     }
 }
 
+// A block owns iters x 8 consecutive slices, taken by its warps from a
+// shared queue; each slice's three sums land in a slot of their own, and the
+// block adds its slots in slot order, so the partial (and the estimate) does
+// not depend on which warp took which slice.
 template <class WT>
 __global__ void __launch_bounds__(kBlockThreads)
 power_spmv_kernel(const SellView A, const float *__restrict__ x, double *scale, float *__restrict__ y,
-                  double *__restrict__ partials, unsigned *ticket, double *lambda) {
-    const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+                  double *__restrict__ partials, unsigned *ticket, double *lambda, int iters) {
+    __shared__ int next_slot;
+    __shared__ double slot_sum[kWarpsPerBlock * PDCA_SWEEP_MAX_ITERS][3];
+    const int count = kWarpsPerBlock * iters;
+    const int first = blockIdx.x * count;
     const int lane = threadIdx.x & 31;
-    float red[3] = {0.f, 0.f, 0.f};
-    if (slice < A.n_slices) {
+    for (int i = threadIdx.x; i < count * 3; i += blockDim.x) slot_sum[i / 3][i % 3] = 0.0;
+    const float s = (float)__ldcg(scale);
+    // (the queue's opening barrier orders the zeroing before any slot store)
+    for_block_slices(first, count, A.n_slices, &next_slot, [&](int slice) {
         float acc[1];
         if constexpr (std::is_same<WT, float>::value) {
             // the sweeps' pipelined slice body (same summation order)
@@ -304,9 +329,20 @@ power_spmv_kernel(const SellView A, const float *__restrict__ x, double *scale, 
         } else {
             gather_row_sum<1, WT, float>(A, A.slice_off[slice], row_len(A, slice, lane), lane, x, acc);
         }
-        power_row(A, slice, lane, acc[0], (float)__ldcg(scale), x, y, red);
+        float red[3] = {0.f, 0.f, 0.f};
+        power_row(A, slice, lane, acc[0], s, x, y, red);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float t = warp_sum_f(red[k]);
+            if (lane == 0) slot_sum[slice - first][k] = (double)t;
+        }
+    });
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int q = 0; q < count; ++q) t += slot_sum[q][threadIdx.x];
+        partials[(size_t)blockIdx.x * kRedSlots + threadIdx.x] = t;
     }
-    block_sum_store<3>(red, partials + (size_t)blockIdx.x * kRedSlots);
     power_last_block<kBlockThreads>(partials, ticket, scale, lambda);
 }
 
@@ -427,11 +463,13 @@ cudaError_t energy_k(const SellView &A, const TileView *T, const Coeffs &cf, con
         if (e != cudaSuccess) return e;
         energy_tiled_kernel<K><<<T->n_tiles, kTileThreads, sm, st>>>(A, *T, cf, u, u_prev, partials);
     } else {
+        const int iters = sweep_iters(A.n_slices);
         if (A.wb)
-            energy_kernel<K, __nv_bfloat16><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, cf, u, u_prev,
-                                                                                                  partials);
+            energy_kernel<K, __nv_bfloat16><<<queue_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, cf, u, u_prev,
+                                                                                                 partials, iters);
         else
-            energy_kernel<K, float><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, cf, u, u_prev, partials);
+            energy_kernel<K, float><<<queue_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, cf, u, u_prev, partials,
+                                                                                        iters);
     }
     return cudaGetLastError();
 }
@@ -446,7 +484,12 @@ cudaError_t labels_k(int32_t n, const float *u, const int32_t *perm, int32_t *ou
 
 int energy_blocks(int32_t n_slices) { return (n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock; }
 
-int reduce_parts(const SellView &A, const TileView *T) { return T ? T->n_tiles : energy_blocks(A.n_slices); }
+int queue_blocks(int32_t n_slices) {
+    const int per_block = kWarpsPerBlock * sweep_iters(n_slices);
+    return (n_slices + per_block - 1) / per_block;
+}
+
+int reduce_parts(const SellView &A, const TileView *T) { return T ? T->n_tiles : queue_blocks(A.n_slices); }
 
 
 #define PDCA_DISPATCH_K(K, CALL)                                                      \
@@ -503,12 +546,14 @@ cudaError_t launch_power_spmv(const SellView &A, const TileView *T, const float 
         power_spmv_tiled_kernel<<<T->n_tiles, kTileThreads, sm, st>>>(A, *T, x, scale, y, partials, ticket,
                                                                         lambda);
     } else {
+        const int iters = sweep_iters(A.n_slices);
+        const int blocks = queue_blocks(A.n_slices);
         if (A.wb)
-            power_spmv_kernel<__nv_bfloat16><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(
-                A, x, scale, y, partials, ticket, lambda);
+            power_spmv_kernel<__nv_bfloat16><<<blocks, kBlockThreads, 0, st>>>(A, x, scale, y, partials, ticket,
+                                                                               lambda, iters);
         else
-            power_spmv_kernel<float><<<energy_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, x, scale, y, partials,
-                                                                                        ticket, lambda);
+            power_spmv_kernel<float><<<blocks, kBlockThreads, 0, st>>>(A, x, scale, y, partials, ticket, lambda,
+                                                                       iters);
     }
     return cudaGetLastError();
 }
