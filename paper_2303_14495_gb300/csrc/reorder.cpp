@@ -48,23 +48,23 @@ void parallel_for(int64_t count, F &&f) {
 // seed and visit nodes breadth-first (edges leaving the chunk are ignored),
 // appending them to the current block; a block closes after `block` nodes,
 // and a new seed continues the same block if a search runs dry first.
+// Node state: 0 fresh, 1 queued by the current search, 2 visited.  When a
+// block closes, the nodes still queued (the tail of the queue) become fresh
+// again for the next search.
 void chunk_blocks(int64_t c0, int64_t c1, const int64_t *rp, const int32_t *col, int32_t block,
                   int32_t *order) {
     const int64_t m = c1 - c0;
-    std::vector<uint8_t> vis((size_t)m, 0), inq((size_t)m, 0);
-    std::vector<int32_t> queue, touched;
+    std::vector<uint8_t> state((size_t)m, 0);
+    std::vector<int32_t> queue;
     queue.reserve((size_t)block * 4);
-    touched.reserve((size_t)block * 4);
     int64_t pos = c0, seed = c0;
     while (pos < c1) {
         int64_t cnt = 0;
         while (cnt < block && pos < c1) {
-            while (vis[(size_t)(seed - c0)]) ++seed;
+            while (state[(size_t)(seed - c0)] == 2) ++seed;
             queue.clear();
-            touched.clear();
             queue.push_back((int32_t)seed);
-            inq[(size_t)(seed - c0)] = 1;
-            touched.push_back((int32_t)seed);
+            state[(size_t)(seed - c0)] = 1;
             size_t qh = 0;
             while (qh < queue.size() && cnt < block) {
                 // the rows of queued nodes are scattered in memory: start
@@ -74,22 +74,21 @@ void chunk_blocks(int64_t c0, int64_t c1, const int64_t *rp, const int32_t *col,
                     __builtin_prefetch(col + rp[a]);
                 }
                 const int32_t v = queue[qh++];
-                vis[(size_t)(v - c0)] = 1;
+                state[(size_t)(v - c0)] = 2;
                 order[pos++] = v;
                 ++cnt;
-                for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
-                    const int64_t j = col[e];
-                    if (j < c0 || j >= c1) continue;
-                    const size_t lj = (size_t)(j - c0);
-                    if (!vis[lj] && !inq[lj]) {
-                        inq[lj] = 1;
-                        queue.push_back((int32_t)j);
-                        touched.push_back((int32_t)j);
-                        __builtin_prefetch(rp + j);
+                const int64_t e1 = rp[v + 1];
+                for (int64_t e = rp[v]; e < e1; ++e) {
+                    const uint64_t lj = (uint64_t)((int64_t)col[e] - c0);
+                    if (lj >= (uint64_t)m) continue;
+                    if (state[lj] == 0) {
+                        state[lj] = 1;
+                        queue.push_back((int32_t)(lj + c0));
+                        __builtin_prefetch(rp + lj + c0);
                     }
                 }
             }
-            for (int32_t t : touched) inq[(size_t)(t - c0)] = 0;
+            for (size_t q = qh; q < queue.size(); ++q) state[(size_t)(queue[q] - c0)] = 0;
         }
     }
 }
@@ -106,12 +105,26 @@ void locality_order(int32_t n, const int64_t *rp, const int32_t *col, int32_t bl
         chunk_blocks(c0, c1, rp, col, block, order);
     });
     // degree sort (descending, stable) inside every window of `sort_window`
-    // positions (a divisor of `block`)
+    // positions (a divisor of `block`): a counting sort on the degrees, which
+    // are read once per node; degrees above kMaxBucket share the top bucket
+    // and are ordered among themselves by a stable comparison sort.
+    constexpr int64_t kMaxBucket = 255;
     const int64_t nwin = ((int64_t)n + sort_window - 1) / sort_window;
     parallel_for(nwin, [&](int64_t wdx) {
         int32_t *b = order + wdx * sort_window;
-        int32_t *e = order + std::min<int64_t>(n, (wdx + 1) * sort_window);
-        std::stable_sort(b, e, [&](int32_t x, int32_t y) { return (rp[x + 1] - rp[x]) > (rp[y + 1] - rp[y]); });
+        const int64_t len = std::min<int64_t>(n, (wdx + 1) * sort_window) - wdx * sort_window;
+        std::vector<int64_t> dg((size_t)len);
+        std::vector<int32_t> tmp(b, b + len);
+        int64_t count[kMaxBucket + 2] = {0};
+        for (int64_t i = 0; i < len; ++i) {
+            dg[(size_t)i] = rp[tmp[(size_t)i] + 1] - rp[tmp[(size_t)i]];
+            ++count[kMaxBucket - std::min(dg[(size_t)i], kMaxBucket) + 1];
+        }
+        for (int64_t k = 1; k <= kMaxBucket + 1; ++k) count[k] += count[k - 1];
+        for (int64_t i = 0; i < len; ++i) b[count[kMaxBucket - std::min(dg[(size_t)i], kMaxBucket)]++] = tmp[(size_t)i];
+        const int64_t top = count[0];   // nodes of degree >= kMaxBucket sit first
+        if (top > 1)
+            std::stable_sort(b, b + top, [&](int32_t x, int32_t y) { return (rp[x + 1] - rp[x]) > (rp[y + 1] - rp[y]); });
     });
 }
 
