@@ -8,19 +8,25 @@
 //   (the points are first centred on their mean, which leaves distances
 //   unchanged and keeps the screening product accurate for data far from
 //   the origin)
-//   dist_tile_kernel  FP32 tiled product of the query tile with all points
-//                     (128 x 128 outputs per block, 8 x 8 per thread, 8-wide
-//                     k-slabs staged in shared memory), turned into approximate squared
-//                     distances |x|^2 + |y|^2 - 2 x.y in the epilogue;
-//   candidate_kernel  one warp per query: each lane keeps its c smallest, a
-//                     c-round warp merge gives the query's c candidates
-//                     (c = 3k + 8, a margin for the FP32 rounding);
+//   dist_mma_kernel   the product of the query tile with all points on the
+//                     tensor cores (mma.sync m16n8k16, every FP32 value split
+//                     into BF16 hi + lo, three products per pair, FP32
+//                     accumulation; 128 x 128 outputs per block), turned into
+//                     approximate squared distances |x|^2 + |y|^2 - 2 x.y in
+//                     the epilogue;
+//   candidate_fast_kernel  one warp per query: each lane keeps its 16
+//                     smallest in registers and a c-round warp merge gives the
+//                     query's c candidates (c = 3k + 8, a margin for the
+//                     rounding of the screen); a query where a lane may have
+//                     dropped one of them is flagged, and candidate_kernel
+//                     (c kept per lane) does it again;
 //   rerank_kernel     exact FP64 distances of the candidates (sums of squared
 //                     coordinate differences, the same bits from either end),
 //                     the k smallest (d2, index) kept (ties to the lower index).
 // Then sigma, and the union: in-degree counts, capacity offsets (scan), out-
 // and in-edges placed, each row sorted by column and deduplicated, final
 // offsets (scan) and the compacted CSR with the weights.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <algorithm>
@@ -34,15 +40,29 @@ namespace {
 
 constexpr int kPgMaxK = 32;
 constexpr int kPgMaxC = 3 * kPgMaxK + 8;
-constexpr int kTB = 128, kTK = 8;   // product tile: 128 x 128 outputs, 8-wide slabs
+constexpr int kTB = 128;   // product tile: 128 x 128 outputs
 
-// column means (FP64), one thread per coordinate (coalesced across threads)
+// column means (FP64): block b sums the rows of chunk b for every coordinate
+// (threads over coordinates, coalesced), then one thread per coordinate adds
+// the chunk sums in chunk order
+constexpr int kMeanChunks = 256;
 __global__ void __launch_bounds__(256)
-colmean_kernel(const float *__restrict__ X, int64_t n, int D, double *__restrict__ mean) {
+colsum_kernel(const float *__restrict__ X, int64_t n, int D, double *__restrict__ part) {
+    const int64_t per = (n + kMeanChunks - 1) / kMeanChunks;
+    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(n, r0 + per);
+    for (int d = threadIdx.x; d < D; d += 256) {
+        double s = 0.0;
+        for (int64_t i = r0; i < r1; ++i) s += (double)__ldg(X + i * D + d);
+        part[(int64_t)blockIdx.x * D + d] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+colmean_kernel(const double *__restrict__ part, int64_t n, int D, double *__restrict__ mean) {
     const int d = blockIdx.x * 256 + threadIdx.x;
     if (d >= D) return;
     double s = 0.0;
-    for (int64_t i = 0; i < n; ++i) s += (double)__ldg(X + i * D + d);
+    for (int b = 0; b < kMeanChunks; ++b) s += part[(int64_t)b * D + d];
     mean[d] = s / (double)n;
 }
 
@@ -67,79 +87,220 @@ sqnorm_kernel(const float *__restrict__ X, int64_t n, int D, float *__restrict__
     sq[i] = s;
 }
 
-// out[t * n + j] = sq[q0 + t] + sq[j] - 2 x_{q0+t} . x_j  (+inf for j == q0 + t).
-// Block: 128 query rows x 128 points, 256 threads with 8 x 8 outputs each;
-// 8-wide k-slabs of both operands staged in shared memory (transposed, so
-// each thread reads its 8 + 8 operands as float4 pairs), the next slab's
-// global loads issued before the current slab's products.
-__global__ void __launch_bounds__(256)
-dist_tile_kernel(const float *__restrict__ X, int64_t n, int D, int64_t q0, int T, const float *__restrict__ sq,
-                 float *__restrict__ out) {
-    __shared__ __align__(16) float As[kTK][kTB];
-    __shared__ __align__(16) float Bs[kTK][kTB];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int64_t row0 = (int64_t)blockIdx.y * kTB, col0 = (int64_t)blockIdx.x * kTB;   // row: query t, col: point j
-    // loader mapping: 128 rows x 8 columns per operand = 1024 values, 4 per thread
-    const int lr = threadIdx.x / 2, lc = (threadIdx.x % 2) * 4;
-    const int64_t qa = q0 + row0 + lr, pb = col0 + lr;
-    const bool arow = row0 + lr < T, brow = pb < n;
-    float ra[4], rb[4];
-    auto fetch = [&](int k0) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int kk = k0 + lc + u;
-            ra[u] = (arow && kk < D) ? __ldg(X + qa * D + kk) : 0.0f;
-            rb[u] = (brow && kk < D) ? __ldg(X + pb * D + kk) : 0.0f;
-        }
-    };
-    float acc[8][8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-#pragma unroll
-        for (int v = 0; v < 8; ++v) acc[u][v] = 0.0f;
-    fetch(0);
-    for (int k0 = 0; k0 < D; k0 += kTK) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            As[lc + u][lr] = ra[u];
-            Bs[lc + u][lr] = rb[u];
-        }
-        __syncthreads();
-        if (k0 + kTK < D) fetch(k0 + kTK);
-#pragma unroll
-        for (int c = 0; c < kTK; ++c) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(&As[c][ty * 4]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&As[c][64 + ty * 4]);
-            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[c][tx * 4]);
-            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[c][64 + tx * 4]);
-            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-#pragma unroll
-                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int64_t t = row0 + (u < 4 ? ty * 4 + u : 64 + ty * 4 + u - 4);
-        if (t >= T) continue;
-#pragma unroll
-        for (int v = 0; v < 8; ++v) {
-            const int64_t j = col0 + (v < 4 ? tx * 4 + v : 64 + tx * 4 + v - 4);
-            if (j >= n) continue;
-            out[t * n + j] = (q0 + t == j) ? INFINITY : sq[q0 + t] + sq[j] - 2.0f * acc[u][v];
-        }
-    }
+// The screening product on the tensor cores (mma.sync, BF16 in, FP32
+// accumulate), with each FP32 coordinate split into two BF16 parts,
+// x = hi + lo + e (|e| <= 2^-17 |x|):  x.y ~ hi.hi' + hi.lo' + lo.hi'  (the
+// lo.lo' term, <= 2^-16 |x||y|, is dropped).  Small integers (|x| < 256)
+// split exactly, so lattice ties stay exact.
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo_k, __nv_bfloat16 hi_k) {
+    return (uint32_t)__bfloat16_as_ushort(lo_k) | ((uint32_t)__bfloat16_as_ushort(hi_k) << 16);
 }
 
-// one warp per query row of the tile: the c smallest approximate distances
-// (ties in order of the lanes' scans; the exact re-rank decides afterwards)
+__device__ __forceinline__ void mma_bf16_16x8x16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+constexpr int kMK = 32;            // k-slab
+constexpr int kMW = (kMK + 8) / 2; // shared row stride in 32-bit words (conflict-free fragment loads)
+
+// out[t * n + j] = sq[q0 + t] + sq[j] - 2 x_{q0+t} . x_j  (+inf for j == q0 + t).
+// Block: 128 query rows x 128 points, 8 warps of 64 x 32 outputs (4 x 4
+// m16n8 tiles each).  A 32-wide k-slab of both operands is split into BF16
+// hi/lo parts in shared memory (rows of kMW words: k pairs packed low k
+// first, as the fragments want them); the next slab's global loads are
+// issued before the current slab's products.  Fragment layouts are those of
+// mma.m16n8k16 (A row-major, B column-major, i.e. both as [row][k]).
 __global__ void __launch_bounds__(256)
-candidate_kernel(const float *__restrict__ dist, int64_t n, int T, int c, int32_t *__restrict__ cand) {
+dist_mma_kernel(const float *__restrict__ X, int64_t n, int D, int64_t q0, int T, const float *__restrict__ sq,
+                float *__restrict__ out) {
+    __shared__ uint32_t sm[4][kTB * kMW];   // A hi, A lo, B hi, B lo
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 2, wn = warp & 3;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int64_t row0 = (int64_t)blockIdx.y * kTB, col0 = (int64_t)blockIdx.x * kTB;
+    // loader: value f = tid + 256 i of the 128 x 32 slab (a warp reads one
+    // row's 32 consecutive floats); as k pairs: thread pairs (2p, 2p+1)
+    float ra[16], rb[16];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int f = tid + 256 * i, r = f / kMK, kk = k0 + f % kMK;
+            const int64_t qa = row0 + r, pb = col0 + r;
+            ra[i] = (qa < T && kk < D) ? __ldg(X + (q0 + qa) * D + kk) : 0.0f;
+            rb[i] = (pb < n && kk < D) ? __ldg(X + pb * D + kk) : 0.0f;
+        }
+    };
+    float acc[4][4][4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[m][q][e] = 0.0f;
+    fetch(0);
+    for (int k0 = 0; k0 < D; k0 += kMK) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            // lanes 2p and 2p+1 hold k = 2p, 2p+1 of the same row: pair them
+            const float xa = ra[i], xb = rb[i];
+            const __nv_bfloat16 ah = __float2bfloat16_rn(xa), bh = __float2bfloat16_rn(xb);
+            const __nv_bfloat16 al = __float2bfloat16_rn(xa - __bfloat162float(ah));
+            const __nv_bfloat16 bl = __float2bfloat16_rn(xb - __bfloat162float(bh));
+            const unsigned short o_ah = __shfl_xor_sync(0xffffffffu, __bfloat16_as_ushort(ah), 1);
+            const unsigned short o_al = __shfl_xor_sync(0xffffffffu, __bfloat16_as_ushort(al), 1);
+            const unsigned short o_bh = __shfl_xor_sync(0xffffffffu, __bfloat16_as_ushort(bh), 1);
+            const unsigned short o_bl = __shfl_xor_sync(0xffffffffu, __bfloat16_as_ushort(bl), 1);
+            if ((lane & 1) == 0) {
+                const int f = tid + 256 * i, r = f / kMK, w = (f % kMK) / 2;
+                sm[0][r * kMW + w] = pack_bf16x2(ah, __ushort_as_bfloat16(o_ah));
+                sm[1][r * kMW + w] = pack_bf16x2(al, __ushort_as_bfloat16(o_al));
+                sm[2][r * kMW + w] = pack_bf16x2(bh, __ushort_as_bfloat16(o_bh));
+                sm[3][r * kMW + w] = pack_bf16x2(bl, __ushort_as_bfloat16(o_bl));
+            }
+        }
+        __syncthreads();
+        if (k0 + kMK < D) fetch(k0 + kMK);
+#pragma unroll
+        for (int s = 0; s < kMK / 16; ++s) {
+            const int p = s * 8 + t4;
+            uint32_t ah[4][4], al[4][4], bh[4][2], bl[4][2];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int r = wm * 64 + m * 16 + g;
+                ah[m][0] = sm[0][r * kMW + p];
+                ah[m][1] = sm[0][(r + 8) * kMW + p];
+                ah[m][2] = sm[0][r * kMW + p + 4];
+                ah[m][3] = sm[0][(r + 8) * kMW + p + 4];
+                al[m][0] = sm[1][r * kMW + p];
+                al[m][1] = sm[1][(r + 8) * kMW + p];
+                al[m][2] = sm[1][r * kMW + p + 4];
+                al[m][3] = sm[1][(r + 8) * kMW + p + 4];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = wn * 32 + q * 8 + g;
+                bh[q][0] = sm[2][r * kMW + p];
+                bh[q][1] = sm[2][r * kMW + p + 4];
+                bl[q][0] = sm[3][r * kMW + p];
+                bl[q][1] = sm[3][r * kMW + p + 4];
+            }
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    mma_bf16_16x8x16(acc[m][q], ah[m], bh[q]);
+                    mma_bf16_16x8x16(acc[m][q], ah[m], bl[q]);
+                    mma_bf16_16x8x16(acc[m][q], al[m], bh[q]);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int64_t t = row0 + wm * 64 + m * 16 + g + (e >= 2 ? 8 : 0);
+                const int64_t j = col0 + wn * 32 + q * 8 + t4 * 2 + (e & 1);
+                if (t >= T || j >= n) continue;
+                out[t * n + j] = (q0 + t == j) ? INFINITY : sq[q0 + t] + sq[j] - 2.0f * acc[m][q][e];
+            }
+}
+
+// One warp per query row of the tile: the c smallest approximate distances
+// (ties in order of the lanes' scans; the exact re-rank decides afterwards).
+// Lane l scans j = l, l + 32, ...  The fast form keeps each lane's 16
+// smallest in registers and merges them; the merge is exact unless some lane
+// that dropped values had its 16th value at or below the merged c-th, and
+// those rows (about 1 in 10^4 for c = 38) are flagged and done again by
+// candidate_kernel, which keeps c per lane.
+constexpr int kLaneKeep = 16;
+__global__ void __launch_bounds__(256)
+candidate_fast_kernel(const float *__restrict__ dist, int64_t n, int T, int c, int32_t *__restrict__ cand,
+                      int32_t *__restrict__ redo) {
     const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (t >= T) return;
+    const int lane = threadIdx.x & 31;
+    float bd[kLaneKeep];
+    int32_t bj[kLaneKeep];
+#pragma unroll
+    for (int i = 0; i < kLaneKeep; ++i) {
+        bd[i] = INFINITY;
+        bj[i] = 0x7fffffff;
+    }
+    int64_t seen = 0;   // values this lane found below +inf
+    const float *row = dist + (int64_t)t * n;
+    auto consider = [&](float d, int64_t j) {
+        if (!(d < bd[kLaneKeep - 1])) {
+            seen += d < INFINITY ? 1 : 0;
+            return;
+        }
+        ++seen;
+        bd[kLaneKeep - 1] = d;
+        bj[kLaneKeep - 1] = (int32_t)j;
+#pragma unroll
+        for (int i = kLaneKeep - 1; i > 0; --i) {
+            if (bd[i] < bd[i - 1]) {
+                const float x = bd[i];
+                bd[i] = bd[i - 1];
+                bd[i - 1] = x;
+                const int32_t y = bj[i];
+                bj[i] = bj[i - 1];
+                bj[i - 1] = y;
+            }
+        }
+    };
+    int64_t j = lane;
+    for (; j + 7 * 32 < n; j += 8 * 32) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcs(row + j + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) consider(v[u], j + 32 * u);
+    }
+    for (; j < n; j += 32) consider(row[j], j);
+    const bool dropped = seen > kLaneKeep;
+    const float last = bd[kLaneKeep - 1];
+    float cth = INFINITY;
+    for (int q = 0; q < c; ++q) {
+        const float v = bd[0];
+        const int32_t id = bj[0];
+        float bv = v;
+        int32_t bid = id;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int32_t oid = __shfl_xor_sync(0xffffffffu, bid, o);
+            if (ov < bv || (ov == bv && oid < bid)) {
+                bv = ov;
+                bid = oid;
+            }
+        }
+        if (bid == id && id != 0x7fffffff) {   // the winning lane pops its head
+#pragma unroll
+            for (int i = 0; i + 1 < kLaneKeep; ++i) {
+                bd[i] = bd[i + 1];
+                bj[i] = bj[i + 1];
+            }
+            bd[kLaneKeep - 1] = INFINITY;
+            bj[kLaneKeep - 1] = 0x7fffffff;
+        }
+        cth = bv;
+        if (lane == 0) cand[(int64_t)t * c + q] = bid == 0x7fffffff ? -1 : bid;
+    }
+    const bool unsure = __any_sync(0xffffffffu, dropped && last <= cth);
+    if (lane == 0) redo[t] = unsure ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(256)
+candidate_kernel(const float *__restrict__ dist, int64_t n, int T, int c, int32_t *__restrict__ cand,
+                 const int32_t *__restrict__ redo) {
+    const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (t >= T) return;
+    if (redo && !redo[t]) return;
     const int lane = threadIdx.x & 31;
     float bd[kPgMaxC];
     int32_t bj[kPgMaxC];
@@ -318,7 +479,8 @@ size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct PgWs {
     float *sq, *dist, *xc;
-    double *mean;
+    double *mean, *mpart;
+    int32_t *redo;
     int32_t *cand, *nbr, *cnt, *fillc, *ecol, *len;
     double *nd2, *sigma, *ed2;
     int64_t *off, *bsum, *total;
@@ -341,6 +503,7 @@ PgWs pg_ws(int64_t n, int k, int dim, char *base) {
     const size_t o_off = take(8 * ((size_t)n + 1)), o_ecol = take(4 * cap), o_ed2 = take(8 * cap);
     const size_t o_bsum = take(8 * nb), o_tot = take(8), o_st = take(4);
     const size_t o_xc = take(4 * (size_t)n * dim), o_mean = take(8 * (size_t)dim);
+    const size_t o_mpart = take(8 * (size_t)kMeanChunks * dim), o_redo = take(4 * (size_t)T);
     s.bytes = o;
     if (base) {
         s.sq = reinterpret_cast<float *>(base + o_sq);
@@ -360,6 +523,8 @@ PgWs pg_ws(int64_t n, int k, int dim, char *base) {
         s.status = reinterpret_cast<uint32_t *>(base + o_st);
         s.xc = reinterpret_cast<float *>(base + o_xc);
         s.mean = reinterpret_cast<double *>(base + o_mean);
+        s.mpart = reinterpret_cast<double *>(base + o_mpart);
+        s.redo = reinterpret_cast<int32_t *>(base + o_redo);
     }
     return s;
 }
@@ -404,16 +569,18 @@ extern "C" pdca_status pdca_point_graph(const float *X, int64_t n, int32_t dim, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int T = tile_rows(n), c = (int)std::min<int64_t>(n - 1, 3 * k + 8);
     const unsigned nblk = (unsigned)((n + 255) / 256);
-    count_launches(3);
-    colmean_kernel<<<(unsigned)((dim + 255) / 256), 256, 0, st>>>(X, n, dim, s.mean);
+    count_launches(4);
+    colsum_kernel<<<kMeanChunks, 256, 0, st>>>(X, n, dim, s.mpart);
+    colmean_kernel<<<(unsigned)((dim + 255) / 256), 256, 0, st>>>(s.mpart, n, dim, s.mean);
     center_kernel<<<(unsigned)((n * dim + 255) / 256), 256, 0, st>>>(X, n, dim, s.mean, s.xc);
     sqnorm_kernel<<<nblk, 256, 0, st>>>(s.xc, n, dim, s.sq);
     for (int64_t q0 = 0; q0 < n; q0 += T) {
         const int rows = (int)std::min<int64_t>(T, n - q0);
         const dim3 g((unsigned)((n + kTB - 1) / kTB), (unsigned)((rows + kTB - 1) / kTB));
-        count_launches(3);
-        dist_tile_kernel<<<g, 256, 0, st>>>(s.xc, n, dim, q0, rows, s.sq, s.dist);
-        candidate_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(s.dist, n, rows, c, s.cand);
+        count_launches(4);
+        dist_mma_kernel<<<g, 256, 0, st>>>(s.xc, n, dim, q0, rows, s.sq, s.dist);
+        candidate_fast_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(s.dist, n, rows, c, s.cand, s.redo);
+        candidate_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(s.dist, n, rows, c, s.cand, s.redo);
         rerank_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(X, n, dim, q0, rows, c, k, s.cand, s.nbr, s.nd2);
     }
     count_launches(5);

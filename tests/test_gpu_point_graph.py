@@ -64,6 +64,19 @@ def test_far_from_origin(B):
     assert_same(gpu_graph(B, X, 10, 7), (rp, col, w))
 
 
+def test_neighbours_in_one_lane(B):
+    """The 31 other points with index = 0 mod 32 sit in a tight cluster far
+    from the rest: a query there has all its nearest points in one lane's
+    scan, more than the 16 a lane keeps, so the screen must flag it and take
+    the exact per-lane path."""
+    rng = np.random.default_rng(5)
+    X = (rng.normal(size=(1024, 3)) * 1.0 + 10.0).astype(np.float32)
+    X[::32] = (rng.normal(size=(32, 3)) * 0.01).astype(np.float32)
+    assert separated(X, 8)
+    rp, col, w, _ = PG.point_graph(X, 8, 5)
+    assert_same(gpu_graph(B, X, 8, 5), (rp, col, w))
+
+
 def test_lattice_ties(B):
     """Integer lattice in 2-D: many exact ties, broken by the lower index."""
     g = np.stack(np.meshgrid(np.arange(23), np.arange(19), indexing="ij"), -1).reshape(-1, 2).astype(np.float32)
