@@ -21,7 +21,8 @@
 //                     dropped one of them is flagged, and candidate_kernel
 //                     (c kept per lane) does it again;
 //   rerank_kernel     exact FP64 distances of the candidates (sums of squared
-//                     coordinate differences, the same bits from either end),
+//                     coordinate differences, a warp per distance, the same
+//                     bits from either end),
 //                     the k smallest (d2, index) kept (ties to the lower index).
 // Then sigma, and the union: in-degree counts, capacity offsets (scan), out-
 // and in-edges placed, each row sorted by column and deduplicated, final
@@ -360,18 +361,27 @@ rerank_kernel(const float *__restrict__ X, int64_t n, int D, int64_t q0, int T, 
     const int t = blockIdx.x * 8 + wp;
     if (t >= T) return;
     const int64_t i = q0 + t;
-    for (int q = lane; q < c; q += 32) {
+    // one candidate at a time, the warp over the coordinates (coalesced):
+    // lane l adds d = l, l + 32, ... in order, then lane 0's fixed tree adds
+    // the lanes; each term depends only on |x_i[d] - x_j[d]|, so the sum has
+    // the same bits for (i, j) and (j, i)
+    for (int q = 0; q < c; ++q) {
         const int32_t j = cand[(int64_t)t * c + q];
         double acc = INFINITY;
         if (j >= 0) {
-            acc = 0.0;
-            for (int d = 0; d < D; ++d) {
+            double part = 0.0;
+            for (int d = lane; d < D; d += 32) {
                 const double diff = (double)__ldg(X + i * D + d) - (double)__ldg(X + (int64_t)j * D + d);
-                acc = __dadd_rn(acc, __dmul_rn(diff, diff));
+                part = __dadd_rn(part, __dmul_rn(diff, diff));
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part = __dadd_rn(part, __shfl_xor_sync(0xffffffffu, part, o));
+            acc = __shfl_sync(0xffffffffu, part, 0);
         }
-        sd[wp][q] = acc;
-        sj[wp][q] = j >= 0 ? j : 0x7fffffff;
+        if (lane == 0) {
+            sd[wp][q] = acc;
+            sj[wp][q] = j >= 0 ? j : 0x7fffffff;
+        }
     }
     __syncwarp();
     if (lane == 0) {
