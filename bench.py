@@ -447,10 +447,16 @@ def run_ours(args, wl, world, rank, local):
             torch.cuda.synchronize(dev)
             pm_ms, pm_n = mp.profile_read()
             mp.profile(False)
+            # the last solve's result against the FP32 path's (same workload)
+            Fm, _ = mp.energy()
+            lab_m = torch.empty(wl.n, dtype=torch.int32, device=dev)
+            mp.labels(lab_m)
+            agree = float((lab_m == lab_dev).float().mean().item())
             passes = mixed_pass_bytes(wl.nnz, wl.n, wl.K, p["inner"])
             mixed[name] = {"ms_per_solve": m0.elapsed_time(m1) / nm, "ms_per_pass": pm_ms / max(pm_n, 1),
                            "algorithmic_gb_s_per_pass": (sum(passes) / len(passes)) / (pm_ms / max(pm_n, 1) * 1e-3) / 1e9,
-                           "solves": nm}
+                           "solves": nm, "label_agreement_vs_fp32": agree,
+                           "energy_rel_diff_vs_fp32": abs(Fm - F) / abs(F)}
             del mp
         torch.cuda.synchronize(dev)
 
