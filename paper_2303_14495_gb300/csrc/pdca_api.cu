@@ -44,7 +44,7 @@ struct Layout {
     size_t o_col, o_w, o_slice, o_rowinfo, o_perm, o_iperm, o_self, o_dsq, o_u[3], o_part, o_red, o_scal, o_trace;
     size_t o_hoff, o_hidx;
     size_t o_mr, o_me[2];              // mixed precision: r and the two corrections (16-bit)
-    size_t o_srp, o_scol, o_sw, o_sdeg, o_smask, o_slab, o_status;
+    size_t o_srp, o_scol, o_sw, o_sdeg, o_sisd, o_smask, o_slab, o_status;
     size_t persistent = 0, total = 0;
 };
 
@@ -299,6 +299,7 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     L.o_scol = take(4 * (size_t)L.nnz);
     L.o_sw = take(4 * (size_t)L.nnz);
     L.o_sdeg = take(8 * nn);
+    L.o_sisd = take(8 * nn);
     L.o_smask = take(nn);
     L.o_slab = take(4 * nn);
     L.o_status = take(16);
@@ -832,6 +833,7 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     int32_t *s_col = reinterpret_cast<int32_t *>(W + L.o_scol);
     float *s_w = reinterpret_cast<float *>(W + L.o_sw);
     double *s_deg = reinterpret_cast<double *>(W + L.o_sdeg);
+    double *s_isd = reinterpret_cast<double *>(W + L.o_sisd);
     uint8_t *s_mask = reinterpret_cast<uint8_t *>(W + L.o_smask);
     int32_t *s_lab = reinterpret_cast<int32_t *>(W + L.o_slab);
     uint32_t *s_status = reinterpret_cast<uint32_t *>(W + L.o_status);
@@ -855,7 +857,7 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
         cp(s_lab, labels, 4 * (size_t)n) != cudaSuccess ||
         cudaMemsetAsync(s_status, 0, 16, sm) != cudaSuccess)
         return fail(PDCA_ERR_CUDA);
-    if (launch_validate(n, k, s_rp, s_col, s_w, s_mask, s_lab, s_deg, s_status, sm) != cudaSuccess)
+    if (launch_validate(n, k, s_rp, s_col, s_w, s_mask, s_lab, s_deg, s_isd, s_status, sm) != cudaSuccess)
         return fail(PDCA_ERR_CUDA);
     uint32_t stat4[4] = {0, 0, 0, 0};
     if (cudaMemcpyAsync(stat4, s_status, 16, cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
@@ -880,11 +882,11 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     if (cp(h->slice_off, L.slice_off.data(), 8 * L.slice_off.size()) != cudaSuccess) return fail(PDCA_ERR_CUDA);
     cudaError_t pe;
     if (h->tiled)
-        pe = launch_pack_tiled(L.n_pad, s_rp, s_col, s_w, s_deg, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
+        pe = launch_pack_tiled(L.n_pad, s_rp, s_col, s_w, s_deg, s_isd, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
                                h->tv.halo_off, h->tv.halo_idx, const_cast<uint16_t *>(h->tv.lcol), h->sell_w,
                                h->rowinfo, s_status, sm);
     else
-        pe = launch_pack(n, L.n_pad, k, s_rp, s_col, s_w, s_deg, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
+        pe = launch_pack(n, L.n_pad, k, s_rp, s_col, s_w, s_deg, s_isd, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
                          h->sell_col, h->mixed ? nullptr : h->sell_w,
                          h->mixed ? reinterpret_cast<__nv_bfloat16 *>(h->sell_w) : nullptr, h->self,
                          h->tiled ? nullptr : h->dsq, h->rowinfo, s_status, sm);

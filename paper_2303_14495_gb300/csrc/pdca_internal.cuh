@@ -207,20 +207,20 @@ cudaError_t launch_batch_pass_un(int K, const BatchTable &t, cudaStream_t st);
 // largest degree as the bits of a double (status must start zeroed).
 cudaError_t launch_validate(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *col,
                             const float *w, const uint8_t *mask, const int32_t *labels,
-                            double *deg, uint32_t *status, cudaStream_t st);
+                            double *deg, double *isd, uint32_t *status, cudaStream_t st);
 cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const int64_t *row_ptr,
                                int32_t *perm, int32_t *iperm, cudaStream_t st);
 // self == nullptr: L_s weights w_ij / sqrt(d_i d_j); else L weights w_ij and
 // self[r] = d_i (0 on padding rows).  dsq (nullable): sqrt(d_i) per row.
 cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_ptr,
-                        const int32_t *col, const float *w, const double *deg,
+                        const int32_t *col, const float *w, const double *deg, const double *isd,
                         const uint8_t *mask, const int32_t *labels, const int32_t *perm,
                         const int32_t *iperm, const int64_t *slice_off, int32_t *sell_col,
                         float *sell_w, __nv_bfloat16 *sell_wb, float *self, float *dsq, uint32_t *rowinfo,
                         uint32_t *status, cudaStream_t st);
 // tiled form: local 16-bit columns (position in the tile's halo) instead of int32
 cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32_t *col, const float *w,
-                              const double *deg, const uint8_t *mask, const int32_t *labels,
+                              const double *deg, const double *isd, const uint8_t *mask, const int32_t *labels,
                               const int32_t *perm, const int32_t *iperm, const int64_t *slice_off,
                               const int64_t *halo_off, const int32_t *halo_idx, uint16_t *lcol,
                               float *sell_w, uint32_t *rowinfo, uint32_t *status, cudaStream_t st);

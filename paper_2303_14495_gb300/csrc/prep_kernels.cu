@@ -3,7 +3,8 @@
 //                       columns, finite non-negative weights, w_ij == w_ji)
 //                       and the degrees d_i = sum_j w_ij (FP64, CSR order);
 //   window_sort_kernel  renumbering: rows sorted by degree inside windows;
-//   pack_kernel         sliced-ELL with w_ij / sqrt(d_i d_j) (L_s) or w_ij plus
+//   pack_kernel         sliced-ELL with w_ij d_i^-1/2 d_j^-1/2 (L_s; the
+//                       factors d_i^-1/2 come from validate_kernel) or w_ij plus
 //                       the per-row d_i (L), and the row tags;
 //   spread_kernel       entry order inside rows for conflict-light gathers;
 //   init_u_kernel       u^0 (prior on labelled rows, centre elsewhere).
@@ -18,7 +19,8 @@ namespace {
 __global__ void validate_kernel(int32_t n, int32_t K, const int64_t *__restrict__ row_ptr,
                                 const int32_t *__restrict__ col, const float *__restrict__ w,
                                 const uint8_t *__restrict__ mask, const int32_t *__restrict__ labels,
-                                double *__restrict__ deg, uint32_t *__restrict__ status) {
+                                double *__restrict__ deg, double *__restrict__ isd,
+                                uint32_t *__restrict__ status) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t bad = 0;
@@ -60,6 +62,7 @@ __global__ void validate_kernel(int32_t n, int32_t K, const int64_t *__restrict_
         if (l < 0 || l >= hiK) bad |= kBadGraph;
     }
     deg[i] = d;
+    isd[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
     if (bad) atomicOr(status, bad);
     // non-negative doubles order like their bit patterns
     atomicMax(reinterpret_cast<unsigned long long *>(status + 2), (unsigned long long)__double_as_longlong(d));
@@ -115,7 +118,8 @@ __global__ void window_sort_kernel(int32_t n, int32_t n_pad, int32_t sigma,
 
 __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
                             const int32_t *__restrict__ col, const float *__restrict__ w,
-                            const double *__restrict__ deg, const uint8_t *__restrict__ mask,
+                            const double *__restrict__ deg, const double *__restrict__ isd,
+                            const uint8_t *__restrict__ mask,
                             const int32_t *__restrict__ labels, const int32_t *__restrict__ perm,
                             const int32_t *__restrict__ iperm, const int64_t *__restrict__ slice_off,
                             int32_t *__restrict__ sell_col, float *__restrict__ sell_w,
@@ -144,7 +148,7 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
             const int32_t oj = col[e0 + j];
             const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
             sell_col[at] = iperm[oj];
-            const double wt = self ? (double)w[e0 + j] : (double)w[e0 + j] / sqrt(di * deg[oj]);
+            const double wt = self ? (double)w[e0 + j] : (double)w[e0 + j] * isd[old] * isd[oj];
             if (sell_wb) sell_wb[at] = __double2bfloat16(wt);
             else sell_w[at] = (float)wt;
         }
@@ -166,7 +170,8 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
 // sorted halo list (binary search); padding entries use position 0.
 __global__ void pack_tiled_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
                                   const int32_t *__restrict__ col, const float *__restrict__ w,
-                                  const double *__restrict__ deg, const uint8_t *__restrict__ mask,
+                                  const double *__restrict__ deg, const double *__restrict__ isd,
+                            const uint8_t *__restrict__ mask,
                                   const int32_t *__restrict__ labels, const int32_t *__restrict__ perm,
                                   const int32_t *__restrict__ iperm, const int64_t *__restrict__ slice_off,
                                   const int64_t *__restrict__ halo_off, const int32_t *__restrict__ halo_idx,
@@ -193,7 +198,6 @@ __global__ void pack_tiled_kernel(int32_t n_pad, const int64_t *__restrict__ row
             atomicOr(status, kLayoutMismatch);
             len = width;
         }
-        const double di = deg[old];
         for (int32_t j = 0; j < len; ++j) {
             const int32_t oj = col[e0 + j];
             const int32_t cj = iperm[oj];
@@ -211,7 +215,7 @@ __global__ void pack_tiled_kernel(int32_t n_pad, const int64_t *__restrict__ row
             }
             const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
             lcol[at] = (uint16_t)(pos - h0);
-            sell_w[at] = (float)((double)w[e0 + j] / sqrt(di * deg[oj]));
+            sell_w[at] = (float)((double)w[e0 + j] * isd[old] * isd[oj]);
         }
         if (mask[old]) tag = (uint32_t)labels[old];
     }
@@ -348,10 +352,10 @@ __global__ void init_u_kernel(int32_t n_pad, int32_t K, const uint32_t *__restri
 }  // namespace
 
 cudaError_t launch_validate(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *col,
-                            const float *w, const uint8_t *mask, const int32_t *labels, double *deg,
+                            const float *w, const uint8_t *mask, const int32_t *labels, double *deg, double *isd,
                             uint32_t *status, cudaStream_t st) {
     count_launches(1);
-    validate_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, K, row_ptr, col, w, mask, labels, deg, status);
+    validate_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, K, row_ptr, col, w, mask, labels, deg, isd, status);
     return cudaGetLastError();
 }
 
@@ -369,26 +373,27 @@ cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const in
 }
 
 cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_ptr, const int32_t *col,
-                        const float *w, const double *deg, const uint8_t *mask, const int32_t *labels,
+                        const float *w, const double *deg, const double *isd, const uint8_t *mask,
+                        const int32_t *labels,
                         const int32_t *perm, const int32_t *iperm, const int64_t *slice_off,
                         int32_t *sell_col, float *sell_w, __nv_bfloat16 *sell_wb, float *self, float *dsq,
                         uint32_t *rowinfo, uint32_t *status, cudaStream_t st) {
     (void)n;
     (void)K;
     count_launches(1);
-    pack_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, mask, labels, perm,
+    pack_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, isd, mask, labels, perm,
                                                      iperm, slice_off, sell_col, sell_w, sell_wb, self, dsq,
                                                      rowinfo, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32_t *col, const float *w,
-                              const double *deg, const uint8_t *mask, const int32_t *labels,
+                              const double *deg, const double *isd, const uint8_t *mask, const int32_t *labels,
                               const int32_t *perm, const int32_t *iperm, const int64_t *slice_off,
                               const int64_t *halo_off, const int32_t *halo_idx, uint16_t *lcol,
                               float *sell_w, uint32_t *rowinfo, uint32_t *status, cudaStream_t st) {
     count_launches(1);
-    pack_tiled_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, mask, labels, perm,
+    pack_tiled_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, isd, mask, labels, perm,
                                                            iperm, slice_off, halo_off, halo_idx, lcol, sell_w,
                                                            rowinfo, status);
     return cudaGetLastError();
