@@ -227,9 +227,6 @@ __global__ void pack_tiled_kernel(int32_t n_pad, const int64_t *__restrict__ row
     rowinfo[r] = ((uint32_t)len << 8) | tag;
 }
 
-// Row tags of a problem that shares another problem's operator: the row
-// lengths come from the base's rowinfo, the tags from the new fidelity data
-// (original node order, checked like the validation kernel does).
 // One thread per quarter of a slice (S = 8 lanes: the rows whose 16-byte
 // neighbour rows one L1 wavefront serves).  Neighbour row c lies in group
 // c / S of S consecutive rows at slot c % S; two rows of the quarter read at
@@ -313,6 +310,9 @@ __global__ void spread_kernel(int32_t n_slices, const int64_t *__restrict__ slic
     }
 }
 
+// Row tags of a problem that shares another problem's operator: the row
+// lengths come from the base's rowinfo, the tags from the new fidelity data
+// (original node order, checked like the validation kernel does).
 __global__ void retag_kernel(int32_t n_pad, int32_t K, const uint32_t *__restrict__ base_rowinfo,
                              const int32_t *__restrict__ perm, const uint8_t *__restrict__ mask,
                              const int32_t *__restrict__ labels, uint32_t *__restrict__ rowinfo,
