@@ -214,13 +214,21 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The largest x over the ranks (the slowest rank's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_value(world, bytes_per_step, steps, ms_total_max):
+    """Whole-job GB/s of `world` independent replicas, each moving
+    bytes_per_step per step, timed by the slowest rank."""
+    return world * bytes_per_step * steps / (ms_total_max * 1e-3) / 1e9
 
 
 # ---------------------------------------------------------------------------
@@ -368,7 +376,7 @@ def run_ours(args, wl, world, rank, local):
     ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
     bytes_step = solve_bytes(wl, lay, precision)
-    value = world * bytes_step * args.steps / (ms_total * 1e-3) / 1e9
+    value = replica_value(world, bytes_step, args.steps, ms_total)
 
     hbm, kind = peaks()
     if precision:
