@@ -354,11 +354,12 @@ pdca_status pdca_image_graph(const float *image, int32_t H, int32_t W, int32_t C
  *   w_ij = exp(-|x_i - x_j|^2 / (sigma_i sigma_j)),
  * sigma_i = distance of i to its scale_nn-th nearest neighbour (self
  * excluded), symmetrised by union (an edge where either end keeps the other).
- * Distances are screened in FP32 on the mean-centred points (a tiled product,
- * |x|^2 + |y|^2 - 2 x.y) to
- * 3k + 8 candidates per point, then recomputed exactly in FP64 as sums of
- * squared coordinate differences; the k smallest (d2, j) are kept (equal
- * distances go to the lower index).  The weights are symmetric bit for bit.
+ * Distances are screened on the mean-centred points (|x|^2 + |y|^2 - 2 x.y,
+ * the products on the tensor cores with each FP32 coordinate split into two
+ * BF16 parts, FP32 accumulation) to 3k + 8 candidates per point, then
+ * recomputed exactly in FP64 as sums of squared coordinate differences; the k
+ * smallest (d2, j) are kept (equal distances go to the lower index).  The
+ * weights are symmetric bit for bit.
  *   X: DEVICE, n x dim float32, row-major; 2 <= n < 2^31, 1 <= k <= 32,
  *   k <= n - 1, 1 <= scale_nn <= k.
  *   workspace: DEVICE scratch of pdca_point_graph_workspace_size bytes,
