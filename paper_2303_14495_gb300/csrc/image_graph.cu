@@ -82,11 +82,28 @@ image_knn_kernel(const float *__restrict__ img, int H, int W, int C, int p, int 
     }
 }
 
+// w = exp(-d / sigma^2) as float32.  FP64 is slow on this GPU, so the
+// exponential runs in FP32 wherever the result is a normal float32: with
+// x = x_h + x_l (x_h = float32(x)), exp(-x) = exp(-x_h) (1 - x_l) to within a
+// few float32 ulps (|x_l| <= 2^-24 x, so the dropped terms are below 2^-40).
+// Near the underflow threshold, where FP32 would lose the subnormal digits,
+// it runs in FP64.  Both ends of an edge see the same d, so w stays symmetric
+// bit for bit.
+__device__ __forceinline__ float edge_weight(float d, double inv_sigma2) {
+    const double x = (double)d * inv_sigma2;   // within an ulp of d / sigma^2
+    if (x < 80.0) {
+        const float xh = (float)x;
+        const float xl = (float)(x - (double)xh);
+        return expf(-xh) * (1.0f - xl);
+    }
+    return (float)exp(-x);
+}
+
 // FILL = false: count[i] = row length; FILL = true: write the row at row_ptr[i].
 template <bool FILL>
 __global__ void __launch_bounds__(128)
 image_union_kernel(int H, int W, int r, int k, const int32_t *__restrict__ nbr, const float *__restrict__ dist,
-                   double sigma2, int32_t *__restrict__ count, const int64_t *__restrict__ row_ptr,
+                   double inv_sigma2, int32_t *__restrict__ count, const int64_t *__restrict__ row_ptr,
                    int32_t *__restrict__ col, float *__restrict__ w) {
     const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
     if (i >= (int64_t)H * W) return;
@@ -123,7 +140,7 @@ image_union_kernel(int H, int W, int r, int k, const int32_t *__restrict__ nbr, 
             if (!edge) continue;
             if (FILL) {
                 col[at] = j;
-                w[at] = (float)exp(-(double)d / sigma2);
+                w[at] = edge_weight(d, inv_sigma2);
                 ++at;
             }
             ++len;
@@ -204,7 +221,7 @@ extern "C" pdca_status pdca_image_graph(const float *image, int32_t H, int32_t W
     const unsigned blocks = (unsigned)((n + 127) / 128);
     count_launches(3);
     image_knn_kernel<<<blocks, 128, 0, st>>>(image, H, W, C, patch_radius, window_radius, k, s.nbr, s.dist);
-    const double s2 = sigma * sigma;
+    const double s2 = 1.0 / ((double)sigma * sigma);   // 1 / sigma^2
     image_union_kernel<false><<<blocks, 128, 0, st>>>(H, W, window_radius, k, s.nbr, s.dist, s2, s.count,
                                                       nullptr, nullptr, nullptr);
     exclusive_scan(n, s.count, row_ptr, s.bsum, s.total, st);

@@ -1,8 +1,9 @@
 """GPU nonlocal image graph (pdca_image_graph) against the oracle's builder.
 
 Bar: the CSR structure (row offsets and columns) is identical; weights agree
-to 1e-6 relative (both sides take exp in double of the same FP32 distance;
-the two exp implementations may round one float32 ulp apart).  The kept
+to 1e-6 relative (the oracle takes exp in FP64 of the same FP32 distance and
+rounds to float32; the kernel evaluates it in FP32 with a correction for the
+rounding of the exponent, a few float32 ulps from the oracle).  The kept
 neighbours are decided by FP32 distances computed in the same order on both
 sides, so ties (constant patches) must break identically.
 """
