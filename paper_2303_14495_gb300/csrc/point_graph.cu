@@ -365,22 +365,34 @@ rerank_kernel(const float *__restrict__ X, int64_t n, int D, int64_t q0, int T, 
     // lane l adds d = l, l + 32, ... in order, then lane 0's fixed tree adds
     // the lanes; each term depends only on |x_i[d] - x_j[d]|, so the sum has
     // the same bits for (i, j) and (j, i)
-    for (int q = 0; q < c; ++q) {
-        const int32_t j = cand[(int64_t)t * c + q];
-        double acc = INFINITY;
-        if (j >= 0) {
-            double part = 0.0;
-            for (int d = lane; d < D; d += 32) {
-                const double diff = (double)__ldg(X + i * D + d) - (double)__ldg(X + (int64_t)j * D + d);
-                part = __dadd_rn(part, __dmul_rn(diff, diff));
-            }
+    // (four candidates at a time: four independent FP64 chains per lane)
+    constexpr int kRr = 4;
+    for (int q0 = 0; q0 < c; q0 += kRr) {
+        int32_t j[kRr];
+        double part[kRr];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part = __dadd_rn(part, __shfl_xor_sync(0xffffffffu, part, o));
-            acc = __shfl_sync(0xffffffffu, part, 0);
+        for (int u = 0; u < kRr; ++u) {
+            j[u] = q0 + u < c ? cand[(int64_t)t * c + q0 + u] : -1;
+            part[u] = 0.0;
         }
-        if (lane == 0) {
-            sd[wp][q] = acc;
-            sj[wp][q] = j >= 0 ? j : 0x7fffffff;
+        for (int d = lane; d < D; d += 32) {
+            const double xi = (double)__ldg(X + i * D + d);
+#pragma unroll
+            for (int u = 0; u < kRr; ++u)
+                if (j[u] >= 0) {
+                    const double diff = xi - (double)__ldg(X + (int64_t)j[u] * D + d);
+                    part[u] = __fma_rn(diff, diff, part[u]);   // FP64 is slow here: one op per term
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < kRr; ++u) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part[u] = __dadd_rn(part[u], __shfl_xor_sync(0xffffffffu, part[u], o));
+            const double acc = j[u] >= 0 ? __shfl_sync(0xffffffffu, part[u], 0) : INFINITY;
+            if (lane == 0 && q0 + u < c) {
+                sd[wp][q0 + u] = acc;
+                sj[wp][q0 + u] = j[u] >= 0 ? j[u] : 0x7fffffff;
+            }
         }
     }
     __syncwarp();
