@@ -42,10 +42,12 @@ __device__ __forceinline__ void load_row(const float *__restrict__ p, float (&x)
 
 template <int K>
 __device__ __forceinline__ void store_row(float *__restrict__ p, const float (&x)[K]) {
+    // (st.global.cs: a pass writes each row once and reads it only in the
+    // next pass, after the whole graph has streamed through the caches)
     if constexpr (K % 4 == 0) {
 #pragma unroll
         for (int q = 0; q < K / 4; ++q)
-            reinterpret_cast<float4 *>(p)[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+            __stcs(reinterpret_cast<float4 *>(p) + q, make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]));
     } else if constexpr (K % 2 == 0) {
 #pragma unroll
         for (int q = 0; q < K / 2; ++q)
@@ -190,6 +192,11 @@ __device__ __forceinline__ int4 ld_stream(const int4 *p) {
 __device__ __forceinline__ uint2 ld_stream(const uint2 *p) {
     uint2 r;
     asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) {
+    uint32_t r;
+    asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(r) : "l"(p));
     return r;
 }
 __device__ __forceinline__ float4 ld_stream(const float4 *p) {
@@ -553,7 +560,8 @@ __device__ __forceinline__ void slice_prologue(const SellView &A, const IdxT *co
     const int64_t base = A.slice_off[slice];
     s.cp = cols + base / kVec + lane;
     s.wp = reinterpret_cast<const float4 *>(A.w + base) + lane;
-    s.info = __ldg(A.rowinfo + r);
+    // the row's own data is read by this lane only: keep L1 for the gathers
+    s.info = ld_stream(A.rowinfo + r);
     s.a = UN ? __ldg(A.self + r) : 1.0f;
     // every real row has an entry and every slice is at least kVec wide, so
     // group 0 always exists; group 1 is loaded when the slice has it
@@ -568,6 +576,12 @@ __device__ __forceinline__ void slice_prologue(const SellView &A, const IdxT *co
     if (u_t == v_src) {
 #pragma unroll
         for (int k = 0; k < K; ++k) s.u[k] = s.v[k];
+    } else if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q) {
+            const float4 t = ld_stream(reinterpret_cast<const float4 *>(u_t + (size_t)r * K) + q);
+            s.u[4 * q + 0] = t.x; s.u[4 * q + 1] = t.y; s.u[4 * q + 2] = t.z; s.u[4 * q + 3] = t.w;
+        }
     } else {
         load_row<K>(u_t + (size_t)r * K, s.u);
     }
