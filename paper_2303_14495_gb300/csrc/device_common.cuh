@@ -42,12 +42,10 @@ __device__ __forceinline__ void load_row(const float *__restrict__ p, float (&x)
 
 template <int K>
 __device__ __forceinline__ void store_row(float *__restrict__ p, const float (&x)[K]) {
-    // (st.global.cs: a pass writes each row once and reads it only in the
-    // next pass, after the whole graph has streamed through the caches)
     if constexpr (K % 4 == 0) {
 #pragma unroll
         for (int q = 0; q < K / 4; ++q)
-            __stcs(reinterpret_cast<float4 *>(p) + q, make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]));
+            reinterpret_cast<float4 *>(p)[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
     } else if constexpr (K % 2 == 0) {
 #pragma unroll
         for (int q = 0; q < K / 2; ++q)
@@ -55,6 +53,20 @@ __device__ __forceinline__ void store_row(float *__restrict__ p, const float (&x
     } else {
 #pragma unroll
         for (int q = 0; q < K; ++q) p[q] = x[q];
+    }
+}
+
+// The same with st.global.cs, for problems whose iterates exceed L2: a pass
+// writes each row once and reads it only in the next pass, after the whole
+// graph has streamed through the caches.
+template <int K>
+__device__ __forceinline__ void store_row_cs(float *__restrict__ p, const float (&x)[K]) {
+    if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q)
+            __stcs(reinterpret_cast<float4 *>(p) + q, make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]));
+    } else {
+        store_row<K>(p, x);
     }
 }
 
@@ -467,7 +479,8 @@ __device__ __forceinline__ float lap_row(float a, float x, float acc) {
 
 template <int K, bool PROJECT, bool UN = false>
 __device__ __forceinline__ void sweep_update(const Coeffs &cf, uint32_t info, float a, const float (&acc)[K],
-                                             const float (&v)[K], const float (&u)[K], float *__restrict__ dst) {
+                                             const float (&v)[K], const float (&u)[K], float *__restrict__ dst,
+                                             bool stream = false) {
     const uint32_t tag = info & 0xFFu;
     const bool lab = tag != kTagUnlabelled;
     const float inv_g = inv_g_of<UN>(cf, lab, a);
@@ -482,7 +495,8 @@ __device__ __forceinline__ void sweep_update(const Coeffs &cf, uint32_t info, fl
         out[k] = v[k] + (b - tv) * inv_g;
     }
     if constexpr (PROJECT) project_simplex<K>(out);
-    store_row<K>(dst, out);
+    if (stream) store_row_cs<K>(dst, out);
+    else store_row<K>(dst, out);
 }
 
 // column i (0..3) of an entry group: int32 global columns or 16-bit locals
@@ -625,7 +639,7 @@ __device__ __forceinline__ void fp32_sweep_slice(const SellView &A, const Coeffs
     float acc[K];
     slice_gather<K, kGlobal>(s, v_src, nullptr, nullptr, acc);
     sweep_update<K, PROJECT, UN>(cf, s.info, s.a, acc, s.v, s.u,
-                                 v_dst + (size_t)(slice * kSliceRows + lane) * K);
+                                 v_dst + (size_t)(slice * kSliceRows + lane) * K, A.stream_rows != 0);
 }
 
 // Mixed precision, pass 0 of an outer step: r = b^t - T u^t and e^1 = G^-1 r

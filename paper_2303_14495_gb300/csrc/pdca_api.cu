@@ -371,6 +371,8 @@ struct pdca_problem {
         A.self = self;
         A.n_slices = L.n_slices;
         A.n = L.n;
+        // three n_pad x K FP32 iterates above half of the 129 MB L2
+        A.stream_rows = 3.0 * 4.0 * (double)L.n_pad * (double)L.K > 64.0 * (1 << 20) ? 1 : 0;
         return A;
     }
     int spare() const { return has_prev ? 3 - cur - prev : (cur + 1) % 3; }

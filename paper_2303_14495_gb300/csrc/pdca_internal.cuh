@@ -52,6 +52,7 @@ struct SellView {
     const float *self;         // a_i = d_i per row (n_pad) for L; nullptr for L_s
     int32_t n_slices;
     int32_t n;                 // real rows; rows >= n are padding
+    int32_t stream_rows;       // 1: the iterates exceed L2, store rows with st.global.cs
 };
 
 // Resident blocks per SM the plain sweep is compiled for (registers per
