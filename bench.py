@@ -317,7 +317,7 @@ def run_serving(args, local):
     if not args.no_autotune:
         # slots and passes per tick from a replay of the first 128 requests
         from paper_2303_14495_gb300 import autotune
-        pick, table = autotune.tune_serving(bm, reqs[:128], slots=(32, 64), passes=(2, 4, 8))
+        pick, table = autotune.tune_serving(bm, reqs[:128], slots=(32, 64, 128), passes=(2, 4, 8))
         slots, ppt = pick["max_slots"], pick["passes_per_tick"]
         tuned = {"pick": pick, "sample": "first 128 requests of the mix",
                  "table": [{k: r[k] for k in ("max_slots", "passes_per_tick", "problems_per_s", "p50_ms", "p99_ms")}
