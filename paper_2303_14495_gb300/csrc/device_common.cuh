@@ -649,7 +649,7 @@ __device__ __forceinline__ void mixed_residual_slice(const SellView &A, const Co
                                                      const float *__restrict__ u, HT *__restrict__ r_out,
                                                      HT *__restrict__ e_out, float *__restrict__ u_out) {
     const int r = slice * kSliceRows + lane;
-    const uint32_t info = __ldg(A.rowinfo + r);
+    const uint32_t info = ld_stream(A.rowinfo + r);   // read by this lane only
     const float a = UN ? __ldg(A.self + r) : 1.0f;
     float acc[K];
     gather_row_sum<K, __nv_bfloat16, float>(A, A.slice_off[slice], (int)(info >> 8), lane, u, acc);
@@ -685,13 +685,22 @@ __device__ __forceinline__ void mixed_sweep_slice(const SellView &A, const Coeff
                                                   HT *__restrict__ e_dst, const float *__restrict__ u,
                                                   float *__restrict__ u_out) {
     const int r = slice * kSliceRows + lane;
-    const uint32_t info = __ldg(A.rowinfo + r);
+    const uint32_t info = ld_stream(A.rowinfo + r);   // read by this lane only
     const float a = UN ? __ldg(A.self + r) : 1.0f;
     float acc[K];
     gather_row_sum<K, __nv_bfloat16, HT>(A, A.slice_off[slice], (int)(info >> 8), lane, e_src, acc);
     float e[K], res[K];
     load_row_t<K, HT>(e_src + (size_t)r * K, e);
-    load_row_t<K, HT>(rr + (size_t)r * K, res);
+    if constexpr (K % 4 == 0) {   // the residual row: read by this lane only
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q) {
+            const uint2 t = ld_stream(reinterpret_cast<const uint2 *>(rr + (size_t)r * K) + q);
+            const float2 lo = unpack2<HT>(t.x), hi = unpack2<HT>(t.y);
+            res[4 * q + 0] = lo.x; res[4 * q + 1] = lo.y; res[4 * q + 2] = hi.x; res[4 * q + 3] = hi.y;
+        }
+    } else {
+        load_row_t<K, HT>(rr + (size_t)r * K, res);
+    }
     const uint32_t tag = info & 0xFFu;
     const bool lab = tag != kTagUnlabelled;
     const float inv_g = inv_g_of<UN>(cf, lab, a);
