@@ -469,8 +469,8 @@ def run_ours(args, wl, world, rank, local):
             pm_ms, pm_n = mp.profile_read()
             mp.profile(False)
             # the last solve's result against the FP32 path's (same workload):
-            # labels compared on the rows the FP32 result decides by a margin
-            # of at least 1e-4 (top-two gap, |u| for K = 1), as in the tests
+            # labels compared on every row that is not a tie under the FP32
+            # rule (top-two gap, |u| for K = 1, below 1e-6), and on all rows
             Fm, _ = mp.energy()
             um = mp.get_u()
             lab_m = mp.labels()
@@ -480,15 +480,16 @@ def run_ours(args, wl, world, rank, local):
             else:
                 srt = np.sort(u_fp32, axis=1)
                 margin = srt[:, -1] - srt[:, -2]
-            decided = margin >= 1e-4
-            agree = float(np.mean(lab_m[decided] == lab_32[decided])) if decided.any() else 1.0
+            nontie = margin >= 1e-6
+            agree = float(np.mean(lab_m[nontie] == lab_32[nontie])) if nontie.any() else 1.0
             rel_u = float(np.linalg.norm((um - u_fp32).ravel()) / max(np.linalg.norm(u_fp32.ravel()), 1e-300))
+            max_abs = float(np.max(np.abs(um.astype(np.float64) - u_fp32)))
             passes = mixed_pass_bytes(wl.nnz, wl.n, wl.K, p["inner"])
             mixed[name] = {"ms_per_solve": m0.elapsed_time(m1) / nm, "ms_per_pass": pm_ms / max(pm_n, 1),
                            "algorithmic_gb_s_per_pass": (sum(passes) / len(passes)) / (pm_ms / max(pm_n, 1) * 1e-3) / 1e9,
-                           "solves": nm, "rel_l2_u_vs_fp32": rel_u,
-                           "decided_rows_fp32": float(np.mean(decided)),
-                           "label_agreement_decided_vs_fp32": agree,
+                           "solves": nm, "rel_l2_u_vs_fp32": rel_u, "max_abs_u_vs_fp32": max_abs,
+                           "tie_rows_fp32": float(1.0 - np.mean(nontie)),
+                           "label_agreement_nontie_vs_fp32": agree,
                            "label_agreement_all_vs_fp32": float(np.mean(lab_m == lab_32)),
                            "energy_rel_diff_vs_fp32": abs(Fm - F) / abs(F)}
             del mp

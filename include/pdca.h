@@ -379,26 +379,33 @@ pdca_status pdca_point_graph(const float *X, int64_t n, int32_t dim, int32_t k, 
 uint64_t pdca_kernel_launches(void);
 
 /* GL energy F(u) of an iterate, computed directly from a device CSR graph,
- * for callers that cannot allocate device memory: they cannot hand the
- * library a workspace, e.g. code running inside a CUDA stream capture (where
- * cudaMalloc is not allowed), a host framework that owns all device memory
- * through its own fixed pool, or a loop that must not pay cudaMalloc's
- * implicit synchronisation.  The paper has no counterpart of this call; it
- * evaluates the same F as pdca_energy (normalized Laplacian).
+ * for callers that cannot allocate device memory and so cannot hand the
+ * library a workspace: a host framework that owns every device byte through
+ * its own fixed pool and allows no other allocator (or a plug-in loaded into
+ * such a process), or a loop that must not pay cudaMalloc's implicit
+ * device-wide synchronisation.  The paper has no counterpart of this call; it
+ * evaluates the same F as pdca_energy for the normalized Laplacian L_s only
+ * (a problem created with PDCA_LAP_UNNORMALIZED has a different F).
  *   row_ptr (n+1 int64), col (nnz int32), w (nnz float32), u (n x k float32,
  *   row-major), fid_mask (n uint8), labels (n int32): DEVICE pointers, same
- *   conventions as pdca_create (the graph is not checked for symmetry);
- *   eps > 0, eta >= 0; stream: cudaStream_t as void*;
- *   F_out: host or device pointer receiving F (written on success).
+ *   conventions as pdca_create; eps > 0, eta >= 0; stream: cudaStream_t as
+ *   void*; F_out: host or device pointer receiving F (written on success
+ *   only; a device F_out is written by a kernel on `stream`).
+ * Checks: row_ptr inside [0, nnz], columns in [0, n), no self loop, weights
+ * finite and >= 0, mask values 0/1, prior labels in [0, max(k, 2)) on
+ * labelled rows.  Symmetry and the column order are NOT checked.
  * Allocates nothing: the scratch is a fixed device array inside the library
  * (about 4.1 MiB, held on every GPU that loads the library until the process
- * exits).  The first call on a device looks up that array's address; make
- * that first call before any stream capture.  All calls share the array
- * and overwrite it; calls whose kernels overlap on the GPU race and must be
- * serialised by the caller.  Synchronises the stream.
+ * exits), limiting n to PDCA_STATIC_MAX_N.  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the array and overwrite it (the status word is cleared at the start of
+ * every call); calls whose kernels overlap on the GPU (two streams, two host
+ * threads) race on it and must be serialised by the caller.  The call reads
+ * its status back and synchronises `stream` before returning.
  * Errors: INVALID_ARG (bad sizes or a host pointer among the inputs),
- * TOO_LARGE (n > PDCA_STATIC_MAX_N), BAD_GRAPH (row_ptr outside [0, nnz] or
- * a column out of range), ISOLATED_NODE, NONFINITE, CUDA. */
+ * TOO_LARGE (n > PDCA_STATIC_MAX_N), BAD_GRAPH (a failed check above),
+ * ISOLATED_NODE, NONFINITE, CUDA. */
 pdca_status pdca_energy_static(const int64_t *row_ptr, const int32_t *col, const float *w,
                                int32_t n, int64_t nnz, int32_t k, const float *u,
                                const uint8_t *fid_mask, const int32_t *labels, double eps,

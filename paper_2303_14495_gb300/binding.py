@@ -257,7 +257,10 @@ def pdca_destroy(h) -> None:
 
 def pdca_energy_static(row_ptr, col, w, n, nnz, k, u, fid_mask, labels, eps, eta, stream=0):
     """F(u) from a device CSR without any allocation (fixed library scratch);
-    returns (status, F)."""
+    returns (status, F).  F is the energy of the normalized Laplacian L_s
+    only: for a problem created with PDCA_LAP_UNNORMALIZED it differs from
+    pdca_energy's value.  Calls share the library's scratch, so calls that
+    overlap on the GPU race; the call synchronises `stream`."""
     F = C.c_double(float("nan"))
     st = lib().pdca_energy_static(_ptr(row_ptr), _ptr(col), _ptr(w), int(n), int(nnz), int(k),
                                   _ptr(u), _ptr(fid_mask), _ptr(labels), float(eps), float(eta),

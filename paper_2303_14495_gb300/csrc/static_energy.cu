@@ -1,14 +1,19 @@
 // pdca_energy_static: the GL energy F(u) of an iterate, computed straight
 // from a device CSR graph, for callers that cannot allocate device memory.
 //
-// Such callers cannot give the library a workspace: for example a caller
-// inside a CUDA stream capture (cudaMalloc is not allowed there), a host
-// framework that owns every device byte through its own fixed-budget pool,
-// or a latency-critical loop that must not pay cudaMalloc's implicit
+// Such callers cannot give the library a workspace: for example a host
+// framework that owns every device byte through its own fixed-budget pool
+// and forbids other allocators, a plug-in loaded into such a process, or a
+// latency-critical loop that must not pay cudaMalloc's implicit device-wide
 // synchronisation.  This entry point therefore keeps its scratch (inverse
 // square-root degrees, per-block partial sums, the result and a status word)
 // in one file-scope __device__ array of fixed size.  Every process that
 // loads the library holds that array on every GPU it uses until it exits.
+//
+// The graph is checked as far as one pass over it allows: row_ptr inside
+// [0, nnz], columns in range, no self loop, finite non-negative weights,
+// mask values 0/1 and prior labels in range on labelled rows (BAD_GRAPH).
+// Symmetry and the column order are not checked.
 //
 // The array is shared by all calls: a call overwrites what the previous call
 // left, and clears the status word before use.  Two calls whose kernels
@@ -55,7 +60,13 @@ __global__ void static_degree_kernel(int32_t n, int64_t nnz, const int64_t *__re
             continue;
         }
         double d = 0.0;
-        for (int64_t e = e0; e < e1; ++e) d += (double)w[e];
+        bool bad = false;
+        for (int64_t e = e0; e < e1; ++e) {
+            const float wv = w[e];
+            if (!(isfinite(wv) && wv >= 0.0f)) bad = true;
+            d += (double)wv;
+        }
+        if (bad) atomicOr(status, kStBadGraph);
         if (!(d > 0.0)) atomicOr(status, kStIsolated);
         s[i] = d > 0.0 ? (float)(1.0 / sqrt(d)) : 0.0f;
     }
@@ -88,7 +99,7 @@ static_energy_kernel(int32_t n, int64_t nnz, const int64_t *__restrict__ row_ptr
         for (int k = 0; k < K; ++k) acc[k] = 0.0f;
         for (int64_t e = e0; e < e1; ++e) {
             const int32_t j = col[e];
-            if (j < 0 || j >= n) {
+            if (j < 0 || j >= n || j == i) {
                 atomicOr(status, kStBadGraph);
                 continue;
             }
@@ -98,6 +109,7 @@ static_energy_kernel(int32_t n, int64_t nnz, const int64_t *__restrict__ row_ptr
         }
         const uint8_t m = mask[i];
         const int32_t lab = m ? labels[i] : 0;
+        if (m > 1 || (m == 1 && (lab < 0 || lab >= (K == 1 ? 2 : K)))) atomicOr(status, kStBadGraph);
         float q = 0.f, wl = 0.f, fd = 0.f, nf = 0.f;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -132,8 +144,12 @@ static_energy_kernel(int32_t n, int64_t nnz, const int64_t *__restrict__ row_ptr
     }
 }
 
-// One block: fixed-order sum of the partials; result[0] = F, result[1] = non-finite count.
-__global__ void static_finalize_kernel(double eps, double eta, unsigned char *__restrict__ scratch) {
+// One block: fixed-order sum of the partials; result[0] = F, result[1] =
+// non-finite count.  F_dev (device pointer or null) receives F when the
+// status word is clear and F is finite, so a device output is written on
+// success only, as a host one is.
+__global__ void static_finalize_kernel(double eps, double eta, unsigned char *__restrict__ scratch,
+                                       double *__restrict__ F_dev) {
     const double *partials = reinterpret_cast<const double *>(scratch + kOffPartials);
     double *result = reinterpret_cast<double *>(scratch + kOffResult);
     __shared__ double sm[kStaticThreads][4];
@@ -151,8 +167,11 @@ __global__ void static_finalize_kernel(double eps, double eta, unsigned char *__
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        result[0] = 0.5 * eps * sm[0][0] + sm[0][1] / (4.0 * eps) + 0.5 * eta * sm[0][2];
+        const double F = 0.5 * eps * sm[0][0] + sm[0][1] / (4.0 * eps) + 0.5 * eta * sm[0][2];
+        result[0] = F;
         result[1] = sm[0][3];
+        const unsigned status = *reinterpret_cast<const unsigned *>(scratch + kOffStatus);
+        if (F_dev && status == 0u && sm[0][3] == 0.0 && isfinite(F)) *F_dev = F;
     }
 }
 
@@ -227,7 +246,8 @@ extern "C" pdca_status pdca_energy_static(const int64_t *row_ptr, const int32_t 
     if (cudaGetLastError() != cudaSuccess) return PDCA_ERR_CUDA;
     if (launch_static_energy(k, n, nnz, row_ptr, col, w, u, fid_mask, labels, scr, sm) != cudaSuccess)
         return PDCA_ERR_CUDA;
-    static_finalize_kernel<<<1, kStaticThreads, 0, sm>>>(eps, eta, scr);
+    const bool dev_out = on_device(F_out);
+    static_finalize_kernel<<<1, kStaticThreads, 0, sm>>>(eps, eta, scr, dev_out ? F_out : nullptr);
     if (cudaGetLastError() != cudaSuccess) return PDCA_ERR_CUDA;
     pdca::count_launches(3);
     if (cudaMemcpyAsync(&status, scr + kOffStatus, sizeof(unsigned), cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
@@ -236,7 +256,7 @@ extern "C" pdca_status pdca_energy_static(const int64_t *row_ptr, const int32_t 
         return PDCA_ERR_CUDA;
     if (status & kStBadGraph) return PDCA_ERR_BAD_GRAPH;
     if (status & kStIsolated) return PDCA_ERR_ISOLATED_NODE;
-    if (cudaMemcpy(F_out, &res[0], sizeof(double), cudaMemcpyDefault) != cudaSuccess) return PDCA_ERR_CUDA;
     if (res[1] > 0 || !std::isfinite(res[0])) return PDCA_ERR_NONFINITE;
+    if (!dev_out) *F_out = res[0];   // a device F_out was written by the finalize kernel
     return PDCA_OK;
 }

@@ -1,16 +1,15 @@
 """Mixed-precision path (BF16 weights, FP16 or BF16 correction storage, FP32
 arithmetic and FP32 master iterate) against the FP64 oracle.
 
-Bar: labels agree with the oracle's on at least 99.9% of the nodes the
-oracle decides by a margin of at least 1e-4 (top-two gap for K >= 2, |u_i|
-for K = 1), and the final GL energy is within 1e-3 relative.  Rows below that
-margin are near-ties whose label flips under any perturbation of order 1e-6
-(the mixed path's measured error), so they are counted but not compared; the
-fraction of decided rows is printed.  The relative L2 error of u after every
-outer step is recorded and bounded.
+Bar: labels agree with the oracle's on at least 99.9% of the rows that are
+not ties under the FP32 rule (top-two gap of the oracle's iterate >= 1e-6 for
+K >= 2, |u_i| >= 1e-6 for K = 1), and the final GL energy is within 1e-3
+relative.  Agreement over all rows, the fraction of tie rows, the maximum
+absolute error of u and the relative L2 error of u after every outer step
+are printed for every case.
 """
 
-MARGIN = 1e-4
+TIE = 1e-6
 
 import numpy as np
 import pytest
@@ -49,16 +48,24 @@ def run_mixed(B, rp, col, w, K, mask, lab, p, outer, inner, precision, lam=None,
     F, _ = g.energy()
     lab_gpu = g.labels()
     lab_ref = ref.labels_of(u_ref)
+    agree, agree_all, tie_frac = label_agreement(lab_gpu, lab_ref, u_ref, K)
+    max_abs = float(np.max(np.abs(g.get_u().astype(np.float64) - u_ref)))
+    print(f"  tie rows {tie_frac:.4f}; agreement on non-tie rows {agree:.6f}, all rows {agree_all:.6f}; "
+          f"max |u - u_oracle| {max_abs:.2e}")
+    return errs, F, e_ref[-1], agree
+
+
+def label_agreement(lab_gpu, lab_ref, u_ref, K):
+    """(agreement on non-tie rows, agreement on all rows, tie fraction); ties
+    follow the FP32 rule: top-two gap (K >= 2) or |u| (K = 1) below 1e-6."""
     if K == 1:
         margin = np.abs(u_ref)
     else:
         srt = np.sort(u_ref, axis=1)
         margin = srt[:, -1] - srt[:, -2]
-    decided = margin >= MARGIN
-    agree = float(np.mean(lab_gpu[decided] == lab_ref[decided])) if decided.any() else 1.0
-    print(f"  decided rows {decided.mean():.4f}, agreement on them {agree:.6f}, "
-          f"all rows {np.mean(lab_gpu == lab_ref):.4f}")
-    return errs, F, e_ref[-1], agree
+    nontie = margin >= TIE
+    agree = float(np.mean(lab_gpu[nontie] == lab_ref[nontie])) if nontie.any() else 1.0
+    return agree, float(np.mean(lab_gpu == lab_ref)), float(1.0 - nontie.mean())
 
 
 def lam_for(wl, omp=True):
@@ -91,9 +98,10 @@ def test_mixed_voronoi2048_full(B):
     p = wl.params
     errs, F, F_ref, agree = run_mixed(B, wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, p,
                                       p["outer"], p["inner"], PREC["fp16u"], lam=lam_for(wl))
-    print(f"voronoi2048 fp16u: per-step rel L2 {['%.1e' % e for e in errs]}, agreement {agree:.5f}")
-    assert agree >= 0.999
-    assert abs(F - F_ref) <= 1e-3 * abs(F_ref)
+    print(f"voronoi2048 fp16u: per-step rel L2 {['%.1e' % e for e in errs]}, agreement {agree:.5f}, "
+          f"F {F:.8g} vs {F_ref:.8g}")
+    assert agree >= 0.999, agree
+    assert abs(F - F_ref) <= 1e-3 * abs(F_ref), (F, F_ref)
 
 
 @pytest.mark.parametrize("K", [1, 2, 3, 5, 10])
@@ -106,7 +114,7 @@ def test_mixed_small_graphs(B, K, inner):
     lab = rng.integers(0, max(K, 2), size=n).astype(np.int32)
     p = dict(eps=1.0, eta=50.0, c=52.0, precond=1)
     errs, F, F_ref, agree = run_mixed(B, rp, col, w, K, mask, lab, p, 4, inner, PREC["fp16u"], omp=False)
-    assert agree >= 0.99, agree       # tiny graph: one label is 0.13%
+    assert agree >= 0.99, agree       # tiny graph: one label is 0.13% of the rows
     assert abs(F - F_ref) <= 1e-3 * abs(F_ref), (F, F_ref)
 
 
