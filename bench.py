@@ -66,17 +66,18 @@ def labels_bytes(n, K, s_u=4):
     return n * (K * s_u + 4)
 
 
-def mixed_pass_bytes(nnz, n, K, inner):
-    """Algorithmic bytes of the passes of one mixed-precision outer step:
-    int32 columns + BF16 weights per entry; pass 0 reads the FP32 iterate and
-    writes r and e^1 (16-bit); correction sweeps read e and r and write e; the
-    last reads e, r and u^t and writes u^{t+1} (FP32); one tag byte per row."""
-    op = nnz * (4 + 2)
+def mixed_pass_bytes(nnz, n, K, inner, s_idx=4):
+    """Algorithmic bytes of the passes of one mixed-precision outer step.
+    Pass 0 (the FP32 residual correction) streams int32 columns and FP32
+    weights, reads the FP32 iterate and writes r (FP32) and e^1 (16-bit); the
+    correction sweeps stream the BF16 weights, read e (16-bit) and r (FP32)
+    and write e; the last one also reads u^t and writes u^{t+1} (FP32); one
+    tag byte per row."""
     if inner == 1:
-        return [op + n * (2 * K * 4 + 1)]
-    first = op + n * (K * 4 + 2 * K * 2 + 1)
-    mid = op + n * (3 * K * 2 + 1)
-    last = op + n * (2 * K * 2 + 2 * K * 4 + 1)
+        return [nnz * (s_idx + 4) + n * (2 * K * 4 + 1)]
+    first = nnz * (s_idx + 4) + n * (K * 4 + K * 4 + K * 2 + 1)
+    mid = nnz * (s_idx + 2) + n * (K * 2 + K * 4 + K * 2 + 1)
+    last = nnz * (s_idx + 2) + n * (K * 2 + K * 4 + 2 * K * 4 + 1)
     return [first] + [mid] * (inner - 2) + [last]
 
 
@@ -84,8 +85,7 @@ def solve_bytes(wl, lay=None, precision=0):
     p = wl.params
     if precision:
         sweeps = p["outer"] * sum(mixed_pass_bytes(wl.nnz, wl.n, wl.K, p["inner"]))
-        ebytes = wl.nnz * (4 + 2) + wl.n * (2 * wl.K * 4 + 1)
-        return sweeps + ebytes + labels_bytes(wl.n, wl.K)
+        return sweeps + energy_bytes(wl.nnz, wl.n, wl.K) + labels_bytes(wl.n, wl.K)
     return (p["outer"] * p["inner"] * sweep_bytes(wl.nnz, wl.n, wl.K, lay)
             + energy_bytes(wl.nnz, wl.n, wl.K, lay) + labels_bytes(wl.n, wl.K))
 
@@ -397,6 +397,16 @@ def run_ours(args, wl, world, rank, local):
         sb = sweep_bytes(wl.nnz, wl.n, wl.K, lay)
     sweep_ms = sweep_ms_tot / max(sweep_launches, 1)
     achieved = sb / (sweep_ms * 1e-3) / 1e9
+    # the same launch against the layout's own bytes: 16-bit columns in the
+    # slices that store them (their share of the entries taken as their share
+    # of the slices)
+    f16 = lay["slices16"] / max(lay["n_slices"], 1)
+    s_idx_layout = 4.0 - 2.0 * f16
+    if precision:
+        lb = mixed_pass_bytes(wl.nnz, wl.n, wl.K, p["inner"], s_idx=s_idx_layout)
+        layout_bytes = sum(lb) / len(lb)
+    else:
+        layout_bytes = wl.nnz * (s_idx_layout + 4) + wl.n * (3 * wl.K * 4 + 1)
     traffic = None if precision else sweep_traffic_record()
     # the FP32 result of the last timed solve, the reference of the mixed forms
     u_fp32 = prob.get_u() if not args.no_mixed and precision == 0 else None
@@ -536,6 +546,7 @@ def run_ours(args, wl, world, rank, local):
                                        "tiled": lay["tiled"],
                                        "sort_window": lay["sort_window"],
                                        "sell_entries": lay["sell_entries"],
+                                       "slices16": lay["slices16"], "n_slices": lay["n_slices"],
                                        "halo_rows": lay["halo_rows"], "max_halo": lay["max_halo"],
                                        "lambda_max_used": lam_used}),
         "ms_per_solve": ms_step,
@@ -546,6 +557,9 @@ def run_ours(args, wl, world, rank, local):
                                 else ("sweep_tiled_kernel<4,*>" if lay["tiled"] else "sweep_kernel<4,*>")
                                 + " (fused sweep)"),
                      "bytes_per_launch": sb, "ms_per_launch": sweep_ms,
+                     "layout_bytes_per_launch": layout_bytes,
+                     "layout_frac": layout_bytes / (sweep_ms * 1e-3) / 1e9 / hbm,
+                     "slices16_frac": f16,
                      "launches_timed": sweep_launches, "peak_kind": kind},
         "gpu_launches": int(launches),
         "clocks": clocks,

@@ -20,5 +20,6 @@ from .workloads import (  # noqa: F401
     knn_graph_image,
     sample_labels,
     random_graph,
+    banded_graph,
     csr_from_pairs,
 )

@@ -142,6 +142,38 @@ def random_graph(n: int, avg_deg: int, seed: int, w_low: float = 0.05,
     return csr_from_pairs(n, p[:, 0], p[:, 1], w)
 
 
+def banded_graph(n: int, avg_deg: int, band: int, seed: int, far_frac: float = 0.0, hubs=(),
+                 hub_deg: int = 100, w_low: float = 0.05, w_high: float = 1.0):
+    """Random symmetric graph whose edges join nodes at most ``band`` apart in
+    index (plus a ring i -- i+1), for tests of any size; ``far_frac`` of the
+    extra edges join uniformly random nodes instead, and every node listed in
+    ``hubs`` gets ``hub_deg`` extra neighbours between 1 and ``band``
+    positions above it.
+    """
+    rng = np.random.default_rng(seed)
+    a = [np.arange(n - 1, dtype=np.int64)]
+    b = [np.arange(1, n, dtype=np.int64)]
+    m = max(0, (avg_deg * n) // 2 - (n - 1))
+    x = rng.integers(0, n, size=m)
+    y = x + rng.integers(-band, band + 1, size=m)
+    far = rng.uniform(size=m) < far_frac
+    y[far] = rng.integers(0, n, size=int(far.sum()))
+    a.append(x)
+    b.append(y)
+    for c in hubs:
+        a.append(np.full(hub_deg, c, np.int64))
+        b.append(c + rng.integers(1, band + 1, size=hub_deg))
+    a = np.concatenate(a)
+    b = np.concatenate(b)
+    ok = (b >= 0) & (b < n) & (a != b)
+    i = np.minimum(a[ok], b[ok])
+    j = np.maximum(a[ok], b[ok])
+    key = np.unique(i * n + j)
+    i, j = key // n, key % n
+    w = rng.uniform(w_low, w_high, size=i.shape[0]).astype(np.float32)
+    return csr_from_pairs(n, i, j, w)
+
+
 # ---------------------------------------------------------------------------
 # Feature data
 # ---------------------------------------------------------------------------

@@ -121,17 +121,32 @@ enum { PDCA_TILING_AUTO = 0, PDCA_TILING_OFF = 1, PDCA_TILING_ON = 2 };
  *   PDCA_ENTRIES_CSR    the order of the caller's CSR columns. */
 enum { PDCA_ENTRIES_SPREAD = 0, PDCA_ENTRIES_CSR = 1 };
 
+/* Column indices of the sliced-ELL operator (plain kernels; a layout choice
+ * with no effect on the arithmetic):
+ *   PDCA_COLUMNS_AUTO (default) a slice whose rows reach only nodes of their
+ *                     own 65536-node chunk (new numbering) and of the two
+ *                     neighbouring chunks stores 16-bit columns (the low 16
+ *                     bits; the chunk of each entry follows from its band,
+ *                     see below), other slices store int32 columns.  Inside
+ *                     such a slice each row keeps its entries in three
+ *                     bands: previous chunk, next chunk, own chunk, with at
+ *                     most 63 entries in each of the first two and at most
+ *                     4095 entries in all;
+ *   PDCA_COLUMNS_32   int32 columns in every slice. */
+enum { PDCA_COLUMNS_AUTO = 0, PDCA_COLUMNS_32 = 1 };
+
 /* Arithmetic of the sweeps.
  *   PDCA_FP32               FP32 pre-scaled weights and iterates, FP32
- *                           accumulation, FP64 accumulation across warps in the
- *                           reductions;
- *   PDCA_MIXED_BF16W_FP16U  BF16 weights; per outer step an FP32 pass forms the
- *                           residual r = b^t - T u^t from the FP32 iterate, the
- *                           inner sweeps then iterate the correction
- *                           e <- e + G^{-1}(r - T e) with r and e stored in FP16
- *                           (FP32 arithmetic), and u^{t+1} = u^t + e in FP32 --
- *                           the same iteration as the FP32 sweeps, rearranged;
- *   PDCA_MIXED_BF16W_BF16U  the same with r and e stored in BF16.
+ *                           accumulation; the reductions add per-row terms
+ *                           in compensated (two-float) arithmetic and FP64;
+ *   PDCA_MIXED_BF16W_FP16U  per outer step one FP32 pass (FP32 weights, FP32
+ *                           iterate) forms the residual r = b^t - T u^t and
+ *                           stores it in FP32; the inner sweeps then iterate
+ *                           the correction e <- e + G^{-1}(r - T e) with BF16
+ *                           weights and e stored in FP16 (FP32 arithmetic),
+ *                           and u^{t+1} = u^t + e in FP32 -- the same
+ *                           iteration as the FP32 sweeps, rearranged;
+ *   PDCA_MIXED_BF16W_BF16U  the same with e stored in BF16.
  * The mixed forms use the plain (non-tiled) kernels. */
 enum { PDCA_FP32 = 0, PDCA_MIXED_BF16W_FP16U = 1, PDCA_MIXED_BF16W_BF16U = 2 };
 
@@ -166,6 +181,7 @@ typedef struct {
     int32_t entry_order; /* PDCA_ENTRIES_SPREAD (default) / PDCA_ENTRIES_CSR              */
     double step_k;       /* step size k > 0 of the DCA with step size, or 0 for the
                             infinite step size (Prop. nopre, the default)            */
+    int32_t columns;     /* PDCA_COLUMNS_AUTO (default) / PDCA_COLUMNS_32             */
 } pdca_params;
 
 typedef struct pdca_problem pdca_problem;
@@ -266,10 +282,12 @@ pdca_status pdca_lambda_max(pdca_problem *h, double *lambda_used, double *lambda
 
 /* Layout facts of a created problem: padded sliced-ELL entries, number of
  * 32-row slices, degree-sort window, whether the tiled kernels run, the total
- * and the largest number of halo rows over tiles (0 if not tiled).  Any
+ * and the largest number of halo rows over tiles (0 if not tiled), and the
+ * number of slices stored with 16-bit columns (PDCA_COLUMNS_AUTO).  Any
  * pointer may be NULL. */
 pdca_status pdca_layout(pdca_problem *h, int64_t *sell_entries, int64_t *n_slices,
-                        int32_t *sort_window, int32_t *tiled, int64_t *halo_rows, int32_t *max_halo);
+                        int32_t *sort_window, int32_t *tiled, int64_t *halo_rows, int32_t *max_halo,
+                        int64_t *slices16);
 
 /* CUDA graph replay of pdca_solve: with on = 1, a call without traces (and
  * with profiling off, a plain non-tiled handle and a non-default stream) is

@@ -37,6 +37,7 @@ PDCA_FP32, PDCA_MIXED_BF16W_FP16U, PDCA_MIXED_BF16W_BF16U = 0, 1, 2
 PDCA_REORDER_NONE, PDCA_REORDER_BFS = 0, 1
 PDCA_TILING_AUTO, PDCA_TILING_OFF, PDCA_TILING_ON = 0, 1, 2
 PDCA_ENTRIES_SPREAD, PDCA_ENTRIES_CSR = 0, 1
+PDCA_COLUMNS_AUTO, PDCA_COLUMNS_32 = 0, 1
 
 # every symbol include/pdca.h declares
 EXPORTS = [
@@ -65,7 +66,7 @@ class pdca_params(C.Structure):
         ("damping", C.c_double), ("delta0", C.c_double), ("lambda_max", C.c_double),
         ("power_iters", C.c_int32), ("precision", C.c_int32),
         ("sort_window", C.c_int32), ("reorder", C.c_int32), ("tiling", C.c_int32),
-        ("entry_order", C.c_int32), ("step_k", C.c_double),
+        ("entry_order", C.c_int32), ("step_k", C.c_double), ("columns", C.c_int32),
     ]
 
 
@@ -96,7 +97,7 @@ def lib():
                 "pdca_labels": (C.c_int, [vp, vp]),
                 "pdca_lambda_max": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(dbl)]),
                 "pdca_layout": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32),
-                                          C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]),
+                                          C.POINTER(i32), C.POINTER(i64), C.POINTER(i32), C.POINTER(i64)]),
                 "pdca_profile_enable": (C.c_int, [vp, i32]),
                 "pdca_profile_read": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i64)]),
                 "pdca_kernel_launches": (u64, []),
@@ -152,7 +153,8 @@ def _ptr(a) -> Optional[int]:
 def make_params(eps=1.0, c=3.0, eta=1.0, precond=PDCA_JACOBI_PERTURBED, damping=0.5, delta0=1e-6,
                 lambda_max=0.0, power_iters=150, laplacian=PDCA_LAP_NORMALIZED,
                 precision=PDCA_FP32, sort_window=0, reorder=PDCA_REORDER_BFS,
-                tiling=PDCA_TILING_AUTO, step_k=0.0, entry_order=PDCA_ENTRIES_SPREAD) -> pdca_params:
+                tiling=PDCA_TILING_AUTO, step_k=0.0, entry_order=PDCA_ENTRIES_SPREAD,
+                columns=PDCA_COLUMNS_AUTO) -> pdca_params:
     p = pdca_params()
     lib().pdca_default_params(C.byref(p))
     p.eps, p.c, p.eta = float(eps), float(c), float(eta)
@@ -161,6 +163,7 @@ def make_params(eps=1.0, c=3.0, eta=1.0, precond=PDCA_JACOBI_PERTURBED, damping=
     p.laplacian, p.precision, p.sort_window = int(laplacian), int(precision), int(sort_window)
     p.reorder, p.tiling, p.step_k = int(reorder), int(tiling), float(step_k)
     p.entry_order = int(entry_order)
+    p.columns = int(columns)
     return p
 
 
@@ -231,10 +234,11 @@ def pdca_lambda_max(h):
 
 def pdca_layout(h):
     e, s, w = C.c_int64(0), C.c_int64(0), C.c_int32(0)
-    t, hr, mh = C.c_int32(0), C.c_int64(0), C.c_int32(0)
-    st = lib().pdca_layout(h, C.byref(e), C.byref(s), C.byref(w), C.byref(t), C.byref(hr), C.byref(mh))
+    t, hr, mh, s16 = C.c_int32(0), C.c_int64(0), C.c_int32(0), C.c_int64(0)
+    st = lib().pdca_layout(h, C.byref(e), C.byref(s), C.byref(w), C.byref(t), C.byref(hr), C.byref(mh),
+                           C.byref(s16))
     return st, dict(sell_entries=e.value, n_slices=s.value, sort_window=w.value, tiled=bool(t.value),
-                    halo_rows=hr.value, max_halo=mh.value)
+                    halo_rows=hr.value, max_halo=mh.value, slices16=s16.value)
 
 
 def pdca_profile_enable(h, on: bool) -> int:

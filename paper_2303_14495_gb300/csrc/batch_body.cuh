@@ -11,56 +11,65 @@ namespace {
 
 using namespace dev;
 
-template <int K, class HT, bool UN>
+template <int K, class HT, bool UN, bool C16>
 __device__ __forceinline__ void mixed_pass(const BatchDesc &d, int slice, int lane) {
     if (d.kind == kPassMixedResidual) {
         const float *u = static_cast<const float *>(d.src);
-        HT *r = static_cast<HT *>(d.dst);
+        float *r = static_cast<float *>(d.dst);
         HT *e = static_cast<HT *>(d.dst2);
-        if (!d.last) mixed_residual_slice<K, HT, false, false, UN>(d.A, d.cf, slice, lane, u, r, e, d.u_out);
+        if (!d.last) mixed_residual_slice<K, HT, false, false, UN, C16>(d.A, d.cf, slice, lane, u, r, e, d.u_out);
         else if (d.project)
-            mixed_residual_slice<K, HT, true, (K >= 2), UN>(d.A, d.cf, slice, lane, u, r, e, d.u_out);
-        else mixed_residual_slice<K, HT, true, false, UN>(d.A, d.cf, slice, lane, u, r, e, d.u_out);
+            mixed_residual_slice<K, HT, true, (K >= 2), UN, C16>(d.A, d.cf, slice, lane, u, r, e, d.u_out);
+        else mixed_residual_slice<K, HT, true, false, UN, C16>(d.A, d.cf, slice, lane, u, r, e, d.u_out);
     } else {
         const HT *es = static_cast<const HT *>(d.src);
-        const HT *rr = static_cast<const HT *>(d.aux);
+        const float *rr = static_cast<const float *>(d.aux);
         HT *ed = static_cast<HT *>(d.dst);
-        if (!d.last) mixed_sweep_slice<K, HT, false, false, UN>(d.A, d.cf, slice, lane, es, rr, ed, d.u, d.u_out);
+        if (!d.last)
+            mixed_sweep_slice<K, HT, false, false, UN, C16>(d.A, d.cf, slice, lane, es, rr, ed, d.u, d.u_out);
         else if (d.project)
-            mixed_sweep_slice<K, HT, true, (K >= 2), UN>(d.A, d.cf, slice, lane, es, rr, ed, d.u, d.u_out);
-        else mixed_sweep_slice<K, HT, true, false, UN>(d.A, d.cf, slice, lane, es, rr, ed, d.u, d.u_out);
+            mixed_sweep_slice<K, HT, true, (K >= 2), UN, C16>(d.A, d.cf, slice, lane, es, rr, ed, d.u, d.u_out);
+        else mixed_sweep_slice<K, HT, true, false, UN, C16>(d.A, d.cf, slice, lane, es, rr, ed, d.u, d.u_out);
     }
 }
 
-// A problem's pass with the slice body of its Laplacian (UN: L = D - W).
-template <int K, bool UN>
+// A problem's pass with the slice body of its Laplacian (UN: L = D - W) and
+// of its column format.
+template <int K, bool UN, bool C16>
 __device__ __forceinline__ void member_pass(const BatchDesc &d, int slice, int lane) {
     if (d.kind == kPassFp32) {
         const float *src = static_cast<const float *>(d.src);
         const float *ut = static_cast<const float *>(d.aux);
         float *dst = static_cast<float *>(d.dst);
-        if (d.project) fp32_sweep_slice<K, (K >= 2), UN>(d.A, d.cf, slice, lane, src, ut, dst);
-        else fp32_sweep_slice<K, false, UN>(d.A, d.cf, slice, lane, src, ut, dst);
+        if (d.project) fp32_sweep_slice<K, (K >= 2), UN, C16>(d.A, d.cf, slice, lane, src, ut, dst);
+        else fp32_sweep_slice<K, false, UN, C16>(d.A, d.cf, slice, lane, src, ut, dst);
     } else if (d.bf16u) {
-        mixed_pass<K, __nv_bfloat16, UN>(d, slice, lane);
+        mixed_pass<K, __nv_bfloat16, UN, C16>(d, slice, lane);
     } else {
-        mixed_pass<K, __half, UN>(d, slice, lane);
+        mixed_pass<K, __half, UN, C16>(d, slice, lane);
     }
 }
 
+// Every member's slices start at a multiple of 8 in the launch's slice range
+// (slice_begin), so the 8 warps of a block work on 8 slices of one member,
+// inside one format group: the member and the column format are uniform
+// over the block.  Warps past the member's last slice return.
 template <int K, bool UN>
 __global__ void __launch_bounds__(kBlockThreads, 4) batch_pass_kernel(const __grid_constant__ BatchTable t) {
-    const int gs = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (gs >= t.total_slices) return;
+    const int b0 = blockIdx.x * kWarpsPerBlock;
+    if (b0 >= t.total_slices) return;
     int lo = 0, hi = t.n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (t.d[mid].slice_begin <= gs) lo = mid;
+        if (t.d[mid].slice_begin <= b0) lo = mid;
         else hi = mid - 1;
     }
     const BatchDesc &d = t.d[lo];
-    const int slice = gs - d.slice_begin;
-    member_pass<K, UN>(d, slice, threadIdx.x & 31);
+    const int first = b0 - d.slice_begin;
+    const int slice = first + (threadIdx.x >> 5);
+    if (slice >= d.A.n_slices) return;
+    if (block_fmt16(d.A, first)) member_pass<K, UN, true>(d, slice, threadIdx.x & 31);
+    else member_pass<K, UN, false>(d, slice, threadIdx.x & 31);
 }
 
 template <int K, bool UN>

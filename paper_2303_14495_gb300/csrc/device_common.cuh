@@ -235,44 +235,195 @@ __device__ __forceinline__ const WT *weights_of(const SellView &A) {
     else return A.wb;
 }
 
-template <int K, class WT = float, class XT = float>
-__device__ __forceinline__ void gather_row_sum(const SellView &A, int64_t base, int len, int lane,
-                                               const XT *__restrict__ x, float (&acc)[K]) {
+// ---------------------------------------------------------------------------
+// plain gathers: acc[k] = sum_j wt_ij x_jk over the lane's row, in either
+// column format of the slice (int32 columns, or 16-bit columns whose chunk
+// follows from the entry's band).  `info` is the row's rowinfo word.  The
+// lane reads only its own ceil(len / kVec) groups, so the slice padding
+// beyond a row's end is never fetched; the padding inside a row's last
+// group points at the row itself with weight 0.
+// ---------------------------------------------------------------------------
+template <bool C16> struct ColFmt { using G = int4; };          // four int32 columns
+template <> struct ColFmt<true> { using G = uint2; };           // four 16-bit columns
+template <class WT> struct WFmt { using G = float4; };          // four FP32 weights
+template <> struct WFmt<__nv_bfloat16> { using G = uint2; };    // four BF16 weights
+
+template <class WT>
+__device__ __forceinline__ float4 wgroup(const typename WFmt<WT>::G &g) {
+    if constexpr (std::is_same_v<WT, float>) {
+        return g;
+    } else {
+        const float2 a = unpack2<__nv_bfloat16>(g.x), b = unpack2<__nv_bfloat16>(g.y);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+__device__ __forceinline__ int info_len(uint32_t info, bool c16) {
+    return c16 ? (int)((info >> 8) & kLen16Max) : (int)(info >> 8);
+}
+
+// Bands of a row with 16-bit columns: entries j < np lie in the previous
+// 65536-node chunk, np <= j < nb in the next one, the rest (and the padding)
+// in the row's own chunk, which starts at node `own`.
+struct Bands {
+    int own, np, nb;
+};
+template <bool C16>
+__device__ __forceinline__ Bands bands_of(uint32_t info, int r) {
+    Bands b{0, 0, 0};
+    if constexpr (C16) {
+        b.own = r & ~((1 << kChunkShift) - 1);
+        b.np = (int)((info >> 20) & kBandMax);
+        b.nb = b.np + (int)((info >> 26) & kBandMax);
+    }
+    return b;
+}
+
+__device__ __forceinline__ int group_col(const int4 &c, int i);
+__device__ __forceinline__ int group_col(const uint2 &c, int i);
+// column i of entry group g
+__device__ __forceinline__ int entry_col(const int4 &c, int i, int, const Bands &) { return group_col(c, i); }
+__device__ __forceinline__ int entry_col(const uint2 &c, int i, int g, const Bands &b) {
+    const int j = kVec * g + i;
+    const int hi = j < b.np ? b.own - (1 << kChunkShift) : (j < b.nb ? b.own + (1 << kChunkShift) : b.own);
+    return hi + group_col(c, i);
+}
+
+// Entry streams of one lane's row, with the first two groups loaded ahead.
+template <bool C16, class WT>
+struct EntryStream {
+    using CG = typename ColFmt<C16>::G;
+    using WG = typename WFmt<WT>::G;
+    const CG *cp;
+    const WG *wp;
+    CG c0, c1;
+    WG w0, w1;
+};
+
+// Issue the loads of the first two entry groups (they depend only on the
+// slice) -- before the row's own data, so their latency overlaps it.  Group
+// 0 always exists (every slice is at least kVec wide); group 1 is loaded when
+// the slice has it.
+template <bool C16, class WT>
+__device__ __forceinline__ void stream_open(const SellView &A, int slice, int lane, EntryStream<C16, WT> &s) {
+    const int64_t base = A.slice_off[slice];
+    if constexpr (C16) s.cp = reinterpret_cast<const uint2 *>(A.col16 + base) + lane;
+    else s.cp = reinterpret_cast<const int4 *>(A.col + base) + lane;
+    s.wp = reinterpret_cast<const typename WFmt<WT>::G *>(weights_of<WT>(A) + base) + lane;
+    const int width_groups = (int)((A.slice_off[slice + 1] - base) >> 5) / kVec;
+    s.c0 = ld_stream(s.cp);
+    s.w0 = ld_stream(s.wp);
+    if (width_groups > 1) {
+        s.c1 = ld_stream(s.cp + 32);
+        s.w1 = ld_stream(s.wp + 32);
+    }
+}
+
+template <int K, class XT, class CG>
+__device__ __forceinline__ void fma_entry_group(float (&acc)[K], const CG &c, const float4 &w, int g,
+                                                const Bands &b, const XT *__restrict__ x) {
+    float r0[K], r1[K], r2[K], r3[K];
+    load_row_t<K, XT>(x + (size_t)entry_col(c, 0, g, b) * K, r0);
+    load_row_t<K, XT>(x + (size_t)entry_col(c, 1, g, b) * K, r1);
+    load_row_t<K, XT>(x + (size_t)entry_col(c, 2, g, b) * K, r2);
+    load_row_t<K, XT>(x + (size_t)entry_col(c, 3, g, b) * K, r3);
+    fma_row<K>(acc, w.x, r0);
+    fma_row<K>(acc, w.y, r1);
+    fma_row<K>(acc, w.z, r2);
+    fma_row<K>(acc, w.w, r3);
+}
+
+// The gather proper: while a lane works on two entry groups the next two are
+// in flight; products are added in entry order.
+template <int K, bool C16, class WT, class XT>
+__device__ __forceinline__ void stream_gather(EntryStream<C16, WT> &s, uint32_t info, int r,
+                                              const XT *__restrict__ x, float (&acc)[K]) {
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0f;
-    const int4 *__restrict__ cp = reinterpret_cast<const int4 *>(A.col + base) + lane;
-    const WT *__restrict__ wp = weights_of<WT>(A) + base + kVec * lane;
-    const int groups = (len + kVec - 1) / kVec;   // this lane's groups only
+    const Bands b = bands_of<C16>(info, r);
+    const int groups = (info_len(info, C16) + kVec - 1) / kVec;   // this lane's own groups
+    for (int g = 0; g < groups; g += 2) {
+        typename ColFmt<C16>::G n0 = s.c0, n1 = s.c1;
+        typename WFmt<WT>::G nw0 = s.w0, nw1 = s.w1;
+        if (g + 2 < groups) {
+            n0 = ld_stream(s.cp + 32 * (g + 2));
+            nw0 = ld_stream(s.wp + 32 * (g + 2));
+        }
+        if (g + 3 < groups) {
+            n1 = ld_stream(s.cp + 32 * (g + 3));
+            nw1 = ld_stream(s.wp + 32 * (g + 3));
+        }
+        fma_entry_group<K, XT>(acc, s.c0, wgroup<WT>(s.w0), g, b, x);
+        if (g + 1 < groups) fma_entry_group<K, XT>(acc, s.c1, wgroup<WT>(s.w1), g + 1, b, x);
+        s.c0 = n0;
+        s.w0 = nw0;
+        s.c1 = n1;
+        s.w1 = nw1;
+    }
+}
+
+// The gather without look-ahead: each step loads two entry groups, then
+// their eight rows, then adds the products in entry order.  It holds fewer
+// registers than stream_gather; the mixed-precision passes use it and keep
+// six blocks per SM.
+template <int K, bool C16, class WT, class XT>
+__device__ __forceinline__ void short_gather(const SellView &A, int slice, int lane, uint32_t info, int r,
+                                             const XT *__restrict__ x, float (&acc)[K]) {
+    using CG = typename ColFmt<C16>::G;
+    using WG = typename WFmt<WT>::G;
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0f;
+    const int64_t base = A.slice_off[slice];
+    const CG *cp;
+    if constexpr (C16) cp = reinterpret_cast<const uint2 *>(A.col16 + base) + lane;
+    else cp = reinterpret_cast<const int4 *>(A.col + base) + lane;
+    const WG *wp = reinterpret_cast<const WG *>(weights_of<WT>(A) + base) + lane;
+    const Bands b = bands_of<C16>(info, r);
+    const int groups = (info_len(info, C16) + kVec - 1) / kVec;
     int g = 0;
     for (; g + 2 <= groups; g += 2) {
-        const int4 ca = ld_stream(cp + 32 * g), cb = ld_stream(cp + 32 * (g + 1));
-        const float4 wa = load_w_group<WT>(wp + 32 * kVec * g), wb = load_w_group<WT>(wp + 32 * kVec * (g + 1));
-        // all eight rows in flight before the first product
-        float x0[K], x1[K], x2[K], x3[K], y0[K], y1[K], y2[K], y3[K];
-        load_row_t<K, XT>(x + (size_t)ca.x * K, x0);
-        load_row_t<K, XT>(x + (size_t)ca.y * K, x1);
-        load_row_t<K, XT>(x + (size_t)ca.z * K, x2);
-        load_row_t<K, XT>(x + (size_t)ca.w * K, x3);
-        load_row_t<K, XT>(x + (size_t)cb.x * K, y0);
-        load_row_t<K, XT>(x + (size_t)cb.y * K, y1);
-        load_row_t<K, XT>(x + (size_t)cb.z * K, y2);
-        load_row_t<K, XT>(x + (size_t)cb.w * K, y3);
+        const CG ca = ld_stream(cp + 32 * g), cb = ld_stream(cp + 32 * (g + 1));
+        const float4 wa = wgroup<WT>(ld_stream(wp + 32 * g)), wb = wgroup<WT>(ld_stream(wp + 32 * (g + 1)));
+        float x0[K], x1[K], x2[K], x3[K], y0[K], y1[K], y2[K], y3[K];   // all eight rows in flight
+        load_row_t<K, XT>(x + (size_t)entry_col(ca, 0, g, b) * K, x0);
+        load_row_t<K, XT>(x + (size_t)entry_col(ca, 1, g, b) * K, x1);
+        load_row_t<K, XT>(x + (size_t)entry_col(ca, 2, g, b) * K, x2);
+        load_row_t<K, XT>(x + (size_t)entry_col(ca, 3, g, b) * K, x3);
+        load_row_t<K, XT>(x + (size_t)entry_col(cb, 0, g + 1, b) * K, y0);
+        load_row_t<K, XT>(x + (size_t)entry_col(cb, 1, g + 1, b) * K, y1);
+        load_row_t<K, XT>(x + (size_t)entry_col(cb, 2, g + 1, b) * K, y2);
+        load_row_t<K, XT>(x + (size_t)entry_col(cb, 3, g + 1, b) * K, y3);
         fma_row<K>(acc, wa.x, x0); fma_row<K>(acc, wa.y, x1);
         fma_row<K>(acc, wa.z, x2); fma_row<K>(acc, wa.w, x3);
         fma_row<K>(acc, wb.x, y0); fma_row<K>(acc, wb.y, y1);
         fma_row<K>(acc, wb.z, y2); fma_row<K>(acc, wb.w, y3);
     }
     if (g < groups) {
-        const int4 ca = ld_stream(cp + 32 * g);
-        const float4 wa = load_w_group<WT>(wp + 32 * kVec * g);
-        float x0[K], x1[K], x2[K], x3[K];
-        load_row_t<K, XT>(x + (size_t)ca.x * K, x0);
-        load_row_t<K, XT>(x + (size_t)ca.y * K, x1);
-        load_row_t<K, XT>(x + (size_t)ca.z * K, x2);
-        load_row_t<K, XT>(x + (size_t)ca.w * K, x3);
-        fma_row<K>(acc, wa.x, x0); fma_row<K>(acc, wa.y, x1);
-        fma_row<K>(acc, wa.z, x2); fma_row<K>(acc, wa.w, x3);
+        const CG ca = ld_stream(cp + 32 * g);
+        const float4 wa = wgroup<WT>(ld_stream(wp + 32 * g));
+        fma_entry_group<K, XT>(acc, ca, wa, g, b, x);
     }
+}
+
+// Column format of the slices one block handles.  The format is decided per
+// group of kFmtGroupSlices slices, and every block of the plain kernels works
+// inside one group (queue ranges of 8, 16 or 32 slices aligned to their size;
+// 8 slices in the batched and spectral kernels), so the branch is uniform over
+// the block and the two forms of a kernel body never share registers.
+__device__ __forceinline__ bool block_fmt16(const SellView &A, int first_slice) {
+    return A.slice_fmt != nullptr && __ldg(A.slice_fmt + first_slice) == kFmt16;
+}
+
+// One row's gather with nothing else overlapped; returns its rowinfo word.
+template <int K, class WT, class XT, bool C16>
+__device__ __forceinline__ uint32_t row_gather(const SellView &A, int slice, int lane, const XT *__restrict__ x,
+                                               float (&acc)[K]) {
+    const int r = slice * kSliceRows + lane;
+    const uint32_t info = ld_stream(A.rowinfo + r);
+    EntryStream<C16, WT> s;
+    stream_open(A, slice, lane, s);
+    stream_gather<K, C16, WT, XT>(s, info, r, x, acc);
+    return info;
 }
 
 // Tiled form: 16-bit local columns (four per 64-bit load) into the halo rows
@@ -431,23 +582,49 @@ __device__ __forceinline__ void project_simplex(float (&u)[K]) {
 }
 
 
-// Sum S values over the block (WARPS warps) in a fixed order and store them
-// at out[0..S): each warp sums its 32 lanes in FP32 (fixed shuffle tree),
-// the warp totals are summed in FP64.
+// Reductions.  Per-row terms are formed in FP32; sums over rows are kept as
+// an unevaluated pair hi + lo of floats (TwoSum of every addition, about 48
+// significant bits: compensated summation in the FP32 pipe, because FP64
+// throughput on GB300 is a small fraction of FP32's) inside a warp, and in
+// FP64 across warps and blocks.  Fixed shuffle tree, fixed order.
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
 
+// (hi, lo) += (bhi, blo) for two-float numbers (|lo| <= ulp(hi) / 2)
+__device__ __forceinline__ void df_add(float &hi, float &lo, float bhi, float blo) {
+    float sum, err;
+    two_sum(hi, bhi, sum, err);
+    err += lo + blo;
+    hi = sum + err;
+    lo = err - (hi - sum);
+}
+
+// Sum of v over the warp's 32 lanes in two-float arithmetic, as a double
+// (the value lane 0 holds is the one used).
+__device__ __forceinline__ double warp_sum_df(float v) {
+    float hi = v, lo = 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bhi = __shfl_xor_sync(kFull, hi, o), blo = __shfl_xor_sync(kFull, lo, o);
+        df_add(hi, lo, bhi, blo);
+    }
+    return (double)hi + (double)lo;
+}
+
+// Sum S values over the block (WARPS warps) in a fixed order and store them
+// at out[0..S): each warp sums its 32 lanes in two-float arithmetic, the
+// warp totals are summed in FP64.
 template <int S, int WARPS = kWarpsPerBlock>
 __device__ __forceinline__ void block_sum_store(float (&v)[S], double *__restrict__ out) {
     __shared__ double sm[WARPS][S];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        const float t = warp_sum_f(v[s]);
-        if (lane == 0) sm[warp][s] = (double)t;
+        const double t = warp_sum_df(v[s]);
+        if (lane == 0) sm[warp][s] = t;
     }
     __syncthreads();
     if (threadIdx.x < S) {
@@ -553,7 +730,19 @@ __device__ __forceinline__ void for_block_slices(int first, int count, int n_sli
     }
 }
 
-// Per-lane state of one slice row, loaded before the gather.
+// The same, with the body told the block's column format:
+// f(slice, std::true_type) for 16-bit columns, f(slice, std::false_type)
+// for int32 columns.
+template <class F>
+__device__ __forceinline__ void for_block_slices_fmt(const SellView &A, int first, int count, int *next_slot,
+                                                     F &&f) {
+    if (block_fmt16(A, first))
+        for_block_slices(first, count, A.n_slices, next_slot, [&](int slice) { f(slice, std::true_type{}); });
+    else
+        for_block_slices(first, count, A.n_slices, next_slot, [&](int slice) { f(slice, std::false_type{}); });
+}
+
+// Per-lane state of one slice row, loaded before the gather (tiled form).
 template <int K, class IdxT>
 struct SliceRow {
     uint32_t info;
@@ -627,32 +816,58 @@ __device__ __forceinline__ void slice_gather(SliceRow<K, IdxT> &s, const float *
     }
 }
 
-// FP32 sweep of one slice (plain gathers, pipelined: the independent loads
-// first, the next two entry groups in flight while two are processed; the
-// products are added in entry order, as in gather_row_sum).
-template <int K, bool PROJECT, bool UN>
+// The row's own data, read by this lane only (L1 is kept for the gathers).
+template <int K>
+__device__ __forceinline__ void load_own_row(const float *__restrict__ p, float (&x)[K]) {
+    if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q) {
+            const float4 t = ld_stream(reinterpret_cast<const float4 *>(p) + q);
+            x[4 * q + 0] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
+        }
+    } else {
+        load_row<K>(p, x);
+    }
+}
+
+// FP32 sweep of one slice: the loads that depend on nothing (the row tag and
+// length, the first two entry groups, the own rows of v^s and u^t) first,
+// then the pipelined gather, then the update.
+template <int K, bool PROJECT, bool UN, bool C16>
 __device__ __forceinline__ void fp32_sweep_slice(const SellView &A, const Coeffs &cf, int slice, int lane,
                                                  const float *__restrict__ v_src, const float *__restrict__ u_t,
                                                  float *__restrict__ v_dst) {
-    SliceRow<K, int4> s;
-    slice_prologue<K, UN>(A, reinterpret_cast<const int4 *>(A.col), slice, lane, v_src, u_t, s);
+    const int r = slice * kSliceRows + lane;
+    const uint32_t info = ld_stream(A.rowinfo + r);
+    EntryStream<C16, float> s;
+    stream_open(A, slice, lane, s);
+    const float a = UN ? __ldg(A.self + r) : 1.0f;
+    float v[K], u[K];
+    load_row<K>(v_src + (size_t)r * K, v);
+    if (u_t == v_src) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) u[k] = v[k];
+    } else {
+        load_own_row<K>(u_t + (size_t)r * K, u);
+    }
     float acc[K];
-    slice_gather<K, kGlobal>(s, v_src, nullptr, nullptr, acc);
-    sweep_update<K, PROJECT, UN>(cf, s.info, s.a, acc, s.v, s.u,
-                                 v_dst + (size_t)(slice * kSliceRows + lane) * K, A.stream_rows != 0);
+    stream_gather<K, C16, float, float>(s, info, r, v_src, acc);
+    sweep_update<K, PROJECT, UN>(cf, info, a, acc, v, u, v_dst + (size_t)r * K, A.stream_rows != 0);
 }
 
-// Mixed precision, pass 0 of an outer step: r = b^t - T u^t and e^1 = G^-1 r
-// (or, with a single sweep, u^{t+1} = u^t + e^1).
-template <int K, class HT, bool LAST, bool PROJECT, bool UN>
+// Mixed precision, pass 0 of an outer step: r = b^t - T u^t with FP32
+// weights and the FP32 iterate (the FP32 residual correction), stored in
+// FP32, and e^1 = G^-1 r in 16-bit storage (or, with a single sweep,
+// u^{t+1} = u^t + e^1).
+template <int K, class HT, bool LAST, bool PROJECT, bool UN, bool C16>
 __device__ __forceinline__ void mixed_residual_slice(const SellView &A, const Coeffs &cf, int slice, int lane,
-                                                     const float *__restrict__ u, HT *__restrict__ r_out,
+                                                     const float *__restrict__ u, float *__restrict__ r_out,
                                                      HT *__restrict__ e_out, float *__restrict__ u_out) {
     const int r = slice * kSliceRows + lane;
-    const uint32_t info = ld_stream(A.rowinfo + r);   // read by this lane only
+    const uint32_t info = ld_stream(A.rowinfo + r);
     const float a = UN ? __ldg(A.self + r) : 1.0f;
     float acc[K];
-    gather_row_sum<K, __nv_bfloat16, float>(A, A.slice_off[slice], (int)(info >> 8), lane, u, acc);
+    short_gather<K, C16, float, float>(A, slice, lane, info, r, u, acc);
     float x[K];
     load_row<K>(u + (size_t)r * K, x);
     const uint32_t tag = info & 0xFFu;
@@ -672,35 +887,27 @@ __device__ __forceinline__ void mixed_residual_slice(const SellView &A, const Co
         if constexpr (PROJECT) project_simplex<K>(out);
         store_row<K>(u_out + (size_t)r * K, out);
     } else {
-        store_row_t<K, HT>(r_out + (size_t)r * K, res);
+        store_row<K>(r_out + (size_t)r * K, res);
         store_row_t<K, HT>(e_out + (size_t)r * K, e);
     }
 }
 
-// Mixed precision correction sweep: e' = e + G^-1 (r - T e); the last one
-// writes u^{t+1} = u^t + e' in FP32 (projected for K >= 2).
-template <int K, class HT, bool LAST, bool PROJECT, bool UN>
+// Mixed precision correction sweep with BF16 weights: e' = e + G^-1 (r - T e)
+// (r in FP32, e in 16-bit storage); the last one writes u^{t+1} = u^t + e' in
+// FP32 (projected for K >= 2).
+template <int K, class HT, bool LAST, bool PROJECT, bool UN, bool C16>
 __device__ __forceinline__ void mixed_sweep_slice(const SellView &A, const Coeffs &cf, int slice, int lane,
-                                                  const HT *__restrict__ e_src, const HT *__restrict__ rr,
+                                                  const HT *__restrict__ e_src, const float *__restrict__ rr,
                                                   HT *__restrict__ e_dst, const float *__restrict__ u,
                                                   float *__restrict__ u_out) {
     const int r = slice * kSliceRows + lane;
-    const uint32_t info = ld_stream(A.rowinfo + r);   // read by this lane only
+    const uint32_t info = ld_stream(A.rowinfo + r);
     const float a = UN ? __ldg(A.self + r) : 1.0f;
     float acc[K];
-    gather_row_sum<K, __nv_bfloat16, HT>(A, A.slice_off[slice], (int)(info >> 8), lane, e_src, acc);
+    short_gather<K, C16, __nv_bfloat16, HT>(A, slice, lane, info, r, e_src, acc);
     float e[K], res[K];
     load_row_t<K, HT>(e_src + (size_t)r * K, e);
-    if constexpr (K % 4 == 0) {   // the residual row: read by this lane only
-#pragma unroll
-        for (int q = 0; q < K / 4; ++q) {
-            const uint2 t = ld_stream(reinterpret_cast<const uint2 *>(rr + (size_t)r * K) + q);
-            const float2 lo = unpack2<HT>(t.x), hi = unpack2<HT>(t.y);
-            res[4 * q + 0] = lo.x; res[4 * q + 1] = lo.y; res[4 * q + 2] = hi.x; res[4 * q + 3] = hi.y;
-        }
-    } else {
-        load_row_t<K, HT>(rr + (size_t)r * K, res);
-    }
+    load_own_row<K>(rr + (size_t)r * K, res);   // the residual row: read by this lane only
     const uint32_t tag = info & 0xFFu;
     const bool lab = tag != kTagUnlabelled;
     const float inv_g = inv_g_of<UN>(cf, lab, a);
@@ -713,7 +920,7 @@ __device__ __forceinline__ void mixed_sweep_slice(const SellView &A, const Coeff
     }
     if constexpr (LAST) {
         float x[K];
-        load_row<K>(u + (size_t)r * K, x);
+        load_own_row<K>(u + (size_t)r * K, x);
 #pragma unroll
         for (int k = 0; k < K; ++k) x[k] += en[k];
         if constexpr (PROJECT) project_simplex<K>(x);

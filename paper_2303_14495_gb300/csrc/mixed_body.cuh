@@ -13,23 +13,25 @@ using namespace dev;
 // shared queue (as in the FP32 sweep).
 template <int K, class HT, bool LAST, bool PROJECT, bool UN>
 __global__ void __launch_bounds__(kBlockThreads)
-mixed_residual_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u, HT *__restrict__ r_out,
+mixed_residual_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u, float *__restrict__ r_out,
                       HT *__restrict__ e_out, float *__restrict__ u_out, int iters) {
     __shared__ int next_slot;
     const int count = kWarpsPerBlock * iters;
-    for_block_slices(blockIdx.x * count, count, A.n_slices, &next_slot, [&](int slice) {
-        mixed_residual_slice<K, HT, LAST, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, u, r_out, e_out, u_out);
+    for_block_slices_fmt(A, blockIdx.x * count, count, &next_slot, [&](int slice, auto fmt) {
+        mixed_residual_slice<K, HT, LAST, PROJECT, UN, decltype(fmt)::value>(A, cf, slice, threadIdx.x & 31, u, r_out,
+                                                                             e_out, u_out);
     });
 }
 
 template <int K, class HT, bool LAST, bool PROJECT, bool UN>
 __global__ void __launch_bounds__(kBlockThreads)
-mixed_sweep_kernel(const SellView A, const Coeffs cf, const HT *__restrict__ e_src, const HT *__restrict__ rr,
+mixed_sweep_kernel(const SellView A, const Coeffs cf, const HT *__restrict__ e_src, const float *__restrict__ rr,
                    HT *__restrict__ e_dst, const float *__restrict__ u, float *__restrict__ u_out, int iters) {
     __shared__ int next_slot;
     const int count = kWarpsPerBlock * iters;
-    for_block_slices(blockIdx.x * count, count, A.n_slices, &next_slot, [&](int slice) {
-        mixed_sweep_slice<K, HT, LAST, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, e_src, rr, e_dst, u, u_out);
+    for_block_slices_fmt(A, blockIdx.x * count, count, &next_slot, [&](int slice, auto fmt) {
+        mixed_sweep_slice<K, HT, LAST, PROJECT, UN, decltype(fmt)::value>(A, cf, slice, threadIdx.x & 31, e_src, rr,
+                                                                          e_dst, u, u_out);
     });
 }
 
@@ -38,7 +40,8 @@ cudaError_t residual_ku(bool last, bool project, const SellView &A, const Coeffs
                         void *e, float *u_out, cudaStream_t st) {
     const int iters = sweep_iters(A.n_slices);
     const int blocks = (A.n_slices + kWarpsPerBlock * iters - 1) / (kWarpsPerBlock * iters);
-    HT *rh = static_cast<HT *>(r), *eh = static_cast<HT *>(e);
+    float *rh = static_cast<float *>(r);
+    HT *eh = static_cast<HT *>(e);
     if (!last)
         mixed_residual_kernel<K, HT, false, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, u, rh, eh, u_out, iters);
     else if (project && K >= 2)
@@ -54,7 +57,8 @@ cudaError_t sweep_ku(bool last, bool project, const SellView &A, const Coeffs &c
                      const void *r, void *e_dst, const float *u, float *u_out, cudaStream_t st) {
     const int iters = sweep_iters(A.n_slices);
     const int blocks = (A.n_slices + kWarpsPerBlock * iters - 1) / (kWarpsPerBlock * iters);
-    const HT *es = static_cast<const HT *>(e_src), *rh = static_cast<const HT *>(r);
+    const HT *es = static_cast<const HT *>(e_src);
+    const float *rh = static_cast<const float *>(r);
     HT *ed = static_cast<HT *>(e_dst);
     if (!last)
         mixed_sweep_kernel<K, HT, false, false, UN><<<blocks, kBlockThreads, 0, st>>>(A, cf, es, rh, ed, u, u_out, iters);

@@ -1,6 +1,6 @@
-// Mixed-precision form of one outer pDCA step: BF16 pre-scaled weights,
-// FP16 or BF16 storage of the correction, FP32 arithmetic, FP32 master
-// iterate.
+// Mixed-precision form of one outer pDCA step: an FP32 residual pass, then
+// correction sweeps with BF16 pre-scaled weights and FP16 or BF16 storage of
+// the correction, FP32 arithmetic, FP32 master iterate.
 //
 // The diagonal sweeps of Prop. nopre started from v^0 = u^t are, written for
 // the correction e^s = v^s - u^t,
@@ -8,10 +8,10 @@
 //   e^1  = G^{-1} r                                     (e^0 = 0)
 //   e^{s+1} = e^s + G^{-1} (r - T e^s),   u^{t+1} = u^t + e^m,
 // the same iteration up to rounding (L_s or, in the UN instances, L).  r is
-// formed in FP32 from the FP32
-// iterate; only the small correction e and r travel in 16-bit storage, so
-// their rounding error is relative to |e|, not to |u| (the FP32 residual
-// correction of each outer step).  In
+// formed with the FP32 weights from the FP32 iterate and kept in FP32 (the
+// FP32 residual correction of each outer step); only the correction e travels
+// in 16-bit storage and only its sweeps use the BF16 weights, so their
+// rounding errors are relative to |e|, not to |u|.  In
 //   b - T u = eta Lambda (y - u) - (u^3 - u)/eps - eps (u - sum_j wt_ij u_j)
 // the two c u terms cancel exactly and are never formed.
 #include "mixed_body.cuh"

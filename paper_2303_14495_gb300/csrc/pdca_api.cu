@@ -41,10 +41,11 @@ struct Layout {
     bool host_order = false;           // renumbering computed on the host (BFS blocks)
     int64_t nnz = 0, sell_entries = 0, sell_cap = 0, halo_cap = 0;
     std::vector<int64_t> slice_off;    // n_slices + 1 (exact; filled at create for host order)
-    size_t o_col, o_w, o_slice, o_rowinfo, o_perm, o_iperm, o_self, o_dsq, o_u[3], o_part, o_red, o_scal, o_trace;
+    size_t o_col, o_col16, o_fmt, o_w, o_wb, o_slice, o_rowinfo, o_perm, o_iperm, o_self, o_dsq, o_u[3], o_part,
+        o_red, o_scal, o_trace;
     size_t o_hoff, o_hidx;
-    size_t o_mr, o_me[2];              // mixed precision: r and the two corrections (16-bit)
-    size_t o_srp, o_scol, o_sw, o_sdeg, o_sisd, o_smask, o_slab, o_status;
+    size_t o_mr, o_me[2];              // mixed precision: r (FP32) and the two corrections (16-bit)
+    size_t o_srp, o_scol, o_sw, o_sdeg, o_sisd, o_smask, o_slab, o_scls, o_status;
     size_t persistent = 0, total = 0;
 };
 
@@ -131,6 +132,7 @@ pdca_status check_params(const pdca_params &p) {
     if (p.tiling < PDCA_TILING_AUTO || p.tiling > PDCA_TILING_ON) return PDCA_ERR_INVALID_ARG;
     if (p.tiling == PDCA_TILING_ON && p.reorder != PDCA_REORDER_BFS) return PDCA_ERR_INVALID_ARG;
     if (p.entry_order != PDCA_ENTRIES_SPREAD && p.entry_order != PDCA_ENTRIES_CSR) return PDCA_ERR_INVALID_ARG;
+    if (p.columns != PDCA_COLUMNS_AUTO && p.columns != PDCA_COLUMNS_32) return PDCA_ERR_INVALID_ARG;
     return PDCA_OK;
 }
 
@@ -274,8 +276,12 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     const size_t parts = (size_t)std::max(1, energy_blocks(L.n_slices)) * kRedSlots;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + std::max<size_t>(bytes, 1)); return at; };
+    const bool mixed = prm.precision != PDCA_FP32;
     L.o_col = take(4 * P);
+    L.o_col16 = take(prm.columns == PDCA_COLUMNS_AUTO ? 2 * P : 0);
+    L.o_fmt = take((size_t)L.n_slices);
     L.o_w = take(4 * P);
+    L.o_wb = take(mixed ? 2 * P : 0);
     L.o_slice = take(8 * ((size_t)L.n_slices + 1));
     L.o_rowinfo = take(4 * np);
     L.o_perm = take(4 * np);
@@ -289,8 +295,8 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     L.o_trace = take(8 * 2 * (size_t)kTraceCap);
     L.o_hoff = take(8 * ((size_t)L.n_tiles + 1));
     L.o_hidx = take(4 * (size_t)L.halo_cap);
-    const size_t half_rows = prm.precision == PDCA_FP32 ? 0 : 2 * np * (size_t)K;
-    L.o_mr = take(half_rows);
+    const size_t half_rows = mixed ? 2 * np * (size_t)K : 0;
+    L.o_mr = take(mixed ? 4 * np * (size_t)K : 0);
     L.o_me[0] = take(half_rows);
     L.o_me[1] = take(half_rows);
     L.persistent = o;
@@ -302,6 +308,7 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     L.o_sisd = take(8 * nn);
     L.o_smask = take(nn);
     L.o_slab = take(4 * nn);
+    L.o_scls = take(4 * np);
     L.o_status = take(16);
     L.total = o;
     return PDCA_OK;
@@ -325,7 +332,11 @@ struct pdca_problem {
     cudaStream_t stream = nullptr;
     char *ws = nullptr;
     int32_t *sell_col = nullptr;
-    float *sell_w = nullptr;
+    uint16_t *col16 = nullptr;        // 16-bit columns (PDCA_COLUMNS_AUTO), else nullptr
+    uint8_t *slice_fmt = nullptr;     // kFmt32 / kFmt16 per slice (with col16)
+    int64_t slices16 = 0;             // slices stored with 16-bit columns
+    float *sell_w = nullptr;          // FP32 weights (both precisions)
+    __nv_bfloat16 *sell_wb = nullptr; // BF16 weights (mixed precision)
     int64_t *slice_off = nullptr;
     uint32_t *rowinfo = nullptr;
     int32_t *perm = nullptr, *iperm = nullptr;
@@ -364,8 +375,10 @@ struct pdca_problem {
     SellView view() const {
         SellView A;
         A.col = sell_col;
-        A.w = mixed ? nullptr : sell_w;
-        A.wb = mixed ? reinterpret_cast<const __nv_bfloat16 *>(sell_w) : nullptr;
+        A.col16 = col16;
+        A.slice_fmt = col16 ? slice_fmt : nullptr;
+        A.w = sell_w;
+        A.wb = mixed ? sell_wb : nullptr;
         A.slice_off = slice_off;
         A.rowinfo = rowinfo;
         A.self = self;
@@ -695,7 +708,7 @@ CloneLayout clone_layout(const Layout &L, int32_t K, int32_t precision) {
     C.o_scal = take(8 * 8);
     C.o_trace = take(8 * 2 * (size_t)kTraceCap);
     const size_t half_rows = precision == PDCA_FP32 ? 0 : 2 * np * (size_t)K;
-    C.o_mr = take(half_rows);
+    C.o_mr = take(precision == PDCA_FP32 ? 0 : 4 * np * (size_t)K);
     C.o_me[0] = take(half_rows);
     C.o_me[1] = take(half_rows);
     C.o_smask = take(nn);
@@ -735,6 +748,7 @@ void pdca_default_params(pdca_params *p) {
     p->tiling = PDCA_TILING_AUTO;
     p->entry_order = PDCA_ENTRIES_SPREAD;
     p->step_k = 0.0;
+    p->columns = PDCA_COLUMNS_AUTO;
 }
 
 const char *pdca_status_string(pdca_status s) {
@@ -815,6 +829,8 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     char *W = h->ws;
     h->sell_col = reinterpret_cast<int32_t *>(W + L.o_col);
     h->sell_w = reinterpret_cast<float *>(W + L.o_w);
+    h->sell_wb = prm.precision != PDCA_FP32 ? reinterpret_cast<__nv_bfloat16 *>(W + L.o_wb) : nullptr;
+    h->slice_fmt = reinterpret_cast<uint8_t *>(W + L.o_fmt);
     h->slice_off = reinterpret_cast<int64_t *>(W + L.o_slice);
     h->rowinfo = reinterpret_cast<uint32_t *>(W + L.o_rowinfo);
     h->perm = reinterpret_cast<int32_t *>(W + L.o_perm);
@@ -839,6 +855,7 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     uint8_t *s_mask = reinterpret_cast<uint8_t *>(W + L.o_smask);
     int32_t *s_lab = reinterpret_cast<int32_t *>(W + L.o_slab);
     uint32_t *s_status = reinterpret_cast<uint32_t *>(W + L.o_status);
+    uint32_t *s_cls = reinterpret_cast<uint32_t *>(W + L.o_scls);
     cudaStream_t sm = h->stream;
 
     // BFS renumbering on a host thread, overlapping the copies and validation
@@ -889,16 +906,21 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
                                h->rowinfo, s_status, sm);
     else
         pe = launch_pack(n, L.n_pad, k, s_rp, s_col, s_w, s_deg, s_isd, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
-                         h->sell_col, h->mixed ? nullptr : h->sell_w,
-                         h->mixed ? reinterpret_cast<__nv_bfloat16 *>(h->sell_w) : nullptr, h->self,
-                         h->tiled ? nullptr : h->dsq, h->rowinfo, s_status, sm);
+                         h->sell_col, h->sell_w, h->sell_wb, h->self, h->dsq, h->rowinfo,
+                         prm.columns == PDCA_COLUMNS_AUTO ? s_cls : nullptr, s_status, sm);
     if (pe != cudaSuccess) return fail(PDCA_ERR_CUDA);
+    const bool c16 = !h->tiled && prm.columns == PDCA_COLUMNS_AUTO;
     if (prm.entry_order == PDCA_ENTRIES_SPREAD &&
-        launch_spread(L.n_pad, h->slice_off, h->rowinfo, h->tiled ? nullptr : h->sell_col,
+        launch_spread(L.n_pad, h->slice_off, h->rowinfo, c16 ? s_cls : nullptr, h->tiled ? nullptr : h->sell_col,
                       h->tiled ? const_cast<uint16_t *>(h->tv.lcol) : nullptr, h->tv.halo_off, h->tv.halo_idx,
-                      h->mixed ? nullptr : h->sell_w, h->mixed ? reinterpret_cast<__nv_bfloat16 *>(h->sell_w) : nullptr,
-                      sm) != cudaSuccess)
+                      h->sell_w, h->sell_wb, sm) != cudaSuccess)
         return fail(PDCA_ERR_CUDA);
+    if (c16) {
+        h->col16 = reinterpret_cast<uint16_t *>(W + L.o_col16);
+        if (launch_compress(L.n_slices, h->slice_off, s_cls, h->sell_col, h->col16, h->rowinfo, h->slice_fmt, sm) !=
+            cudaSuccess)
+            return fail(PDCA_ERR_CUDA);
+    }
     if (prm.precond == PDCA_RICHARDSON) {
         if (prm.lambda_max > 0) {
             h->lambda_used = prm.lambda_max;
@@ -914,10 +936,13 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     h->cur = 0;
     h->prev = 1;
     h->has_prev = false;
+    std::vector<uint8_t> fmt(c16 ? (size_t)L.n_slices : 0);
     if (cudaMemcpyAsync(&status, s_status, 4, cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
+        (c16 && cudaMemcpyAsync(fmt.data(), h->slice_fmt, fmt.size(), cudaMemcpyDeviceToHost, sm) != cudaSuccess) ||
         cudaStreamSynchronize(sm) != cudaSuccess)
         return fail(PDCA_ERR_CUDA);
     if (status & kLayoutMismatch) return fail(PDCA_ERR_CUDA);
+    for (uint8_t f : fmt) h->slices16 += f == kFmt16 ? 1 : 0;
     *out = h;
     return PDCA_OK;
 }
@@ -963,7 +988,11 @@ pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t 
     h->stream = base->stream;
     h->ws = static_cast<char *>(workspace);
     h->sell_col = base->sell_col;
+    h->col16 = base->col16;
+    h->slice_fmt = base->slice_fmt;
+    h->slices16 = base->slices16;
     h->sell_w = base->sell_w;
+    h->sell_wb = base->sell_wb;
     h->slice_off = base->slice_off;
     h->perm = base->perm;
     h->iperm = base->iperm;
@@ -1222,8 +1251,9 @@ pdca_status pdca_lambda_max(pdca_problem *h, double *lambda_used, double *lambda
 }
 
 pdca_status pdca_layout(pdca_problem *h, int64_t *sell_entries, int64_t *n_slices, int32_t *sort_window,
-                        int32_t *tiled, int64_t *halo_rows, int32_t *max_halo) {
+                        int32_t *tiled, int64_t *halo_rows, int32_t *max_halo, int64_t *slices16) {
     if (!h) return PDCA_ERR_INVALID_ARG;
+    if (slices16) *slices16 = h->slices16;
     if (sell_entries) *sell_entries = h->L.sell_entries;
     if (n_slices) *n_slices = h->L.n_slices;
     if (sort_window) *sort_window = h->L.sigma;
@@ -1294,7 +1324,8 @@ pdca_status pdca_batch_step(pdca_batch *b, int32_t passes, int32_t *active_after
                     BatchDesc &d = t.d[t.n++];
                     member_desc(m, d);
                     d.slice_begin = t.total_slices;
-                    t.total_slices += m.h->L.n_slices;
+                    // members start at multiples of 8 slices (one block never spans two)
+                    t.total_slices += (m.h->L.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock * kWarpsPerBlock;
                     if (t.n == kBatchMax) {
                         PDCA_TRY(launch_batch_pass(K, un == 1, t, b->stream));
                         t.n = 0;

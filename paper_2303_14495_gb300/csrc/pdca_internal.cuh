@@ -13,7 +13,14 @@
 //     one of weights, and a warp reads 512 contiguous bytes per load;
 //     slice width = longest row of the slice rounded up to kVec; padding
 //     entries point at a valid row with weight 0;
-//   * rowinfo[r] = (row length << 8) | tag, tag = prior class or 0xFF;
+//   * columns: int32 (new numbering), or, in slices that allow it, 16-bit
+//     (the low 16 bits; the column's 65536-node chunk is the row's own, the
+//     previous or the next one, told apart by the entry's band: each row of
+//     such a slice keeps first its entries in the previous chunk, then those
+//     in the next chunk, then those in its own chunk and the padding);
+//   * rowinfo[r] = (row length << 8) | tag, tag = prior class or 0xFF; in a
+//     slice with 16-bit columns: tag | len << 8 (12 bits) | n_prev << 20
+//     (6 bits) | n_next << 26 (6 bits);
 //   * u is n_pad x K float32 row-major (n_pad = 32 * number of slices).
 #pragma once
 
@@ -43,10 +50,17 @@ constexpr uint32_t kLayoutMismatch = 8u;   // internal: packed row longer than i
 
 // The Laplacian as (L x)_i = a_i x_i - sum_j w'_ij x_j:  L_s has a_i = 1 and
 // w' = w_ij / sqrt(d_i d_j);  L = D - W has a_i = d_i and w' = w_ij.
+constexpr int kChunkShift = 16;              // 16-bit columns: 65536-node chunks
+constexpr uint8_t kFmt32 = 0, kFmt16 = 1;   // column format of a slice
+constexpr uint32_t kBandMax = 63;           // largest n_prev / n_next of a 16-bit row
+constexpr uint32_t kLen16Max = 4095;        // longest row of a 16-bit slice
+constexpr int kFmtGroupSlices = 32;         // slices sharing one column format
 struct SellView {
     const int32_t *col;        // padded sliced-ELL column indices (new numbering)
-    const float *w;            // w'_ij, FP32 (FP32 path)
-    const __nv_bfloat16 *wb;   // the same in BF16 (mixed-precision path)
+    const uint16_t *col16;     // low 16 bits of the columns (slices with slice_fmt = kFmt16)
+    const uint8_t *slice_fmt;  // kFmt32 / kFmt16 per slice; nullptr: every slice kFmt32
+    const float *w;            // w'_ij, FP32 (both precisions)
+    const __nv_bfloat16 *wb;   // the same in BF16 (mixed-precision path; nullptr otherwise)
     const int64_t *slice_off;  // n_slices + 1 entry offsets
     const uint32_t *rowinfo;   // (len << 8) | tag, n_pad
     const float *self;         // a_i = d_i per row (n_pad) for L; nullptr for L_s
@@ -68,12 +82,15 @@ struct SellView {
 #define PDCA_SWEEP_MAX_ITERS 4
 #endif
 constexpr int kSmCount = 152;   // GB300
-// slice groups per block for a graph of n_slices slices (at least 4 waves)
+// slice groups per block for a graph of n_slices slices (at least 4 waves):
+// 1, 2 or 4, so a block's range of 8 x iters slices never crosses a group of
+// kFmtGroupSlices slices (one column format per group)
 inline int sweep_iters(int32_t n_slices) {
     const int groups = (n_slices + 7) / 8;
     const int it = groups / (4 * kSmCount * PDCA_SWEEP_MIN_BLOCKS);
-    return it < 1 ? 1 : (it > PDCA_SWEEP_MAX_ITERS ? PDCA_SWEEP_MAX_ITERS : it);
+    return it >= 4 && PDCA_SWEEP_MAX_ITERS >= 4 ? 4 : (it >= 2 && PDCA_SWEEP_MAX_ITERS >= 2 ? 2 : 1);
 }
+static_assert(PDCA_SWEEP_MAX_ITERS * 8 <= kFmtGroupSlices, "a queue range must fit in one format group");
 
 // Tiled form of the operator: tiles of kTileSlices slices; each tile lists
 // the distinct rows its entries reference (its halo, sorted), and every entry
@@ -149,7 +166,8 @@ cudaError_t launch_labels(int K, int32_t n, const float *u, const int32_t *perm,
                           int32_t *out, cudaStream_t st);
 
 // --- mixed precision (mixed_kernels.cu) --------------------------------------
-// r and e are n_pad x K arrays of FP16 (bf16u = false) or BF16 (bf16u = true).
+// r is an n_pad x K FP32 array; e an n_pad x K array of FP16 (bf16u = false)
+// or BF16 (bf16u = true).
 cudaError_t launch_mixed_residual(int K, bool bf16u, bool last, bool project, const SellView &A,
                                   const Coeffs &cf, const float *u, void *r, void *e, float *u_out,
                                   cudaStream_t st);
@@ -180,11 +198,11 @@ enum BatchPassKind : int32_t { kPassFp32 = 0, kPassMixedResidual = 1, kPassMixed
 struct BatchDesc {
     SellView A;
     Coeffs cf;
-    int32_t slice_begin;     // first slice of this problem in the launch's slice range
+    int32_t slice_begin;     // first slice of this problem in the launch's slice range (a multiple of 8)
     int32_t kind;            // BatchPassKind
     int32_t last;            // last pass of the outer step
     int32_t project;         // project rows onto the simplex (last pass, K >= 2)
-    int32_t bf16u;           // mixed: r and e stored as BF16 (else FP16)
+    int32_t bf16u;           // mixed: e stored as BF16 (else FP16); r is FP32
     int32_t pad_;
     const void *src;         // fp32: v^s;  mixed residual: u^t;  mixed sweep: e^s
     const void *aux;         // fp32: u^t;  mixed sweep: r
@@ -213,12 +231,14 @@ cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const in
                                int32_t *perm, int32_t *iperm, cudaStream_t st);
 // self == nullptr: L_s weights w_ij / sqrt(d_i d_j); else L weights w_ij and
 // self[r] = d_i (0 on padding rows).  dsq (nullable): sqrt(d_i) per row.
+// rowcls (nullable): entries are written in bands (previous, next, own
+// chunk) and rowcls[r] records n_prev | n_next << 8 | 16-bit-capable << 16.
 cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_ptr,
                         const int32_t *col, const float *w, const double *deg, const double *isd,
                         const uint8_t *mask, const int32_t *labels, const int32_t *perm,
                         const int32_t *iperm, const int64_t *slice_off, int32_t *sell_col,
                         float *sell_w, __nv_bfloat16 *sell_wb, float *self, float *dsq, uint32_t *rowinfo,
-                        uint32_t *status, cudaStream_t st);
+                        uint32_t *rowcls, uint32_t *status, cudaStream_t st);
 // tiled form: local 16-bit columns (position in the tile's halo) instead of int32
 cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32_t *col, const float *w,
                               const double *deg, const double *isd, const uint8_t *mask, const int32_t *labels,
@@ -229,9 +249,16 @@ cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32
 // Entry order for the gathers (PDCA_ENTRIES_SPREAD), in place after the pack.
 // Exactly one of sell_col (plain form) and lcol (tiled form, with its halo
 // lists) is given, and exactly one of sell_w (FP32) and sell_wb (BF16).
+// rowcls (nullable; from the pack): per row n_prev | n_next << 8 | 16-bit-capable
+// << 16; the entries of a row are reordered only inside their band.
 cudaError_t launch_spread(int32_t n_pad, const int64_t *slice_off, const uint32_t *rowinfo,
-                          int32_t *sell_col, uint16_t *lcol, const int64_t *halo_off, const int32_t *halo_idx,
-                          float *sell_w, __nv_bfloat16 *sell_wb, cudaStream_t st);
+                          const uint32_t *rowcls, int32_t *sell_col, uint16_t *lcol, const int64_t *halo_off,
+                          const int32_t *halo_idx, float *sell_w, __nv_bfloat16 *sell_wb, cudaStream_t st);
+// 16-bit columns for every slice whose rows all allow them (rowcls), the
+// rowinfo of those rows in the 16-bit form, and slice_fmt per slice.
+cudaError_t launch_compress(int32_t n_slices, const int64_t *slice_off, const uint32_t *rowcls,
+                            const int32_t *sell_col, uint16_t *col16, uint32_t *rowinfo, uint8_t *slice_fmt,
+                            cudaStream_t st);
 
 // f(0) .. f(count - 1) on the host's threads (index order per thread is
 // fixed, so results written per index do not depend on the thread count).

@@ -5,8 +5,10 @@
 //   window_sort_kernel  renumbering: rows sorted by degree inside windows;
 //   pack_kernel         sliced-ELL with w_ij d_i^-1/2 d_j^-1/2 (L_s; the
 //                       factors d_i^-1/2 come from validate_kernel) or w_ij plus
-//                       the per-row d_i (L), and the row tags;
+//                       the per-row d_i (L), and the row tags; entries in
+//                       chunk bands where 16-bit columns are possible;
 //   spread_kernel       entry order inside rows for conflict-light gathers;
+//   compress_kernel     16-bit columns for the slices that allow them;
 //   init_u_kernel       u^0 (prior on labelled rows, centre elsewhere).
 #include "pdca_internal.cuh"
 
@@ -116,6 +118,12 @@ __global__ void window_sort_kernel(int32_t n, int32_t n_pad, int32_t sigma,
     }
 }
 
+// One thread per row.  With rowcls, a row's entries are written in three
+// bands -- columns in the previous 65536-node chunk, in the next one, in the
+// row's own chunk (each band in CSR order) -- and rowcls[r] records n_prev |
+// n_next << 8 | 1 << 16 when the row can take 16-bit columns (no column
+// further than one chunk away, the band and length limits met), 0 otherwise
+// (entries then in CSR order).  Padding rows count as able.
 __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
                             const int32_t *__restrict__ col, const float *__restrict__ w,
                             const double *__restrict__ deg, const double *__restrict__ isd,
@@ -125,7 +133,7 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
                             int32_t *__restrict__ sell_col, float *__restrict__ sell_w,
                             __nv_bfloat16 *__restrict__ sell_wb, float *__restrict__ self,
                             float *__restrict__ dsq, uint32_t *__restrict__ rowinfo,
-                            uint32_t *__restrict__ status) {
+                            uint32_t *__restrict__ rowcls, uint32_t *__restrict__ status) {
     const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_pad) return;
     const int32_t s = r >> 5, lane = r & 31;
@@ -134,6 +142,8 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
     const int32_t old = perm[r];
     int32_t len = 0;
     uint32_t tag = kTagUnlabelled;
+    uint32_t cls = 1u << 16;
+    auto at = [&](int32_t j) { return base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec); };
     if (old >= 0) {
         const int64_t e0 = row_ptr[old];
         len = (int32_t)(row_ptr[old + 1] - e0);
@@ -144,26 +154,80 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
         const double di = deg[old];
         if (self) self[r] = (float)di;
         if (dsq) dsq[r] = (float)sqrt(di);
+        // chunk distance of every column: band counts
+        const int32_t hr = r >> kChunkShift;
+        int32_t np = 0, nn = 0;
+        bool banded = rowcls != nullptr;
+        if (banded) {
+            for (int32_t j = 0; j < len; ++j) {
+                const int32_t d = (iperm[col[e0 + j]] >> kChunkShift) - hr;
+                np += d == -1;
+                nn += d == 1;
+                if (d < -1 || d > 1) banded = false;
+            }
+        }
+        int32_t p_prev = 0, p_next = np, p_own = np + nn;
         for (int32_t j = 0; j < len; ++j) {
             const int32_t oj = col[e0 + j];
-            const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
-            sell_col[at] = iperm[oj];
+            const int32_t cj = iperm[oj];
+            int32_t pos = j;
+            if (banded) {
+                const int32_t d = (cj >> kChunkShift) - hr;
+                pos = d < 0 ? p_prev++ : (d > 0 ? p_next++ : p_own++);
+            }
+            const int64_t a = at(pos);
+            sell_col[a] = cj;
             const double wt = self ? (double)w[e0 + j] : (double)w[e0 + j] * isd[old] * isd[oj];
-            if (sell_wb) sell_wb[at] = __double2bfloat16(wt);
-            else sell_w[at] = (float)wt;
+            sell_w[a] = (float)wt;
+            if (sell_wb) sell_wb[a] = __double2bfloat16(wt);
         }
         if (mask[old]) tag = (uint32_t)labels[old];
+        const bool ok16 = banded && (uint32_t)len <= kLen16Max && (uint32_t)np <= kBandMax &&
+                          (uint32_t)nn <= kBandMax;
+        // counts above 255 are kept at 255 (such a row is not 16-bit capable
+        // anyway); the fields must not run into the capability bit
+        cls = banded ? ((uint32_t)min(np, 255) | ((uint32_t)min(nn, 255) << 8) | (ok16 ? 1u << 16 : 0u)) : 0u;
     } else {
         if (self) self[r] = 0.0f;
         if (dsq) dsq[r] = 0.0f;
     }
     for (int32_t j = len; j < width; ++j) {
-        const int64_t at = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
-        sell_col[at] = r;
-        if (sell_wb) sell_wb[at] = __float2bfloat16(0.0f);
-        else sell_w[at] = 0.0f;
+        const int64_t a = at(j);
+        sell_col[a] = r;
+        sell_w[a] = 0.0f;
+        if (sell_wb) sell_wb[a] = __float2bfloat16(0.0f);
     }
     rowinfo[r] = ((uint32_t)len << 8) | tag;
+    if (rowcls) rowcls[r] = cls;
+}
+
+// One block per group of kFmtGroupSlices slices, one warp per slice: when
+// every row of the group can take 16-bit columns (rowcls), store the low 16
+// bits of the group's columns in col16, rewrite its rowinfo words in the
+// 16-bit form (tag | len << 8 | n_prev << 20 | n_next << 26) and mark its
+// slices kFmt16; otherwise mark them kFmt32.  The kernels pick the column
+// format once per block, and no block range crosses a group.
+__global__ void __launch_bounds__(kFmtGroupSlices * 32)
+compress_kernel(int32_t n_slices, const int64_t *__restrict__ slice_off, const uint32_t *__restrict__ rowcls,
+                const int32_t *__restrict__ sell_col, uint16_t *__restrict__ col16, uint32_t *__restrict__ rowinfo,
+                uint8_t *__restrict__ slice_fmt) {
+    const int32_t s = blockIdx.x * kFmtGroupSlices + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const bool real = s < n_slices;   // slices past the end count as able
+    const int32_t r = s * kSliceRows + lane;
+    const uint32_t cls = real ? rowcls[r] : (1u << 16);
+    const bool ok = __syncthreads_and((int)((cls >> 16) & 1u)) != 0;
+    if (!real) return;
+    if (lane == 0) slice_fmt[s] = ok ? kFmt16 : kFmt32;
+    if (!ok) return;
+    const int64_t base = slice_off[s];
+    const int32_t width = (int32_t)((slice_off[s + 1] - base) >> 5);
+    for (int32_t j = 0; j < width; ++j) {
+        const int64_t a = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
+        col16[a] = (uint16_t)((uint32_t)sell_col[a] & 0xFFFFu);
+    }
+    const uint32_t info = rowinfo[r];   // len <= kLen16Max: bits 20..31 are free
+    rowinfo[r] = info | ((cls & 0xFFu) << 20) | (((cls >> 8) & 0xFFu) << 26);
 }
 
 // Tiled form: the column of every entry becomes its position in the tile's
@@ -241,7 +305,8 @@ constexpr int kSpreadLook = 64;
 constexpr int kSpreadLanes = 8;   // S
 
 __global__ void spread_kernel(int32_t n_slices, const int64_t *__restrict__ slice_off,
-                              const uint32_t *__restrict__ rowinfo, int32_t *__restrict__ sell_col,
+                              const uint32_t *__restrict__ rowinfo, const uint32_t *__restrict__ rowcls,
+                              int32_t *__restrict__ sell_col,
                               uint16_t *__restrict__ lcol, const int64_t *__restrict__ halo_off,
                               const int32_t *__restrict__ halo_idx, float *__restrict__ sell_w,
                               __nv_bfloat16 *__restrict__ sell_wb) {
@@ -252,11 +317,15 @@ __global__ void spread_kernel(int32_t n_slices, const int64_t *__restrict__ slic
     const int32_t lane0 = (int32_t)(t % groups) * S;
     const int64_t base = slice_off[s];
     const int64_t h0 = lcol ? halo_off[(s * kSliceRows) / kTileRows] : 0;
-    int32_t len[S];
+    int32_t len[S], np[S], nb[S];
     int32_t maxlen = 0;
 #pragma unroll
     for (int32_t l = 0; l < S; ++l) {
-        len[l] = (int32_t)(rowinfo[s * kSliceRows + lane0 + l] >> 8);
+        const int64_t r = s * kSliceRows + lane0 + l;
+        len[l] = (int32_t)(rowinfo[r] >> 8);
+        const uint32_t c = rowcls ? rowcls[r] : 0u;
+        np[l] = (int32_t)(c & 0xFFu);
+        nb[l] = np[l] + (int32_t)((c >> 8) & 0xFFu);
         maxlen = max(maxlen, len[l]);
     }
     auto at = [&](int32_t lane, int32_t j) {
@@ -270,7 +339,9 @@ __global__ void spread_kernel(int32_t n_slices, const int64_t *__restrict__ slic
         for (int32_t l = 0; l < S; ++l) {
             if (p >= len[l]) continue;
             const int32_t lane = lane0 + l;
-            const int32_t lim = min(len[l], p + kSpreadLook);
+            // the entry stays inside its band (previous, next, own chunk)
+            const int32_t band_end = p < np[l] ? np[l] : (p < nb[l] ? nb[l] : len[l]);
+            const int32_t lim = min(band_end, p + kSpreadLook);
             int32_t pick = -1, slot = 0, grp = 0;
             for (int32_t j = p; j < lim; ++j) {
                 const int32_t c = gcol(at(lane, j));
@@ -301,7 +372,8 @@ __global__ void spread_kernel(int32_t n_slices, const int64_t *__restrict__ slic
                 const __nv_bfloat16 x = sell_wb[a];
                 sell_wb[a] = sell_wb[b];
                 sell_wb[b] = x;
-            } else {
+            }
+            if (sell_w) {
                 const float x = sell_w[a];
                 sell_w[a] = sell_w[b];
                 sell_w[b] = x;
@@ -377,13 +449,23 @@ cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_
                         const int32_t *labels,
                         const int32_t *perm, const int32_t *iperm, const int64_t *slice_off,
                         int32_t *sell_col, float *sell_w, __nv_bfloat16 *sell_wb, float *self, float *dsq,
-                        uint32_t *rowinfo, uint32_t *status, cudaStream_t st) {
+                        uint32_t *rowinfo, uint32_t *rowcls, uint32_t *status, cudaStream_t st) {
     (void)n;
     (void)K;
     count_launches(1);
     pack_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, isd, mask, labels, perm,
                                                      iperm, slice_off, sell_col, sell_w, sell_wb, self, dsq,
-                                                     rowinfo, status);
+                                                     rowinfo, rowcls, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compress(int32_t n_slices, const int64_t *slice_off, const uint32_t *rowcls,
+                            const int32_t *sell_col, uint16_t *col16, uint32_t *rowinfo, uint8_t *slice_fmt,
+                            cudaStream_t st) {
+    if (n_slices <= 0) return cudaSuccess;
+    count_launches(1);
+    compress_kernel<<<(n_slices + kFmtGroupSlices - 1) / kFmtGroupSlices, kFmtGroupSlices * 32, 0, st>>>(
+        n_slices, slice_off, rowcls, sell_col, col16, rowinfo, slice_fmt);
     return cudaGetLastError();
 }
 
@@ -399,15 +481,15 @@ cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32
     return cudaGetLastError();
 }
 
-cudaError_t launch_spread(int32_t n_pad, const int64_t *slice_off, const uint32_t *rowinfo, int32_t *sell_col,
-                          uint16_t *lcol, const int64_t *halo_off, const int32_t *halo_idx, float *sell_w,
-                          __nv_bfloat16 *sell_wb, cudaStream_t st) {
+cudaError_t launch_spread(int32_t n_pad, const int64_t *slice_off, const uint32_t *rowinfo, const uint32_t *rowcls,
+                          int32_t *sell_col, uint16_t *lcol, const int64_t *halo_off, const int32_t *halo_idx,
+                          float *sell_w, __nv_bfloat16 *sell_wb, cudaStream_t st) {
     const int32_t n_slices = n_pad / kSliceRows;
     const int64_t threads = (int64_t)n_slices * (kSliceRows / kSpreadLanes);
     if (threads == 0) return cudaSuccess;
     count_launches(1);
-    spread_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n_slices, slice_off, rowinfo, sell_col, lcol,
-                                                                     halo_off, halo_idx, sell_w, sell_wb);
+    spread_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n_slices, slice_off, rowinfo, rowcls, sell_col,
+                                                                     lcol, halo_off, halo_idx, sell_w, sell_wb);
     return cudaGetLastError();
 }
 

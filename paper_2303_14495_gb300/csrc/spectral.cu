@@ -38,7 +38,8 @@ constexpr int kGramSlots = 16;              // Gram products per launch slot
 constexpr int kMaxGrams = 8;                // Gram launches per synchronisation
 
 // Y = L X for n_pad x 4 FP32 blocks (renumbered rows; padding rows stay 0).
-template <bool UN, bool BF16>
+// (FP32 weights, which every problem keeps whatever its precision.)
+template <bool UN>
 __global__ void __launch_bounds__(kBlockThreads)
 spmm4_kernel(const SellView A, const float *__restrict__ x, float *__restrict__ y) {
     const int slice = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
@@ -46,10 +47,8 @@ spmm4_kernel(const SellView A, const float *__restrict__ x, float *__restrict__ 
     const int lane = threadIdx.x & 31;
     const int r = slice * kSliceRows + lane;
     float acc[kM], v[kM];
-    if constexpr (BF16)
-        gather_row_sum<kM, __nv_bfloat16, float>(A, A.slice_off[slice], row_len(A, slice, lane), lane, x, acc);
-    else
-        gather_row_sum<kM, float, float>(A, A.slice_off[slice], row_len(A, slice, lane), lane, x, acc);
+    if (block_fmt16(A, blockIdx.x * kWarpsPerBlock)) row_gather<kM, float, float, true>(A, slice, lane, x, acc);
+    else row_gather<kM, float, float, false>(A, slice, lane, x, acc);
     load_row<kM>(x + (size_t)r * kM, v);
     const float a = UN ? __ldg(A.self + r) : 1.0f;
     float out[kM];
@@ -309,14 +308,8 @@ struct Ctx {
 cudaError_t spmm(Ctx &c, const float *x, float *y) {
     const int blocks = (c.A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
     count_launches(1);
-    const bool bf = c.A.wb != nullptr;
-    if (c.un) {
-        if (bf) spmm4_kernel<true, true><<<blocks, kBlockThreads, 0, c.st>>>(c.A, x, y);
-        else spmm4_kernel<true, false><<<blocks, kBlockThreads, 0, c.st>>>(c.A, x, y);
-    } else {
-        if (bf) spmm4_kernel<false, true><<<blocks, kBlockThreads, 0, c.st>>>(c.A, x, y);
-        else spmm4_kernel<false, false><<<blocks, kBlockThreads, 0, c.st>>>(c.A, x, y);
-    }
+    if (c.un) spmm4_kernel<true><<<blocks, kBlockThreads, 0, c.st>>>(c.A, x, y);
+    else spmm4_kernel<false><<<blocks, kBlockThreads, 0, c.st>>>(c.A, x, y);
     return cudaGetLastError();
 }
 

@@ -4,14 +4,14 @@
 //                linearisation (eq. bt:ut), the fidelity term and, on the last
 //                sweep of an outer step, the simplex projection fused in;
 // energy_kernel  F(u) (eqs. gl:functional:graph, functional:GL) and the
-//                residual ||b^t - T u^{t+1}|| with FP64 accumulation;
+//                residual ||b^t - T u^{t+1}||, summed in two-float and FP64;
 // power kernels  power method for lambda_max(L_s) (Sec. 3.1);
 // labels / permutation kernels for the results.
 //
 // All of them walk the sliced-ELL operator the same way: one warp per 32-row
 // slice, one lane per row, entry j of every lane read as one coalesced warp
-// load of column indices and one of weights (streamed without L1
-// allocation).  Neighbour rows of u come either from global memory through
+// load of column indices (int32 or 16-bit) and one of weights (streamed
+// without L1 allocation).  Neighbour rows of u come either from global memory through
 // L1/L2 (plain form) or, in the tiled form, from shared memory: a block
 // handles a tile of 16 slices and first copies the tile's halo rows (the distinct rows
 // its entries reference) into shared memory, so every gather is a shared
@@ -52,8 +52,8 @@ sweep_kernel(const SellView A, const Coeffs cf, const float *__restrict__ v_src,
              const float *__restrict__ u_t, float *__restrict__ v_dst, int iters) {
     __shared__ int next_slot;
     const int count = kWarpsPerBlock * iters;
-    for_block_slices(blockIdx.x * count, count, A.n_slices, &next_slot, [&](int slice) {
-        fp32_sweep_slice<K, PROJECT, UN>(A, cf, slice, threadIdx.x & 31, v_src, u_t, v_dst);
+    for_block_slices_fmt(A, blockIdx.x * count, count, &next_slot, [&](int slice, auto fmt) {
+        fp32_sweep_slice<K, PROJECT, UN, decltype(fmt)::value>(A, cf, slice, threadIdx.x & 31, v_src, u_t, v_dst);
     });
 }
 
@@ -85,28 +85,24 @@ sweep_tiled_kernel(const SellView A, const TileView T, const Coeffs cf, const fl
 // ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
-// Per-row contributions (FP32 inside a row and a warp, FP64 across warps):
+// Per-row contributions (FP32 inside a row, two-float across a warp's rows,
+// FP64 across warps and blocks):
 //   quad += u_i . (L u)_i  (L_s or L: a_i u_i - sum_j w'_ij u_j),  well += sum_k (u_ik^2 - 1)^2,
 //   fid  += Lambda_i sum_k (u_ik - y_ik)^2,
 //   rr   += ||b_i - (T u)_i||^2 with b from u_prev, bb += ||b_i||^2.
 // b - T u is formed as c (u_prev - u) + eta Lambda (y - u)
 //   - (u_prev^3 - u_prev)/eps - eps (L_s u), which avoids the cancellation
-// of the two large terms c u_prev and c u.
+// of the two large terms c u_prev and c u.  x and xp are the row's own u and
+// u_prev (xp unused without u_prev).
 template <int K>
-__device__ __forceinline__ void energy_row(const SellView &A, const Coeffs &cf, int slice, int lane,
-                                           const float (&acc)[K], const float *__restrict__ u,
-                                           const float *__restrict__ u_prev, float (&red)[6]) {
-    const int r = slice * kSliceRows + lane;
+__device__ __forceinline__ void energy_row(const SellView &A, const Coeffs &cf, int r, uint32_t info,
+                                           const float (&acc)[K], const float (&x)[K], const float (&xp)[K],
+                                           bool has_prev, float (&red)[6]) {
     if (r >= A.n) return;
-    const uint32_t info = A.rowinfo[r];
     const float a = A.self ? A.self[r] : 1.0f;
-    float x[K];
-    load_row<K>(u + (size_t)r * K, x);
     const uint32_t tag = info & 0xFFu;
     const bool lab = tag != kTagUnlabelled;
     float q = 0.f, wl = 0.f, fd = 0.f, rr = 0.f, bb = 0.f, nf = 0.f;
-    float xp[K];
-    if (u_prev) load_row<K>(u_prev + (size_t)r * K, xp);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const float ls = a * x[k] - acc[k];
@@ -116,7 +112,7 @@ __device__ __forceinline__ void energy_row(const SellView &A, const Coeffs &cf, 
         const float y = lab ? prior_of<K>(tag, k) : 0.0f;
         if (lab) fd = fmaf(x[k] - y, x[k] - y, fd);
         if (!isfinite(x[k])) nf += 1.0f;
-        if (u_prev) {
+        if (has_prev) {
             const float up = xp[k];
             const float grad_w = (up * up * up - up) * cf.inv_eps;
             const float b = (lab ? cf.eta * y : 0.0f) + cf.c * up - grad_w;
@@ -128,7 +124,10 @@ __device__ __forceinline__ void energy_row(const SellView &A, const Coeffs &cf, 
     red[0] += q; red[1] += wl; red[2] += fd; red[3] += rr; red[4] += bb; red[5] += nf;
 }
 
-template <int K, class WT>
+// FP32 weights in both precisions (the mixed forms keep an FP32 copy of the
+// operator for their residual passes), so F does not depend on the precision
+// of the sweeps beyond the iterate itself.
+template <int K>
 __global__ void __launch_bounds__(kBlockThreads)
 energy_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u,
               const float *__restrict__ u_prev, double *__restrict__ partials, int iters) {
@@ -140,22 +139,23 @@ energy_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u,
     const int first = blockIdx.x * count;
     const int lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < count * 6; i += blockDim.x) slot_sum[i / 6][i % 6] = 0.0;
-    for_block_slices(first, count, A.n_slices, &next_slot, [&](int slice) {
-        float acc[K];
-        if constexpr (std::is_same<WT, float>::value) {
-            // the sweeps' pipelined slice body (same summation order)
-            SliceRow<K, int4> sr;
-            slice_prologue<K>(A, reinterpret_cast<const int4 *>(A.col), slice, lane, u, u, sr);
-            slice_gather<K, kGlobal>(sr, u, nullptr, nullptr, acc);
-        } else {
-            gather_row_sum<K, WT, float>(A, A.slice_off[slice], row_len(A, slice, lane), lane, u, acc);
-        }
+    for_block_slices_fmt(A, first, count, &next_slot, [&](int slice, auto fmt) {
+        constexpr bool C16 = decltype(fmt)::value;
         float red[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        energy_row<K>(A, cf, slice, lane, acc, u, u_prev, red);
+        const int r = slice * kSliceRows + lane;
+        const uint32_t info = ld_stream(A.rowinfo + r);
+        EntryStream<C16, float> s;
+        stream_open(A, slice, lane, s);
+        float x[K], xp[K];
+        load_row<K>(u + (size_t)r * K, x);
+        if (u_prev) load_own_row<K>(u_prev + (size_t)r * K, xp);
+        float acc[K];
+        stream_gather<K, C16, float, float>(s, info, r, u, acc);
+        energy_row<K>(A, cf, r, info, acc, x, xp, u_prev != nullptr, red);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            const float t = warp_sum_f(red[k]);
-            if (lane == 0) slot_sum[slice - first][k] = (double)t;
+            const double t = warp_sum_df(red[k]);
+            if (lane == 0) slot_sum[slice - first][k] = t;
         }
     });
     __syncthreads();
@@ -185,7 +185,11 @@ energy_tiled_kernel(const SellView A, const TileView T, const Coeffs cf, const f
         const int64_t base = A.slice_off[slice];
         float acc[K];
         tile_row_sum<K>(T, A, base, row_len(A, slice, lane), lane, staged, T.halo_idx + h0, hs, u, acc);
-        energy_row<K>(A, cf, slice, lane, acc, u, u_prev, red);
+        const int r = slice * kSliceRows + lane;
+        float x[K], xp[K];
+        load_row<K>(u + (size_t)r * K, x);
+        if (u_prev) load_row<K>(u_prev + (size_t)r * K, xp);
+        energy_row<K>(A, cf, r, A.rowinfo[r], acc, x, xp, u_prev != nullptr, red);
     }
     block_sum_store<6, kTileThreads / 32>(red, partials + (size_t)blockIdx.x * kRedSlots);
 }
@@ -307,7 +311,6 @@ __device__ __forceinline__ void power_row(const SellView &A, int slice, int lane
 // shared queue; each slice's three sums land in a slot of their own, and the
 // block adds its slots in slot order, so the partial (and the estimate) does
 // not depend on which warp took which slice.
-template <class WT>
 __global__ void __launch_bounds__(kBlockThreads)
 power_spmv_kernel(const SellView A, const float *__restrict__ x, double *scale, float *__restrict__ y,
                   double *__restrict__ partials, unsigned *ticket, double *lambda, int iters) {
@@ -319,22 +322,15 @@ power_spmv_kernel(const SellView A, const float *__restrict__ x, double *scale, 
     for (int i = threadIdx.x; i < count * 3; i += blockDim.x) slot_sum[i / 3][i % 3] = 0.0;
     const float s = (float)__ldcg(scale);
     // (the queue's opening barrier orders the zeroing before any slot store)
-    for_block_slices(first, count, A.n_slices, &next_slot, [&](int slice) {
+    for_block_slices_fmt(A, first, count, &next_slot, [&](int slice, auto fmt) {
         float acc[1];
-        if constexpr (std::is_same<WT, float>::value) {
-            // the sweeps' pipelined slice body (same summation order)
-            SliceRow<1, int4> sr;
-            slice_prologue<1>(A, reinterpret_cast<const int4 *>(A.col), slice, lane, x, x, sr);
-            slice_gather<1, kGlobal>(sr, x, nullptr, nullptr, acc);
-        } else {
-            gather_row_sum<1, WT, float>(A, A.slice_off[slice], row_len(A, slice, lane), lane, x, acc);
-        }
+        row_gather<1, float, float, decltype(fmt)::value>(A, slice, lane, x, acc);
         float red[3] = {0.f, 0.f, 0.f};
         power_row(A, slice, lane, acc[0], s, x, y, red);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float t = warp_sum_f(red[k]);
-            if (lane == 0) slot_sum[slice - first][k] = (double)t;
+            const double t = warp_sum_df(red[k]);
+            if (lane == 0) slot_sum[slice - first][k] = t;
         }
     });
     __syncthreads();
@@ -464,12 +460,7 @@ cudaError_t energy_k(const SellView &A, const TileView *T, const Coeffs &cf, con
         energy_tiled_kernel<K><<<T->n_tiles, kTileThreads, sm, st>>>(A, *T, cf, u, u_prev, partials);
     } else {
         const int iters = sweep_iters(A.n_slices);
-        if (A.wb)
-            energy_kernel<K, __nv_bfloat16><<<queue_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, cf, u, u_prev,
-                                                                                                 partials, iters);
-        else
-            energy_kernel<K, float><<<queue_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, cf, u, u_prev, partials,
-                                                                                        iters);
+        energy_kernel<K><<<queue_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, cf, u, u_prev, partials, iters);
     }
     return cudaGetLastError();
 }
@@ -548,12 +539,7 @@ cudaError_t launch_power_spmv(const SellView &A, const TileView *T, const float 
     } else {
         const int iters = sweep_iters(A.n_slices);
         const int blocks = queue_blocks(A.n_slices);
-        if (A.wb)
-            power_spmv_kernel<__nv_bfloat16><<<blocks, kBlockThreads, 0, st>>>(A, x, scale, y, partials, ticket,
-                                                                               lambda, iters);
-        else
-            power_spmv_kernel<float><<<blocks, kBlockThreads, 0, st>>>(A, x, scale, y, partials, ticket, lambda,
-                                                                       iters);
+        power_spmv_kernel<<<blocks, kBlockThreads, 0, st>>>(A, x, scale, y, partials, ticket, lambda, iters);
     }
     return cudaGetLastError();
 }
