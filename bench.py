@@ -251,6 +251,57 @@ def oracle_sample(wl, omp, sweeps):
     return dt, nb, oracle.num_threads(omp)
 
 
+def small_configs(args, dev):
+    """The three small configurations (two moons, 256^2 ellipses, the
+    70 000-point mixture): full solves on the GPU (median of 20 CUDA-event
+    timings after 3 warm-ups, direct launches and CUDA-graph replay) beside
+    the FP64 oracle's full solve, single thread and all cores."""
+    import torch
+    import oracle
+    from gen import make_workload
+    from paper_2303_14495_gb300 import binding as B
+    out = {}
+    for name in ("moons2k", "ellipses256", "gmm70k"):
+        wl = make_workload(name)
+        p = wl.params
+        lam = 0.0
+        if p["precond"] == 2:
+            lam = oracle.safe_lambda(oracle.Problem(wl.row_ptr, wl.col, wl.w, 1, wl.fid_mask, wl.fid_labels,
+                                                    p["eps"], p["eta"], p["c"], omp=True).power_max_eig(150))
+        prm = B.params_from_workload(p, lambda_max=lam)
+        stream = torch.cuda.Stream(device=dev)
+        g = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm, device=dev, stream=stream)
+        res = {"n": wl.n, "nnz": wl.nnz, "K": wl.K, "outer": p["outer"], "inner": p["inner"]}
+        for mode in ("direct", "graph"):
+            g.graphs(mode == "graph")
+            times = []
+            with torch.cuda.stream(stream):
+                for it in range(23):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    g.set_u(None)
+                    e0.record(stream)
+                    g.solve(p["outer"], p["inner"])
+                    e1.record(stream)
+                    e1.synchronize()
+                    if it >= 3:
+                        times.append(e0.elapsed_time(e1))
+            res[f"gpu_ms_per_solve_{mode}"] = statistics.median(times)
+        g.graphs(False)
+        del g
+        sweeps = p["outer"] * p["inner"]
+        for omp in (False, True):
+            P = oracle.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, p["eps"], p["eta"],
+                               p["c"], precond=p["precond"], damping=p["damping"] or 0.5, lambda_max=lam, omp=omp)
+            t0 = time.perf_counter()
+            P.solve(p["outer"], p["inner"], P.init_u())
+            dt = time.perf_counter() - t0
+            key = "cpu_allcores" if omp else "cpu_1thread"
+            res[key] = {"ms_per_solve": 1e3 * dt, "ms_per_sweep": 1e3 * dt / sweeps, "cores": oracle.num_threads(omp)}
+        out[name] = res
+    return out
+
+
 # ---------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------
@@ -529,6 +580,11 @@ def run_ours(args, wl, world, rank, local):
             dt2, nb2, thr2 = oracle_sample(wl, True, 2)
             cpu["allcores"] = {"value": nb2 / dt2 / 1e9, "cores": thr2,
                                "sample": f"same work, OpenMP over rows, {dt2:.1f} s"}
+        # per-sweep times of the sample above, and the small configurations
+        cpu["voronoi2048_ms_per_sweep"] = {"1thread": 1e3 * dt / 2}
+        if not args.no_cpu_allcores:
+            cpu["voronoi2048_ms_per_sweep"]["allcores"] = 1e3 * dt2 / 2
+        cpu["small_configs"] = small_configs(args, dev)
 
     serve = None
     if rank == 0 and not args.no_serving:

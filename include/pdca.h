@@ -182,6 +182,15 @@ typedef struct {
     double step_k;       /* step size k > 0 of the DCA with step size, or 0 for the
                             infinite step size (Prop. nopre, the default)            */
     int32_t columns;     /* PDCA_COLUMNS_AUTO (default) / PDCA_COLUMNS_32             */
+    int32_t row_split;   /* split length T (plain kernels): a row longer than T keeps
+                            its first T entries in the sliced ELL and the rest in an
+                            overflow CSR that a pre-pass reduces one warp per row, so
+                            a hub row does not hold up its sweep.  0 = automatic
+                            (split only if some row is longer than max(256, t), at
+                            t = max(64, nnz / 200000)); otherwise T rounded up to a
+                            multiple of 4, at most 2044.  Rows longer than 2044 are
+                            always split.  Arithmetic: the row's overflow sum is
+                            added after its sliced entries                          */
 } pdca_params;
 
 typedef struct pdca_problem pdca_problem;
@@ -282,12 +291,13 @@ pdca_status pdca_lambda_max(pdca_problem *h, double *lambda_used, double *lambda
 
 /* Layout facts of a created problem: padded sliced-ELL entries, number of
  * 32-row slices, degree-sort window, whether the tiled kernels run, the total
- * and the largest number of halo rows over tiles (0 if not tiled), and the
- * number of slices stored with 16-bit columns (PDCA_COLUMNS_AUTO).  Any
+ * and the largest number of halo rows over tiles (0 if not tiled), the
+ * number of slices stored with 16-bit columns (PDCA_COLUMNS_AUTO), the split
+ * length in use (0 if tiled) and the number of rows longer than it.  Any
  * pointer may be NULL. */
 pdca_status pdca_layout(pdca_problem *h, int64_t *sell_entries, int64_t *n_slices,
                         int32_t *sort_window, int32_t *tiled, int64_t *halo_rows, int32_t *max_halo,
-                        int64_t *slices16);
+                        int64_t *slices16, int32_t *split_len, int64_t *split_rows);
 
 /* CUDA graph replay of pdca_solve: with on = 1, a call without traces (and
  * with profiling off, a plain non-tiled handle and a non-default stream) is

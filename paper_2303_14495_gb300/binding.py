@@ -67,6 +67,7 @@ class pdca_params(C.Structure):
         ("power_iters", C.c_int32), ("precision", C.c_int32),
         ("sort_window", C.c_int32), ("reorder", C.c_int32), ("tiling", C.c_int32),
         ("entry_order", C.c_int32), ("step_k", C.c_double), ("columns", C.c_int32),
+        ("row_split", C.c_int32),
     ]
 
 
@@ -97,7 +98,8 @@ def lib():
                 "pdca_labels": (C.c_int, [vp, vp]),
                 "pdca_lambda_max": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(dbl)]),
                 "pdca_layout": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32),
-                                          C.POINTER(i32), C.POINTER(i64), C.POINTER(i32), C.POINTER(i64)]),
+                                          C.POINTER(i32), C.POINTER(i64), C.POINTER(i32), C.POINTER(i64),
+                                          C.POINTER(i32), C.POINTER(i64)]),
                 "pdca_profile_enable": (C.c_int, [vp, i32]),
                 "pdca_profile_read": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i64)]),
                 "pdca_kernel_launches": (u64, []),
@@ -154,7 +156,7 @@ def make_params(eps=1.0, c=3.0, eta=1.0, precond=PDCA_JACOBI_PERTURBED, damping=
                 lambda_max=0.0, power_iters=150, laplacian=PDCA_LAP_NORMALIZED,
                 precision=PDCA_FP32, sort_window=0, reorder=PDCA_REORDER_BFS,
                 tiling=PDCA_TILING_AUTO, step_k=0.0, entry_order=PDCA_ENTRIES_SPREAD,
-                columns=PDCA_COLUMNS_AUTO) -> pdca_params:
+                columns=PDCA_COLUMNS_AUTO, row_split=0) -> pdca_params:
     p = pdca_params()
     lib().pdca_default_params(C.byref(p))
     p.eps, p.c, p.eta = float(eps), float(c), float(eta)
@@ -164,6 +166,7 @@ def make_params(eps=1.0, c=3.0, eta=1.0, precond=PDCA_JACOBI_PERTURBED, damping=
     p.reorder, p.tiling, p.step_k = int(reorder), int(tiling), float(step_k)
     p.entry_order = int(entry_order)
     p.columns = int(columns)
+    p.row_split = int(row_split)
     return p
 
 
@@ -235,10 +238,12 @@ def pdca_lambda_max(h):
 def pdca_layout(h):
     e, s, w = C.c_int64(0), C.c_int64(0), C.c_int32(0)
     t, hr, mh, s16 = C.c_int32(0), C.c_int64(0), C.c_int32(0), C.c_int64(0)
+    sl, sr = C.c_int32(0), C.c_int64(0)
     st = lib().pdca_layout(h, C.byref(e), C.byref(s), C.byref(w), C.byref(t), C.byref(hr), C.byref(mh),
-                           C.byref(s16))
+                           C.byref(s16), C.byref(sl), C.byref(sr))
     return st, dict(sell_entries=e.value, n_slices=s.value, sort_window=w.value, tiled=bool(t.value),
-                    halo_rows=hr.value, max_halo=mh.value, slices16=s16.value)
+                    halo_rows=hr.value, max_halo=mh.value, slices16=s16.value, split_len=sl.value,
+                    split_rows=sr.value)
 
 
 def pdca_profile_enable(h, on: bool) -> int:

@@ -258,8 +258,19 @@ __device__ __forceinline__ float4 wgroup(const typename WFmt<WT>::G &g) {
     }
 }
 
-__device__ __forceinline__ int info_len(uint32_t info, bool c16) {
-    return c16 ? (int)((info >> 8) & kLen16Max) : (int)(info >> 8);
+// the row's entries in the sliced ELL (plain kernels, either format)
+__device__ __forceinline__ int info_len(uint32_t info, bool) { return (int)((info >> 8) & kLenMask); }
+
+// A row longer than the split length continues in the overflow CSR: add the
+// pre-pass's sum of its remaining entries (after the sliced entries, so the
+// order of the additions is fixed).
+template <int K>
+__device__ __forceinline__ void add_overflow(const SellView &A, int r, uint32_t info, float (&acc)[K]) {
+    if (info & kOvFlag) {
+        const float *p = A.ov_acc + (size_t)__ldg(A.ov_index + r) * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] += __ldg(p + k);
+    }
 }
 
 // Bands of a row with 16-bit columns: entries j < np lie in the previous
@@ -336,7 +347,7 @@ __device__ __forceinline__ void fma_entry_group(float (&acc)[K], const CG &c, co
 // The gather proper: while a lane works on two entry groups the next two are
 // in flight; products are added in entry order.
 template <int K, bool C16, class WT, class XT>
-__device__ __forceinline__ void stream_gather(EntryStream<C16, WT> &s, uint32_t info, int r,
+__device__ __forceinline__ void stream_gather(const SellView &A, EntryStream<C16, WT> &s, uint32_t info, int r,
                                               const XT *__restrict__ x, float (&acc)[K]) {
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0f;
@@ -360,6 +371,7 @@ __device__ __forceinline__ void stream_gather(EntryStream<C16, WT> &s, uint32_t 
         s.c1 = n1;
         s.w1 = nw1;
     }
+    add_overflow<K>(A, r, info, acc);
 }
 
 // The gather without look-ahead: each step loads two entry groups, then
@@ -403,6 +415,7 @@ __device__ __forceinline__ void short_gather(const SellView &A, int slice, int l
         const float4 wa = wgroup<WT>(ld_stream(wp + 32 * g));
         fma_entry_group<K, XT>(acc, ca, wa, g, b, x);
     }
+    add_overflow<K>(A, r, info, acc);
 }
 
 // Column format of the slices one block handles.  The format is decided per
@@ -422,7 +435,7 @@ __device__ __forceinline__ uint32_t row_gather(const SellView &A, int slice, int
     const uint32_t info = ld_stream(A.rowinfo + r);
     EntryStream<C16, WT> s;
     stream_open(A, slice, lane, s);
-    stream_gather<K, C16, WT, XT>(s, info, r, x, acc);
+    stream_gather<K, C16, WT, XT>(A, s, info, r, x, acc);
     return info;
 }
 
@@ -612,6 +625,52 @@ __device__ __forceinline__ double warp_sum_df(float v) {
         df_add(hi, lo, bhi, blo);
     }
     return (double)hi + (double)lo;
+}
+
+// Sums of eight per-lane values over the warp's 32 lanes in two-float
+// arithmetic, with 9 shuffle pairs instead of 40: at each of the first three
+// levels a lane keeps half of its values and sends the other half to its
+// partner (lane ^ 16, ^ 8, ^ 4), the last two levels add whole values.  The
+// pattern is fixed, so the result is too.  On return lane l holds the total
+// of value q(l) = 4 [l & 16] + 2 [l & 8] + [l & 4] (four lanes per value).
+__device__ __forceinline__ double warp_sum8_df(const float (&v)[8]) {
+    const int lane = threadIdx.x & 31;
+    float hi[4], lo[4];
+    {
+        const bool up = (lane & 16) != 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float keep = up ? v[i + 4] : v[i], send = up ? v[i] : v[i + 4];
+            hi[i] = keep;
+            lo[i] = 0.0f;
+            df_add(hi[i], lo[i], __shfl_xor_sync(kFull, send, 16), 0.0f);
+        }
+    }
+    {
+        const bool up = (lane & 8) != 0;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            float khi = up ? hi[i + 2] : hi[i], klo = up ? lo[i + 2] : lo[i];
+            const float shi = up ? hi[i] : hi[i + 2], slo = up ? lo[i] : lo[i + 2];
+            df_add(khi, klo, __shfl_xor_sync(kFull, shi, 8), __shfl_xor_sync(kFull, slo, 8));
+            hi[i] = khi;
+            lo[i] = klo;
+        }
+    }
+    {
+        const bool up = (lane & 4) != 0;
+        float khi = up ? hi[1] : hi[0], klo = up ? lo[1] : lo[0];
+        const float shi = up ? hi[0] : hi[1], slo = up ? lo[0] : lo[1];
+        df_add(khi, klo, __shfl_xor_sync(kFull, shi, 4), __shfl_xor_sync(kFull, slo, 4));
+        hi[0] = khi;
+        lo[0] = klo;
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1) {
+        const float bhi = __shfl_xor_sync(kFull, hi[0], o), blo = __shfl_xor_sync(kFull, lo[0], o);
+        df_add(hi[0], lo[0], bhi, blo);
+    }
+    return (double)hi[0] + (double)lo[0];
 }
 
 // Sum S values over the block (WARPS warps) in a fixed order and store them
@@ -851,7 +910,7 @@ __device__ __forceinline__ void fp32_sweep_slice(const SellView &A, const Coeffs
         load_own_row<K>(u_t + (size_t)r * K, u);
     }
     float acc[K];
-    stream_gather<K, C16, float, float>(s, info, r, v_src, acc);
+    stream_gather<K, C16, float, float>(A, s, info, r, v_src, acc);
     sweep_update<K, PROJECT, UN>(cf, info, a, acc, v, u, v_dst + (size_t)r * K, A.stream_rows != 0);
 }
 

@@ -40,12 +40,16 @@ struct Layout {
     int32_t n = 0, K = 0, n_pad = 0, n_slices = 0, sigma = 0, n_tiles = 0;
     bool host_order = false;           // renumbering computed on the host (BFS blocks)
     int64_t nnz = 0, sell_entries = 0, sell_cap = 0, halo_cap = 0;
+    int32_t split = 0;                 // split length T (rows longer than T use the overflow CSR)
+    int32_t n_ov = 0;                  // rows longer than T
+    int64_t ov_entries = 0;            // their entries past T
     std::vector<int64_t> slice_off;    // n_slices + 1 (exact; filled at create for host order)
     size_t o_col, o_col16, o_fmt, o_w, o_wb, o_slice, o_rowinfo, o_perm, o_iperm, o_self, o_dsq, o_u[3], o_part,
         o_red, o_scal, o_trace;
     size_t o_hoff, o_hidx;
+    size_t o_ovrp, o_ovcol, o_ovw, o_ovwb, o_ovidx, o_ovacc;   // overflow CSR and its pre-pass sums
     size_t o_mr, o_me[2];              // mixed precision: r (FP32) and the two corrections (16-bit)
-    size_t o_srp, o_scol, o_sw, o_sdeg, o_sisd, o_smask, o_slab, o_scls, o_status;
+    size_t o_srp, o_scol, o_sw, o_sdeg, o_sisd, o_smask, o_slab, o_scls, o_spow, o_status;
     size_t persistent = 0, total = 0;
 };
 
@@ -87,23 +91,24 @@ int64_t sell_bound(const int64_t *rp, int32_t n, int32_t sigma, int64_t max_deg)
 
 // Slice widths for one sort window: the degrees of the window sorted
 // descending; a slice's width is the degree at its first position.
-void window_widths(const int64_t *rp, int64_t base, int64_t end, std::vector<int32_t> &scratch,
+void window_widths(const int64_t *rp, int64_t base, int64_t end, int32_t split, std::vector<int32_t> &scratch,
                    std::vector<int64_t> &widths) {
     scratch.resize((size_t)(end - base));
-    for (int64_t i = base; i < end; ++i) scratch[(size_t)(i - base)] = (int32_t)(rp[i + 1] - rp[i]);
+    for (int64_t i = base; i < end; ++i)
+        scratch[(size_t)(i - base)] = (int32_t)std::min<int64_t>(rp[i + 1] - rp[i], split);
     std::sort(scratch.begin(), scratch.end(), std::greater<int32_t>());
     for (int64_t p = 0; p < end - base; p += kSliceRows)
         widths[(size_t)((base + p) / kSliceRows)] = (scratch[(size_t)p] + kVec - 1) / kVec * kVec;
 }
 
-int64_t sell_entries_for(const int64_t *rp, int32_t n, int32_t sigma, std::vector<int64_t> &widths) {
+int64_t sell_entries_for(const int64_t *rp, int32_t n, int32_t sigma, int32_t split, std::vector<int64_t> &widths) {
     const int32_t n_slices = (n + kSliceRows - 1) / kSliceRows;
     widths.assign((size_t)n_slices, 0);
     const int64_t nwin = ((int64_t)n + sigma - 1) / sigma;
     host_parallel_for(nwin, [&](int64_t wdx) {
         std::vector<int32_t> scratch;
         const int64_t base = wdx * sigma;
-        window_widths(rp, base, std::min<int64_t>(n, base + sigma), scratch, widths);
+        window_widths(rp, base, std::min<int64_t>(n, base + sigma), split, scratch, widths);
     });
     int64_t tot = 0;
     for (int64_t w : widths) tot += w * kSliceRows;
@@ -133,6 +138,7 @@ pdca_status check_params(const pdca_params &p) {
     if (p.tiling == PDCA_TILING_ON && p.reorder != PDCA_REORDER_BFS) return PDCA_ERR_INVALID_ARG;
     if (p.entry_order != PDCA_ENTRIES_SPREAD && p.entry_order != PDCA_ENTRIES_CSR) return PDCA_ERR_INVALID_ARG;
     if (p.columns != PDCA_COLUMNS_AUTO && p.columns != PDCA_COLUMNS_32) return PDCA_ERR_INVALID_ARG;
+    if (p.row_split < 0) return PDCA_ERR_INVALID_ARG;
     return PDCA_OK;
 }
 
@@ -237,6 +243,21 @@ pdca_status host_row_ptr(const int64_t *row_ptr, int32_t n, std::vector<int64_t>
     return PDCA_OK;
 }
 
+// Split length T: a row longer than T keeps its first T entries in the
+// sliced ELL and the rest in the overflow CSR, reduced one warp per row by a
+// pre-pass.  A sweep waits for its longest row (one lane per row), so hub
+// rows set its time on graphs whose rows are otherwise short.  Automatic
+// choice: split only when some row is longer than max(256, t), with
+// t = max(64, nnz / 200000) -- a row that a sweep over the whole graph
+// would not hide -- and then at t.  Tiled kernels keep whole rows.
+int32_t split_length(const pdca_params &p, int64_t nnz, int64_t max_deg) {
+    if (p.tiling == PDCA_TILING_ON) return INT32_MAX;
+    if (p.row_split > 0) return std::min<int32_t>(kSplitMax, (p.row_split + kVec - 1) / kVec * kVec);
+    const int64_t t = std::max<int64_t>(64, (nnz / 200000 + kVec - 1) / kVec * kVec);
+    if (max_deg > std::max<int64_t>(256, t)) return (int32_t)std::min<int64_t>(t, kSplitMax);
+    return kSplitMax;
+}
+
 pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_params &prm, int64_t max_deg,
                            Layout &L) {
     const int32_t sigma_req = prm.sort_window;
@@ -246,6 +267,24 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     L.n_slices = (n + kSliceRows - 1) / kSliceRows;
     L.n_pad = L.n_slices * kSliceRows;
     L.n_tiles = (L.n_slices + kTileSlices - 1) / kTileSlices;
+    L.split = split_length(prm, L.nnz, max_deg);
+    if (max_deg > L.split) {
+        const int64_t chunk = 1 << 18, nch = ((int64_t)n + chunk - 1) / chunk;
+        std::vector<int64_t> cnt((size_t)nch, 0), ent((size_t)nch, 0);
+        host_parallel_for(nch, [&](int64_t c) {
+            for (int64_t i = c * chunk; i < std::min<int64_t>(n, (c + 1) * chunk); ++i) {
+                const int64_t d = rp[i + 1] - rp[i];
+                if (d > L.split) {
+                    ++cnt[(size_t)c];
+                    ent[(size_t)c] += d - L.split;
+                }
+            }
+        });
+        for (int64_t c = 0; c < nch; ++c) {
+            L.n_ov += (int32_t)cnt[(size_t)c];
+            L.ov_entries += ent[(size_t)c];
+        }
+    }
     std::vector<int64_t> widths;
     if (prm.reorder == PDCA_REORDER_BFS) {
         // the widths depend on the renumbering (computed at create); size for the bound
@@ -256,12 +295,12 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
         L.halo_cap = std::max<int64_t>(L.nnz, 1);
     } else if (sigma_req) {
         L.sigma = sigma_req;
-        L.sell_entries = sell_entries_for(rp, n, L.sigma, widths);
+        L.sell_entries = sell_entries_for(rp, n, L.sigma, L.split, widths);
     } else {
         // smallest window (from 128 rows up) whose slice padding is <= 10%
         for (int s = 128;; s <<= 1) {
             L.sigma = s;
-            L.sell_entries = sell_entries_for(rp, n, s, widths);
+            L.sell_entries = sell_entries_for(rp, n, s, L.split, widths);
             if (s >= 8192 || (double)L.sell_entries <= kPadTarget * (double)std::max<int64_t>(L.nnz, 1)) break;
         }
     }
@@ -295,6 +334,13 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     L.o_trace = take(8 * 2 * (size_t)kTraceCap);
     L.o_hoff = take(8 * ((size_t)L.n_tiles + 1));
     L.o_hidx = take(4 * (size_t)L.halo_cap);
+    const size_t nov = (size_t)L.n_ov, eov = (size_t)L.ov_entries;
+    L.o_ovrp = take(nov ? 8 * (nov + 1) : 0);
+    L.o_ovcol = take(4 * eov);
+    L.o_ovw = take(4 * eov);
+    L.o_ovwb = take(mixed ? 2 * eov : 0);
+    L.o_ovidx = take(nov ? 4 * np : 0);
+    L.o_ovacc = take(4 * nov * (size_t)std::max(K, 4));
     const size_t half_rows = mixed ? 2 * np * (size_t)K : 0;
     L.o_mr = take(mixed ? 4 * np * (size_t)K : 0);
     L.o_me[0] = take(half_rows);
@@ -309,6 +355,8 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     L.o_smask = take(nn);
     L.o_slab = take(4 * nn);
     L.o_scls = take(4 * np);
+    // the power method on the CSR input (Richardson without a given lambda_max)
+    L.o_spow = take(prm.precond == PDCA_RICHARDSON && prm.lambda_max <= 0.0 ? power_csr_scratch_bytes(n) : 0);
     L.o_status = take(16);
     L.total = o;
     return PDCA_OK;
@@ -337,6 +385,9 @@ struct pdca_problem {
     int64_t slices16 = 0;             // slices stored with 16-bit columns
     float *sell_w = nullptr;          // FP32 weights (both precisions)
     __nv_bfloat16 *sell_wb = nullptr; // BF16 weights (mixed precision)
+    OverflowView ov{};                // entries of the rows longer than the split length
+    int32_t *ov_index = nullptr;      // overflow row of every split row (n_pad), or nullptr
+    float *ov_acc = nullptr;          // the pre-pass sums (max(K, 4) floats per overflow row)
     int64_t *slice_off = nullptr;
     uint32_t *rowinfo = nullptr;
     int32_t *perm = nullptr, *iperm = nullptr;
@@ -382,6 +433,8 @@ struct pdca_problem {
         A.slice_off = slice_off;
         A.rowinfo = rowinfo;
         A.self = self;
+        A.ov_index = ov_index;
+        A.ov_acc = ov_acc;
         A.n_slices = L.n_slices;
         A.n = L.n;
         // three n_pad x K FP32 iterates above half of the 129 MB L2
@@ -422,8 +475,19 @@ pdca_status timed_pass(pdca_problem *h, F launch) {
     return PDCA_OK;
 }
 
+// The overflow pre-pass of the row sums over x (K columns; weights and row
+// storage as given) into the handle's ov_acc; nothing without split rows.
+cudaError_t overflow_pass(pdca_problem *h, int K, int wkind, int xkind, const void *x) {
+    if (h->ov.n_rows <= 0) return cudaSuccess;
+    return launch_overflow(K, wkind, xkind, h->ov, x, h->ov_acc, h->stream);
+}
+
 pdca_status sweep(pdca_problem *h, bool project, const float *src, const float *ut, float *dst) {
-    return timed_pass(h, [&] { return launch_sweep(h->L.K, project, h->view(), h->tiles(), h->cf, src, ut, dst, h->stream); });
+    return timed_pass(h, [&] {
+        cudaError_t e = overflow_pass(h, h->L.K, kOvW32, kOvX32, src);
+        if (e != cudaSuccess) return e;
+        return launch_sweep(h->L.K, project, h->view(), h->tiles(), h->cf, src, ut, dst, h->stream);
+    });
 }
 
 // Mixed-precision outer step: pass 0 forms r = b^t - T u^t and e^1 in FP32,
@@ -436,7 +500,10 @@ pdca_status outer_step_mixed(pdca_problem *h, int32_t inner) {
     const float *u = h->U[h->cur];
     float *u_out = h->U[dst];
     const bool proj = K >= 2;
+    const int xkind = h->bf16u ? kOvXBf16 : kOvXHalf;
     pdca_status st = timed_pass(h, [&] {
+        cudaError_t e = overflow_pass(h, K, kOvW32, kOvX32, u);
+        if (e != cudaSuccess) return e;
         return launch_mixed_residual(K, h->bf16u, inner == 1, proj, A, h->cf, u, h->mr, h->me[0], u_out, h->stream);
     });
     if (st != PDCA_OK) return st;
@@ -444,6 +511,8 @@ pdca_status outer_step_mixed(pdca_problem *h, int32_t inner) {
         const bool last = s == inner - 1;
         void *src = h->me[(s - 1) % 2], *dstb = h->me[s % 2];
         st = timed_pass(h, [&] {
+            cudaError_t e = overflow_pass(h, K, kOvW16, xkind, src);
+            if (e != cudaSuccess) return e;
             return launch_mixed_sweep(K, h->bf16u, last, proj, A, h->cf, src, h->mr, dstb, u, u_out, h->stream);
         });
         if (st != PDCA_OK) return st;
@@ -478,6 +547,7 @@ pdca_status outer_step(pdca_problem *h, int32_t inner) {
 
 pdca_status reduce_energy(pdca_problem *h, double *trace_F, double *trace_r) {
     const SellView A = h->view();
+    PDCA_TRY(overflow_pass(h, h->L.K, kOvW32, kOvX32, h->U[h->cur]));
     PDCA_TRY(launch_energy(h->L.K, A, h->tiles(), h->cf, h->U[h->cur], h->has_prev ? h->U[h->prev] : nullptr,
                            h->partials, h->stream));
     PDCA_TRY(launch_energy_finalize(h->partials, reduce_parts(A, h->tiles()), h->prm.eps, h->prm.eta,
@@ -500,6 +570,7 @@ pdca_status power_method(pdca_problem *h) {
     PDCA_TRY(launch_power_finalize(h->partials, energy_blocks(A.n_slices), scale, lam, h->stream));
     for (int it = 0; it <= h->prm.power_iters; ++it) {
         // the SpMV's last block reduces the partials and updates scale / lambda
+        PDCA_TRY(overflow_pass(h, 1, kOvW32, kOvX32, x));
         PDCA_TRY(launch_power_spmv(A, h->tiles(), x, scale, y, h->partials, ticket, lam, h->stream));
         std::swap(x, y);
     }
@@ -542,6 +613,35 @@ struct OrderJob {
     }
 };
 
+// The overflow CSR's row offsets (rows longer than the split length, in new
+// row order) and the overflow row of every such row, uploaded; the pack
+// kernel fills the columns and weights.  perm: new row -> old row (n_pad,
+// -1 on padding).
+pdca_status build_overflow(pdca_problem *h, const int64_t *rp, const int32_t *perm) {
+    Layout &L = h->L;
+    if (L.n_ov == 0) return PDCA_OK;
+    std::vector<int64_t> orp((size_t)L.n_ov + 1, 0);
+    std::vector<int32_t> idx((size_t)L.n_pad, -1);
+    int32_t q = 0;
+    for (int32_t r = 0; r < L.n_pad; ++r) {
+        const int32_t old = perm[r];
+        if (old < 0) continue;
+        const int64_t d = rp[old + 1] - rp[old];
+        if (d <= L.split) continue;
+        if (q >= L.n_ov) return PDCA_ERR_CUDA;   // the counts are a theorem; never expected
+        idx[(size_t)r] = q;
+        orp[(size_t)q + 1] = orp[(size_t)q] + (d - L.split);
+        ++q;
+    }
+    if (q != L.n_ov || orp.back() != L.ov_entries) return PDCA_ERR_CUDA;
+    int64_t *d_rp = reinterpret_cast<int64_t *>(h->ws + L.o_ovrp);
+    PDCA_TRY(cudaMemcpyAsync(d_rp, orp.data(), 8 * orp.size(), cudaMemcpyHostToDevice, h->stream));
+    PDCA_TRY(cudaMemcpyAsync(h->ov_index, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice, h->stream));
+    // the copies read host vectors that go out of scope
+    PDCA_TRY(cudaStreamSynchronize(h->stream));
+    return PDCA_OK;
+}
+
 pdca_status host_renumber(pdca_problem *h, const int64_t *rp, OrderJob &job) {
     Layout &L = h->L;
     const int32_t n = L.n;
@@ -565,7 +665,9 @@ pdca_status host_renumber(pdca_problem *h, const int64_t *rp, OrderJob &job) {
             int64_t wmax = 0;
             for (int32_t l = 0; l < kSliceRows; ++l) {
                 const int32_t r = s * kSliceRows + l;
-                if (r < n) wmax = std::max<int64_t>(wmax, rp[perm[(size_t)r] + 1] - rp[perm[(size_t)r]]);
+                if (r < n)
+                    wmax = std::max<int64_t>(wmax, std::min<int64_t>(rp[perm[(size_t)r] + 1] - rp[perm[(size_t)r]],
+                                                                     L.split));
             }
             width[(size_t)s] = (wmax + kVec - 1) / kVec * kVec;
         }
@@ -615,7 +717,7 @@ pdca_status host_renumber(pdca_problem *h, const int64_t *rp, OrderJob &job) {
     PDCA_TRY(cudaMemcpyAsync(h->perm, perm.data(), 4 * perm.size(), cudaMemcpyHostToDevice, h->stream));
     PDCA_TRY(cudaMemcpyAsync(h->iperm, iperm.data(), 4 * iperm.size(), cudaMemcpyHostToDevice, h->stream));
     PDCA_TRY(cudaStreamSynchronize(h->stream));
-    return PDCA_OK;
+    return build_overflow(h, rp, perm.data());
 }
 
 // ---------------------------------------------------------------------------
@@ -692,7 +794,8 @@ bool member_advance(BatchMember &m) {
 // per-problem state (tags, iterates, reductions, mixed buffers, fidelity
 // staging).
 struct CloneLayout {
-    size_t o_rowinfo, o_u[3], o_part, o_red, o_scal, o_trace, o_mr, o_me[2], o_smask, o_slab, o_status, total;
+    size_t o_rowinfo, o_u[3], o_part, o_red, o_scal, o_trace, o_mr, o_me[2], o_ovacc, o_smask, o_slab, o_status,
+        total;
 };
 
 CloneLayout clone_layout(const Layout &L, int32_t K, int32_t precision) {
@@ -711,6 +814,7 @@ CloneLayout clone_layout(const Layout &L, int32_t K, int32_t precision) {
     C.o_mr = take(precision == PDCA_FP32 ? 0 : 4 * np * (size_t)K);
     C.o_me[0] = take(half_rows);
     C.o_me[1] = take(half_rows);
+    C.o_ovacc = take(4 * (size_t)L.n_ov * (size_t)std::max(K, 4));
     C.o_smask = take(nn);
     C.o_slab = take(4 * nn);
     C.o_status = take(16);
@@ -726,6 +830,7 @@ struct pdca_batch {
     std::vector<BatchMember> members;
     std::vector<pdca_problem *> done;
     BatchTable table;
+    BatchOvTable ov_table;
 };
 
 extern "C" {
@@ -749,6 +854,7 @@ void pdca_default_params(pdca_params *p) {
     p->entry_order = PDCA_ENTRIES_SPREAD;
     p->step_k = 0.0;
     p->columns = PDCA_COLUMNS_AUTO;
+    p->row_split = 0;
 }
 
 const char *pdca_status_string(pdca_status s) {
@@ -838,6 +944,15 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     h->self = prm.laplacian == PDCA_LAP_UNNORMALIZED ? reinterpret_cast<float *>(W + L.o_self) : nullptr;
     h->dsq = prm.laplacian == PDCA_LAP_NORMALIZED ? reinterpret_cast<float *>(W + L.o_dsq) : nullptr;
     for (int b = 0; b < 3; ++b) h->U[b] = reinterpret_cast<float *>(W + L.o_u[b]);
+    if (L.n_ov > 0) {
+        h->ov.rp = reinterpret_cast<const int64_t *>(W + L.o_ovrp);
+        h->ov.col = reinterpret_cast<const int32_t *>(W + L.o_ovcol);
+        h->ov.w = reinterpret_cast<const float *>(W + L.o_ovw);
+        h->ov.wb = prm.precision != PDCA_FP32 ? reinterpret_cast<const __nv_bfloat16 *>(W + L.o_ovwb) : nullptr;
+        h->ov.n_rows = L.n_ov;
+        h->ov_index = reinterpret_cast<int32_t *>(W + L.o_ovidx);
+        h->ov_acc = reinterpret_cast<float *>(W + L.o_ovacc);
+    }
     h->mixed = prm.precision != PDCA_FP32;
     h->bf16u = prm.precision == PDCA_MIXED_BF16W_BF16U;
     h->mr = W + L.o_mr;
@@ -891,12 +1006,27 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
         st = feasible(prm, omega, prm.lambda_max, h->dmax);
         if (st != PDCA_OK) return fail(st);
     }
+    // lambda_max by the power method on the CSR input: queued now, it runs on
+    // the device while the host computes the renumbering
+    const bool power = prm.precond == PDCA_RICHARDSON && prm.lambda_max <= 0.0;
+    if (power && launch_power_csr(n, s_rp, s_col, s_w, s_isd, s_deg, prm.laplacian == PDCA_LAP_UNNORMALIZED,
+                                  prm.power_iters, W + L.o_spow, h->scal, h->scal + 1, sm) != cudaSuccess)
+        return fail(PDCA_ERR_CUDA);
 
     if (L.host_order) {
         st = host_renumber(h, rp, job);
         if (st != PDCA_OK) return fail(st);
-    } else if (launch_window_sort(n, L.n_pad, L.sigma, s_rp, h->perm, h->iperm, sm) != cudaSuccess) {
-        return fail(PDCA_ERR_CUDA);
+    } else {
+        if (launch_window_sort(n, L.n_pad, L.sigma, s_rp, h->perm, h->iperm, sm) != cudaSuccess)
+            return fail(PDCA_ERR_CUDA);
+        if (L.n_ov > 0) {   // the overflow rows follow the device's renumbering
+            std::vector<int32_t> perm_h((size_t)L.n_pad);
+            if (cudaMemcpyAsync(perm_h.data(), h->perm, 4 * perm_h.size(), cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
+                cudaStreamSynchronize(sm) != cudaSuccess)
+                return fail(PDCA_ERR_CUDA);
+            st = build_overflow(h, rp, perm_h.data());
+            if (st != PDCA_OK) return fail(st);
+        }
     }
     if (cp(h->slice_off, L.slice_off.data(), 8 * L.slice_off.size()) != cudaSuccess) return fail(PDCA_ERR_CUDA);
     cudaError_t pe;
@@ -907,11 +1037,14 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     else
         pe = launch_pack(n, L.n_pad, k, s_rp, s_col, s_w, s_deg, s_isd, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
                          h->sell_col, h->sell_w, h->sell_wb, h->self, h->dsq, h->rowinfo,
-                         prm.columns == PDCA_COLUMNS_AUTO ? s_cls : nullptr, s_status, sm);
+                         prm.columns == PDCA_COLUMNS_AUTO ? s_cls : nullptr, L.split, h->ov_index,
+                         h->ov.rp, const_cast<int32_t *>(h->ov.col), const_cast<float *>(h->ov.w),
+                         const_cast<__nv_bfloat16 *>(h->ov.wb), s_status, sm);
     if (pe != cudaSuccess) return fail(PDCA_ERR_CUDA);
     const bool c16 = !h->tiled && prm.columns == PDCA_COLUMNS_AUTO;
     if (prm.entry_order == PDCA_ENTRIES_SPREAD &&
-        launch_spread(L.n_pad, h->slice_off, h->rowinfo, c16 ? s_cls : nullptr, h->tiled ? nullptr : h->sell_col,
+        launch_spread(L.n_pad, h->slice_off, h->rowinfo, h->tiled ? 0xFFFFFFu : kLenMask, c16 ? s_cls : nullptr,
+                      h->tiled ? nullptr : h->sell_col,
                       h->tiled ? const_cast<uint16_t *>(h->tv.lcol) : nullptr, h->tv.halo_off, h->tv.halo_idx,
                       h->sell_w, h->sell_wb, sm) != cudaSuccess)
         return fail(PDCA_ERR_CUDA);
@@ -925,8 +1058,12 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
         if (prm.lambda_max > 0) {
             h->lambda_used = prm.lambda_max;
         } else {
-            st = power_method(h);
-            if (st != PDCA_OK) return fail(st);
+            double lam_h = 0.0;
+            if (cudaMemcpyAsync(&lam_h, h->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
+                cudaStreamSynchronize(sm) != cudaSuccess)
+                return fail(PDCA_ERR_CUDA);
+            h->lambda_est = lam_h;
+            h->lambda_used = std::min(lambda_bound(h), 1.001 * lam_h);
         }
         st = feasible(prm, omega, h->lambda_used, h->dmax);
         if (st != PDCA_OK) return fail(st);
@@ -993,6 +1130,8 @@ pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t 
     h->slices16 = base->slices16;
     h->sell_w = base->sell_w;
     h->sell_wb = base->sell_wb;
+    h->ov = base->ov;
+    h->ov_index = base->ov_index;
     h->slice_off = base->slice_off;
     h->perm = base->perm;
     h->iperm = base->iperm;
@@ -1014,6 +1153,7 @@ pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t 
     h->mr = W + CL.o_mr;
     h->me[0] = W + CL.o_me[0];
     h->me[1] = W + CL.o_me[1];
+    h->ov_acc = base->L.n_ov > 0 ? reinterpret_cast<float *>(W + CL.o_ovacc) : nullptr;
     uint8_t *s_mask = reinterpret_cast<uint8_t *>(W + CL.o_smask);
     int32_t *s_lab = reinterpret_cast<int32_t *>(W + CL.o_slab);
     uint32_t *s_status = reinterpret_cast<uint32_t *>(W + CL.o_status);
@@ -1090,7 +1230,7 @@ pdca_status pdca_spectral_init(pdca_problem *h, void *workspace, size_t ws_bytes
     float *vec = reinterpret_cast<float *>(static_cast<char *>(workspace) + align_up(spectral_workspace_bytes(h->L.n_pad)));
     // the tolerance is relative to the bound of the spectrum
     const double bound = h->self ? 2.0 * h->dmax : 2.0;
-    const pdca_status st = spectral_eigvec(h->view(), h->self != nullptr, h->self ? nullptr : h->dsq, h->perm,
+    const pdca_status st = spectral_eigvec(h->view(), h->ov, h->self != nullptr, h->self ? nullptr : h->dsq, h->perm,
                                            h->L.n, h->L.n_pad, h->stream, workspace, max_iters, tol * bound,
                                            lambda2, vec, iters_done);
     if (st != PDCA_OK && st != PDCA_ERR_NOT_CONVERGED) return st;
@@ -1251,8 +1391,11 @@ pdca_status pdca_lambda_max(pdca_problem *h, double *lambda_used, double *lambda
 }
 
 pdca_status pdca_layout(pdca_problem *h, int64_t *sell_entries, int64_t *n_slices, int32_t *sort_window,
-                        int32_t *tiled, int64_t *halo_rows, int32_t *max_halo, int64_t *slices16) {
+                        int32_t *tiled, int64_t *halo_rows, int32_t *max_halo, int64_t *slices16,
+                        int32_t *split_len, int64_t *split_rows) {
     if (!h) return PDCA_ERR_INVALID_ARG;
+    if (split_len) *split_len = h->tiled ? 0 : h->L.split;
+    if (split_rows) *split_rows = h->L.n_ov;
     if (slices16) *slices16 = h->slices16;
     if (sell_entries) *sell_entries = h->L.sell_entries;
     if (n_slices) *n_slices = h->L.n_slices;
@@ -1316,8 +1459,23 @@ pdca_status pdca_batch_step(pdca_batch *b, int32_t passes, int32_t *active_after
             for (int K = 1; K <= PDCA_MAX_K; ++K) {
                 if (!used[un][K]) continue;
                 BatchTable &t = b->table;
+                BatchOvTable &o = b->ov_table;
                 t.n = 0;
                 t.total_slices = 0;
+                o.n = 0;
+                o.total_rows = 0;
+                // the overflow pre-pass of the members gathered so far, then their pass
+                auto flush = [&]() -> cudaError_t {
+                    if (t.n == 0) return cudaSuccess;
+                    cudaError_t e = launch_batch_overflow(K, o, b->stream);
+                    if (e != cudaSuccess) return e;
+                    e = launch_batch_pass(K, un == 1, t, b->stream);
+                    t.n = 0;
+                    t.total_slices = 0;
+                    o.n = 0;
+                    o.total_rows = 0;
+                    return e;
+                };
                 for (size_t i = 0; i < b->members.size(); ++i) {
                     const BatchMember &m = b->members[i];
                     if (m.h->L.K != K || (m.h->self ? 1 : 0) != un) continue;
@@ -1326,13 +1484,20 @@ pdca_status pdca_batch_step(pdca_batch *b, int32_t passes, int32_t *active_after
                     d.slice_begin = t.total_slices;
                     // members start at multiples of 8 slices (one block never spans two)
                     t.total_slices += (m.h->L.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock * kWarpsPerBlock;
-                    if (t.n == kBatchMax) {
-                        PDCA_TRY(launch_batch_pass(K, un == 1, t, b->stream));
-                        t.n = 0;
-                        t.total_slices = 0;
+                    if (m.h->ov.n_rows > 0) {
+                        BatchOvDesc &q = o.d[o.n++];
+                        q.O = m.h->ov;
+                        q.x = d.src;
+                        q.acc = m.h->ov_acc;
+                        q.q_begin = o.total_rows;
+                        q.wkind = d.kind == kPassMixedSweep ? kOvW16 : kOvW32;
+                        q.xkind = d.kind == kPassMixedSweep ? (m.h->bf16u ? kOvXBf16 : kOvXHalf) : kOvX32;
+                        q.pad_ = 0;
+                        o.total_rows += m.h->ov.n_rows;
                     }
+                    if (t.n == kBatchMax) PDCA_TRY(flush());
                 }
-                PDCA_TRY(launch_batch_pass(K, un == 1, t, b->stream));
+                PDCA_TRY(flush());
             }
         std::vector<BatchMember> keep;
         keep.reserve(b->members.size());

@@ -18,9 +18,14 @@
 //     previous or the next one, told apart by the entry's band: each row of
 //     such a slice keeps first its entries in the previous chunk, then those
 //     in the next chunk, then those in its own chunk and the padding);
-//   * rowinfo[r] = (row length << 8) | tag, tag = prior class or 0xFF; in a
-//     slice with 16-bit columns: tag | len << 8 (12 bits) | n_prev << 20
-//     (6 bits) | n_next << 26 (6 bits);
+//   * rows longer than a split length T (plain kernels only) keep their
+//     first T entries in the sliced ELL; the rest go to an overflow CSR (one
+//     row per such row, in row order) whose sums a pre-pass forms, one warp
+//     per row, before the kernel that needs them;
+//   * rowinfo[r] = tag | len << 8 | overflow << 19 (plain kernels: len <= T
+//     <= 2044, 11 bits), and in a slice with 16-bit columns also
+//     n_prev << 20 (6 bits) | n_next << 26 (6 bits); tiled kernels:
+//     tag | len << 8 (24 bits);
 //   * u is n_pad x K float32 row-major (n_pad = 32 * number of slices).
 #pragma once
 
@@ -53,7 +58,9 @@ constexpr uint32_t kLayoutMismatch = 8u;   // internal: packed row longer than i
 constexpr int kChunkShift = 16;              // 16-bit columns: 65536-node chunks
 constexpr uint8_t kFmt32 = 0, kFmt16 = 1;   // column format of a slice
 constexpr uint32_t kBandMax = 63;           // largest n_prev / n_next of a 16-bit row
-constexpr uint32_t kLen16Max = 4095;        // longest row of a 16-bit slice
+constexpr uint32_t kLenMask = 0x7FFu;       // rowinfo length field (plain kernels)
+constexpr uint32_t kOvFlag = 1u << 19;      // the row continues in the overflow CSR
+constexpr int32_t kSplitMax = 2044;         // largest split length (fits kLenMask, multiple of kVec)
 constexpr int kFmtGroupSlices = 32;         // slices sharing one column format
 struct SellView {
     const int32_t *col;        // padded sliced-ELL column indices (new numbering)
@@ -64,10 +71,24 @@ struct SellView {
     const int64_t *slice_off;  // n_slices + 1 entry offsets
     const uint32_t *rowinfo;   // (len << 8) | tag, n_pad
     const float *self;         // a_i = d_i per row (n_pad) for L; nullptr for L_s
+    const int32_t *ov_index;   // overflow row of each row with kOvFlag (n_pad), else unused
+    const float *ov_acc;       // the pre-pass sums, K floats per overflow row
     int32_t n_slices;
     int32_t n;                 // real rows; rows >= n are padding
     int32_t stream_rows;       // 1: the iterates exceed L2, store rows with st.global.cs
 };
+
+// The overflow CSR of the rows longer than the split length (entries past
+// the first T, in the pack's order), in new row order.
+struct OverflowView {
+    const int64_t *rp;         // n_rows + 1 offsets
+    const int32_t *col;        // columns (new numbering)
+    const float *w;            // FP32 weights
+    const __nv_bfloat16 *wb;   // BF16 weights (mixed precision; else nullptr)
+    int32_t n_rows;
+};
+enum OvWeights : int32_t { kOvW32 = 0, kOvW16 = 1 };
+enum OvRows : int32_t { kOvX32 = 0, kOvXHalf = 1, kOvXBf16 = 2 };
 
 // Resident blocks per SM the plain sweep is compiled for (registers per
 // thread <= 65536 / (256 x blocks)).
@@ -162,8 +183,23 @@ cudaError_t launch_power_spmv(const SellView &A, const TileView *T, const float 
                               float *y, double *partials, unsigned *ticket, double *lambda, cudaStream_t st);
 cudaError_t launch_power_finalize(const double *partials, int n_parts, double *scale,
                                   double *lambda, cudaStream_t st);
+// The power method on the caller's CSR graph (power_csr.cu): power_iters + 1
+// products from x0_i = 1 + 0.5 sin(i + 1); *scale and *lambda (device) hold
+// 1/||y|| and the Rayleigh quotient when the launches complete.  isd (L_s)
+// or deg (L, un = true) are the validation kernel's FP64 arrays.  scratch:
+// power_csr_scratch_bytes(n) device bytes.
+size_t power_csr_scratch_bytes(int32_t n);
+cudaError_t launch_power_csr(int32_t n, const int64_t *rp, const int32_t *col, const float *w, const double *isd,
+                             const double *deg, bool un, int32_t iters, void *scratch, double *scale, double *lambda,
+                             cudaStream_t st);
 cudaError_t launch_labels(int K, int32_t n, const float *u, const int32_t *perm,
                           int32_t *out, cudaStream_t st);
+
+// --- overflow pre-pass (overflow.cu) -----------------------------------------
+// acc[q K + k] = sum over the overflow entries e of row q of w_e x[col_e][k]
+// (x: n_pad x K rows of FP32, FP16 or BF16; weights FP32 or BF16).
+cudaError_t launch_overflow(int K, int wkind, int xkind, const OverflowView &O, const void *x, float *acc,
+                            cudaStream_t st);
 
 // --- mixed precision (mixed_kernels.cu) --------------------------------------
 // r is an n_pad x K FP32 array; e an n_pad x K array of FP16 (bf16u = false)
@@ -211,12 +247,28 @@ struct BatchDesc {
     const float *u;          // mixed sweep: u^t
     float *u_out;            // mixed, last pass: u^{t+1}
 };
-constexpr int kBatchMax = 160;   // descriptors per launch (kernel parameter space)
+constexpr int kBatchMax = 144;   // descriptors per launch (kernel parameter space)
 struct BatchTable {
     int32_t n;
     int32_t total_slices;
     BatchDesc d[kBatchMax];
 };
+// The overflow pre-pass of a batched pass: every member with overflow rows,
+// its rows numbered from q_begin in the launch's overflow-row range.
+struct BatchOvDesc {
+    OverflowView O;
+    const void *x;
+    float *acc;
+    int32_t q_begin;
+    int32_t wkind, xkind;
+    int32_t pad_;
+};
+struct BatchOvTable {
+    int32_t n;
+    int32_t total_rows;
+    BatchOvDesc d[kBatchMax];
+};
+cudaError_t launch_batch_overflow(int K, const BatchOvTable &t, cudaStream_t st);
 // un: the table holds problems on the unnormalized Laplacian (A.self set).
 cudaError_t launch_batch_pass(int K, bool un, const BatchTable &t, cudaStream_t st);
 cudaError_t launch_batch_pass_un(int K, const BatchTable &t, cudaStream_t st);
@@ -232,13 +284,16 @@ cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const in
 // self == nullptr: L_s weights w_ij / sqrt(d_i d_j); else L weights w_ij and
 // self[r] = d_i (0 on padding rows).  dsq (nullable): sqrt(d_i) per row.
 // rowcls (nullable): entries are written in bands (previous, next, own
-// chunk) and rowcls[r] records n_prev | n_next << 8 | 16-bit-capable << 16.
+// chunk) and rowcls[r] records n_prev | n_next << 8 | 16-bit-capable << 16
+// for the row's first split_len entries.  Entries past split_len go to the
+// overflow CSR row ov_index[r] (ov_index: -1 for rows that fit).
 cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_ptr,
                         const int32_t *col, const float *w, const double *deg, const double *isd,
                         const uint8_t *mask, const int32_t *labels, const int32_t *perm,
                         const int32_t *iperm, const int64_t *slice_off, int32_t *sell_col,
                         float *sell_w, __nv_bfloat16 *sell_wb, float *self, float *dsq, uint32_t *rowinfo,
-                        uint32_t *rowcls, uint32_t *status, cudaStream_t st);
+                        uint32_t *rowcls, int32_t split_len, const int32_t *ov_index, const int64_t *ov_rp,
+                        int32_t *ov_col, float *ov_w, __nv_bfloat16 *ov_wb, uint32_t *status, cudaStream_t st);
 // tiled form: local 16-bit columns (position in the tile's halo) instead of int32
 cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32_t *col, const float *w,
                               const double *deg, const double *isd, const uint8_t *mask, const int32_t *labels,
@@ -251,7 +306,9 @@ cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32
 // lists) is given, and exactly one of sell_w (FP32) and sell_wb (BF16).
 // rowcls (nullable; from the pack): per row n_prev | n_next << 8 | 16-bit-capable
 // << 16; the entries of a row are reordered only inside their band.
-cudaError_t launch_spread(int32_t n_pad, const int64_t *slice_off, const uint32_t *rowinfo,
+// len_mask: the rowinfo length field (kLenMask for the plain layout, 2^24 - 1
+// for the tiled one).
+cudaError_t launch_spread(int32_t n_pad, const int64_t *slice_off, const uint32_t *rowinfo, uint32_t len_mask,
                           const uint32_t *rowcls, int32_t *sell_col, uint16_t *lcol, const int64_t *halo_off,
                           const int32_t *halo_idx, float *sell_w, __nv_bfloat16 *sell_wb, cudaStream_t st);
 // 16-bit columns for every slice whose rows all allow them (rowcls), the
@@ -288,7 +345,7 @@ size_t spectral_workspace_bytes(int32_t n_pad);
 // largest-magnitude entry positive) in the caller's node order to
 // out_caller_order (device, n floats).  PDCA_ERR_NOT_CONVERGED when
 // max_iters ran out (the output is still written).
-pdca_status spectral_eigvec(const SellView &A, bool un, const float *q, const int32_t *perm, int32_t n,
+pdca_status spectral_eigvec(const SellView &A, const OverflowView &O, bool un, const float *q, const int32_t *perm, int32_t n,
                             int32_t n_pad, cudaStream_t st, void *workspace, int32_t max_iters, double tol,
                             double *lambda2, float *out_caller_order, int32_t *iters_done);
 

@@ -118,12 +118,15 @@ __global__ void window_sort_kernel(int32_t n, int32_t n_pad, int32_t sigma,
     }
 }
 
-// One thread per row.  With rowcls, a row's entries are written in three
+// One thread per row.  With rowcls, a row's entries are ordered in three
 // bands -- columns in the previous 65536-node chunk, in the next one, in the
-// row's own chunk (each band in CSR order) -- and rowcls[r] records n_prev |
-// n_next << 8 | 1 << 16 when the row can take 16-bit columns (no column
-// further than one chunk away, the band and length limits met), 0 otherwise
-// (entries then in CSR order).  Padding rows count as able.
+// row's own chunk (each band in CSR order) -- otherwise kept in CSR order.
+// The first split_len entries of that order go to the sliced ELL, the rest
+// to the row's overflow CSR row ov_index[r] (kOvFlag in rowinfo).  rowcls[r]
+// records the bands of the sliced entries, n_prev | n_next << 8, and
+// 1 << 16 when they can take 16-bit columns (no column further than one
+// chunk away, the band limits met); 0 for a row whose columns reach further
+// (its entries then stay in CSR order).  Padding rows count as able.
 __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
                             const int32_t *__restrict__ col, const float *__restrict__ w,
                             const double *__restrict__ deg, const double *__restrict__ isd,
@@ -133,23 +136,41 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
                             int32_t *__restrict__ sell_col, float *__restrict__ sell_w,
                             __nv_bfloat16 *__restrict__ sell_wb, float *__restrict__ self,
                             float *__restrict__ dsq, uint32_t *__restrict__ rowinfo,
-                            uint32_t *__restrict__ rowcls, uint32_t *__restrict__ status) {
+                            uint32_t *__restrict__ rowcls, int32_t split_len, const int32_t *__restrict__ ov_index,
+                            const int64_t *__restrict__ ov_rp, int32_t *__restrict__ ov_col,
+                            float *__restrict__ ov_w, __nv_bfloat16 *__restrict__ ov_wb,
+                            uint32_t *__restrict__ status) {
     const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_pad) return;
     const int32_t s = r >> 5, lane = r & 31;
     const int64_t base = slice_off[s];
     const int32_t width = (int32_t)((slice_off[s + 1] - base) >> 5);
     const int32_t old = perm[r];
-    int32_t len = 0;
-    uint32_t tag = kTagUnlabelled;
+    int32_t len = 0, kept = 0;
+    uint32_t tag = kTagUnlabelled, ovf = 0u;
     uint32_t cls = 1u << 16;
     auto at = [&](int32_t j) { return base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec); };
     if (old >= 0) {
         const int64_t e0 = row_ptr[old];
         len = (int32_t)(row_ptr[old + 1] - e0);
-        if (len > width) {  // host and device layouts disagree: never write past the slice
+        kept = len < split_len ? len : split_len;
+        int64_t o0 = 0;
+        if (len > split_len) {
+            const int32_t q = ov_index ? ov_index[r] : -1;
+            if (q < 0 || ov_rp[q + 1] - ov_rp[q] != (int64_t)(len - split_len)) {
+                // host and device layouts disagree: keep the row inside its slice
+                atomicOr(status, kLayoutMismatch);
+                len = kept;
+            } else {
+                o0 = ov_rp[q];
+                ovf = kOvFlag;
+            }
+        }
+        if (kept > width) {  // never write past the slice
             atomicOr(status, kLayoutMismatch);
-            len = width;
+            kept = width;
+            len = len < width ? len : width;
+            ovf = 0u;
         }
         const double di = deg[old];
         if (self) self[r] = (float)di;
@@ -175,29 +196,39 @@ __global__ void pack_kernel(int32_t n_pad, const int64_t *__restrict__ row_ptr,
                 const int32_t d = (cj >> kChunkShift) - hr;
                 pos = d < 0 ? p_prev++ : (d > 0 ? p_next++ : p_own++);
             }
-            const int64_t a = at(pos);
-            sell_col[a] = cj;
             const double wt = self ? (double)w[e0 + j] : (double)w[e0 + j] * isd[old] * isd[oj];
-            sell_w[a] = (float)wt;
-            if (sell_wb) sell_wb[a] = __double2bfloat16(wt);
+            if (pos < kept) {
+                const int64_t a = at(pos);
+                sell_col[a] = cj;
+                sell_w[a] = (float)wt;
+                if (sell_wb) sell_wb[a] = __double2bfloat16(wt);
+            } else if (ovf) {
+                const int64_t a = o0 + (pos - kept);
+                ov_col[a] = cj;
+                ov_w[a] = (float)wt;
+                if (ov_wb) ov_wb[a] = __double2bfloat16(wt);
+            }
         }
         if (mask[old]) tag = (uint32_t)labels[old];
-        const bool ok16 = banded && (uint32_t)len <= kLen16Max && (uint32_t)np <= kBandMax &&
-                          (uint32_t)nn <= kBandMax;
+        // bands of the sliced entries (the first `kept` of the banded order)
+        const int32_t np_k = np < kept ? np : kept;
+        const int32_t nb_k = np + nn < kept ? np + nn : kept;
+        const int32_t nn_k = nb_k - np_k;
+        const bool ok16 = banded && (uint32_t)np_k <= kBandMax && (uint32_t)nn_k <= kBandMax;
         // counts above 255 are kept at 255 (such a row is not 16-bit capable
         // anyway); the fields must not run into the capability bit
-        cls = banded ? ((uint32_t)min(np, 255) | ((uint32_t)min(nn, 255) << 8) | (ok16 ? 1u << 16 : 0u)) : 0u;
+        cls = banded ? ((uint32_t)min(np_k, 255) | ((uint32_t)min(nn_k, 255) << 8) | (ok16 ? 1u << 16 : 0u)) : 0u;
     } else {
         if (self) self[r] = 0.0f;
         if (dsq) dsq[r] = 0.0f;
     }
-    for (int32_t j = len; j < width; ++j) {
+    for (int32_t j = kept; j < width; ++j) {
         const int64_t a = at(j);
         sell_col[a] = r;
         sell_w[a] = 0.0f;
         if (sell_wb) sell_wb[a] = __float2bfloat16(0.0f);
     }
-    rowinfo[r] = ((uint32_t)len << 8) | tag;
+    rowinfo[r] = ((uint32_t)kept << 8) | tag | ovf;
     if (rowcls) rowcls[r] = cls;
 }
 
@@ -226,7 +257,7 @@ compress_kernel(int32_t n_slices, const int64_t *__restrict__ slice_off, const u
         const int64_t a = base + 32 * kVec * (int64_t)(j / kVec) + kVec * lane + (j % kVec);
         col16[a] = (uint16_t)((uint32_t)sell_col[a] & 0xFFFFu);
     }
-    const uint32_t info = rowinfo[r];   // len <= kLen16Max: bits 20..31 are free
+    const uint32_t info = rowinfo[r];   // len <= kSplitMax: bits 20..31 are free
     rowinfo[r] = info | ((cls & 0xFFu) << 20) | (((cls >> 8) & 0xFFu) << 26);
 }
 
@@ -305,7 +336,8 @@ constexpr int kSpreadLook = 64;
 constexpr int kSpreadLanes = 8;   // S
 
 __global__ void spread_kernel(int32_t n_slices, const int64_t *__restrict__ slice_off,
-                              const uint32_t *__restrict__ rowinfo, const uint32_t *__restrict__ rowcls,
+                              const uint32_t *__restrict__ rowinfo, uint32_t len_mask,
+                              const uint32_t *__restrict__ rowcls,
                               int32_t *__restrict__ sell_col,
                               uint16_t *__restrict__ lcol, const int64_t *__restrict__ halo_off,
                               const int32_t *__restrict__ halo_idx, float *__restrict__ sell_w,
@@ -322,7 +354,7 @@ __global__ void spread_kernel(int32_t n_slices, const int64_t *__restrict__ slic
 #pragma unroll
     for (int32_t l = 0; l < S; ++l) {
         const int64_t r = s * kSliceRows + lane0 + l;
-        len[l] = (int32_t)(rowinfo[r] >> 8);
+        len[l] = (int32_t)((rowinfo[r] >> 8) & len_mask);
         const uint32_t c = rowcls ? rowcls[r] : 0u;
         np[l] = (int32_t)(c & 0xFFu);
         nb[l] = np[l] + (int32_t)((c >> 8) & 0xFFu);
@@ -449,13 +481,16 @@ cudaError_t launch_pack(int32_t n, int32_t n_pad, int32_t K, const int64_t *row_
                         const int32_t *labels,
                         const int32_t *perm, const int32_t *iperm, const int64_t *slice_off,
                         int32_t *sell_col, float *sell_w, __nv_bfloat16 *sell_wb, float *self, float *dsq,
-                        uint32_t *rowinfo, uint32_t *rowcls, uint32_t *status, cudaStream_t st) {
+                        uint32_t *rowinfo, uint32_t *rowcls, int32_t split_len, const int32_t *ov_index,
+                        const int64_t *ov_rp, int32_t *ov_col, float *ov_w, __nv_bfloat16 *ov_wb, uint32_t *status,
+                        cudaStream_t st) {
     (void)n;
     (void)K;
     count_launches(1);
     pack_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n_pad, row_ptr, col, w, deg, isd, mask, labels, perm,
                                                      iperm, slice_off, sell_col, sell_w, sell_wb, self, dsq,
-                                                     rowinfo, rowcls, status);
+                                                     rowinfo, rowcls, split_len, ov_index, ov_rp, ov_col, ov_w,
+                                                     ov_wb, status);
     return cudaGetLastError();
 }
 
@@ -481,15 +516,16 @@ cudaError_t launch_pack_tiled(int32_t n_pad, const int64_t *row_ptr, const int32
     return cudaGetLastError();
 }
 
-cudaError_t launch_spread(int32_t n_pad, const int64_t *slice_off, const uint32_t *rowinfo, const uint32_t *rowcls,
-                          int32_t *sell_col, uint16_t *lcol, const int64_t *halo_off, const int32_t *halo_idx,
-                          float *sell_w, __nv_bfloat16 *sell_wb, cudaStream_t st) {
+cudaError_t launch_spread(int32_t n_pad, const int64_t *slice_off, const uint32_t *rowinfo, uint32_t len_mask,
+                          const uint32_t *rowcls, int32_t *sell_col, uint16_t *lcol, const int64_t *halo_off,
+                          const int32_t *halo_idx, float *sell_w, __nv_bfloat16 *sell_wb, cudaStream_t st) {
     const int32_t n_slices = n_pad / kSliceRows;
     const int64_t threads = (int64_t)n_slices * (kSliceRows / kSpreadLanes);
     if (threads == 0) return cudaSuccess;
     count_launches(1);
-    spread_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n_slices, slice_off, rowinfo, rowcls, sell_col,
-                                                                     lcol, halo_off, halo_idx, sell_w, sell_wb);
+    spread_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n_slices, slice_off, rowinfo, len_mask, rowcls,
+                                                                     sell_col, lcol, halo_off, halo_idx, sell_w,
+                                                                     sell_wb);
     return cudaGetLastError();
 }
 

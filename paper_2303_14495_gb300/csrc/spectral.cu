@@ -296,6 +296,7 @@ bool ortho_coeffs(const double *g, double *cmat) {
 
 struct Ctx {
     SellView A;
+    OverflowView O;
     cudaStream_t st;
     int32_t n, n_pad;
     bool un;
@@ -307,6 +308,9 @@ struct Ctx {
 
 cudaError_t spmm(Ctx &c, const float *x, float *y) {
     const int blocks = (c.A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    // the split rows' remaining entries first (kM columns per overflow row)
+    cudaError_t e = launch_overflow(kM, kOvW32, kOvX32, c.O, x, const_cast<float *>(c.A.ov_acc), c.st);
+    if (e != cudaSuccess) return e;
     count_launches(1);
     if (c.un) spmm4_kernel<true><<<blocks, kBlockThreads, 0, c.st>>>(c.A, x, y);
     else spmm4_kernel<false><<<blocks, kBlockThreads, 0, c.st>>>(c.A, x, y);
@@ -368,7 +372,7 @@ size_t spectral_workspace_bytes(int32_t n_pad) {
     return kBufs * blk + (size_t)kMaxGrams * kGramBlocks * kGramSlots * sizeof(double) + 3 * 256 * 4;
 }
 
-pdca_status spectral_eigvec(const SellView &A, bool un, const float *q, const int32_t *perm, int32_t n,
+pdca_status spectral_eigvec(const SellView &A, const OverflowView &O, bool un, const float *q, const int32_t *perm, int32_t n,
                             int32_t n_pad, cudaStream_t st, void *workspace, int32_t max_iters, double tol,
                             double *lambda2, float *out_caller_order, int32_t *iters_done) {
 
@@ -378,6 +382,7 @@ pdca_status spectral_eigvec(const SellView &A, bool un, const float *q, const in
     for (int b = 0; b < kBufs; ++b) buf[b] = reinterpret_cast<float *>(W + (size_t)b * blk);
     Ctx c;
     c.A = A;
+    c.O = O;
     c.st = st;
     c.n = n;
     c.n_pad = n_pad;

@@ -150,13 +150,12 @@ energy_kernel(const SellView A, const Coeffs cf, const float *__restrict__ u,
         load_row<K>(u + (size_t)r * K, x);
         if (u_prev) load_own_row<K>(u_prev + (size_t)r * K, xp);
         float acc[K];
-        stream_gather<K, C16, float, float>(s, info, r, u, acc);
+        stream_gather<K, C16, float, float>(A, s, info, r, u, acc);
         energy_row<K>(A, cf, r, info, acc, x, xp, u_prev != nullptr, red);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const double t = warp_sum_df(red[k]);
-            if (lane == 0) slot_sum[slice - first][k] = t;
-        }
+        const float red8[8] = {red[0], red[1], red[2], red[3], red[4], red[5], 0.f, 0.f};
+        const double t = warp_sum8_df(red8);
+        const int q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        if ((lane & 3) == 0 && q < 6) slot_sum[slice - first][q] = t;
     });
     __syncthreads();
     if (threadIdx.x < 6) {
@@ -327,10 +326,12 @@ power_spmv_kernel(const SellView A, const float *__restrict__ x, double *scale, 
         row_gather<1, float, float, decltype(fmt)::value>(A, slice, lane, x, acc);
         float red[3] = {0.f, 0.f, 0.f};
         power_row(A, slice, lane, acc[0], s, x, y, red);
+        // FP32 inside the warp (the sums only normalise the iterate and
+        // form the Rayleigh quotient), FP64 across warps and blocks
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const double t = warp_sum_df(red[k]);
-            if (lane == 0) slot_sum[slice - first][k] = t;
+            const float t = warp_sum_f(red[k]);
+            if (lane == 0) slot_sum[slice - first][k] = (double)t;
         }
     });
     __syncthreads();

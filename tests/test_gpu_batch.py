@@ -36,6 +36,7 @@ def problem_specs(variants=False):
     if variants:
         rows += [(1500, 4, 0, 3, 1, 0.0), (900, 2, 0, 2, 0, 0.5), (1200, 5, 1, 3, 1, 0.0),
                  (800, 1, 0, 4, 1, 2.0), (2600, 10, 0, 2, 0, 0.05)]
+    splits = {9: 8, 10: 12, 11: 8, 12: 4}     # members whose long rows continue in the overflow CSR
     specs = []
     for i, (n, K, prec, inner, lap, k) in enumerate(rows):
         rp, col, w = random_graph(n, 8, seed=100 + i)
@@ -43,13 +44,13 @@ def problem_specs(variants=False):
         mask = (rng.uniform(size=n) < 0.1).astype(np.uint8)
         lab = rng.integers(0, max(K, 2), size=n).astype(np.int32)
         specs.append(dict(rp=rp, col=col, w=w, K=K, mask=mask, lab=lab, prec=prec, inner=inner, outer=2 + i % 3,
-                          lap=lap, k=k))
+                          lap=lap, k=k, split=splits.get(i, 0) if variants else 0))
     return specs
 
 
 def make(B, sp):
     prm = B.make_params(eps=EPS, eta=ETA, c=C, precond=1, precision=sp["prec"], laplacian=sp.get("lap", 0),
-                        step_k=sp.get("k", 0.0))
+                        step_k=sp.get("k", 0.0), row_split=sp.get("split", 0))
     return B.Problem(sp["rp"], sp["col"], sp["w"], sp["K"], sp["mask"], sp["lab"], prm)
 
 

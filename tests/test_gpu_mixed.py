@@ -118,6 +118,31 @@ def test_mixed_small_graphs(B, K, inner):
     assert abs(F - F_ref) <= 1e-3 * abs(F_ref), (F, F_ref)
 
 
+@pytest.mark.parametrize("prec", list(PREC))
+def test_mixed_split_rows(B, prec):
+    """Forced split length 8: the residual pass and the correction sweeps add
+    the overflow pre-pass sums (FP32 and BF16 weights, 16-bit rows)."""
+    n = 2500
+    rp, col, w = random_graph(n, 14, seed=61)
+    rng = np.random.default_rng(4)
+    mask = (rng.uniform(size=n) < 0.1).astype(np.uint8)
+    lab = rng.integers(0, 4, size=n).astype(np.int32)
+    p = dict(eps=1.0, eta=50.0, c=52.0, precond=1)
+    prm = B.make_params(eps=1.0, eta=50.0, c=52.0, precond=1, precision=PREC[prec], row_split=8)
+    g = B.Problem(rp, col, w, 4, mask, lab, prm)
+    assert g.layout()["split_rows"] > n // 2
+    ref = oracle.Problem(rp, col, w, 4, mask, lab, 1.0, 50.0, 52.0, precond=1)
+    u_ref = ref.init_u()
+    for _ in range(4):
+        g.step(3)
+        u_ref, e_ref, _ = ref.solve(1, 3, u_ref)
+        assert rel_l2(g.get_u(), u_ref) <= 1e-4
+    agree, _, _ = label_agreement(g.labels(), ref.labels_of(u_ref), u_ref, 4)
+    assert agree >= 0.999, agree
+    F, _ = g.energy()
+    assert abs(F - e_ref[-1]) <= 1e-3 * abs(e_ref[-1])
+
+
 def test_mixed_keeps_exact_fixed_point(B):
     """Without fidelity and from u^0 = 0 the iterate is the fixed point 0 of
     the DCA map (b = 0, T 0 = 0): every precision must keep it exactly."""

@@ -263,6 +263,39 @@ def test_column_formats_bitwise(B):
     assert out[0][1] == out[1][1]
 
 
+@pytest.mark.parametrize("K", [1, 4, 10])
+@pytest.mark.parametrize("layout", ["bfs_plain", "window_sort", "csr_entries"])
+@pytest.mark.parametrize("lap", [0, 1])
+def test_split_rows(B, K, layout, lap):
+    """A forced split length of 8 entries: most rows continue in the overflow
+    CSR, whose pre-pass sums every sweep and the energy pass add."""
+    n = 3001
+    rp, col, w = random_graph(n, 14, seed=97 + K)
+    rng = np.random.default_rng(K)
+    mask = (rng.uniform(size=n) < 0.1).astype(np.uint8)
+    lab = rng.integers(0, max(K, 2), size=n).astype(np.int32)
+    prm = B.make_params(eps=1.0, eta=20.0, c=22.0, precond=B.PDCA_JACOBI_PERTURBED, laplacian=lap, row_split=8,
+                        **LAYOUTS[layout])
+    gpu = B.Problem(rp, col, w, K, mask, lab, prm)
+    ref = oracle.Problem(rp, col, w, K, mask, lab, 1.0, 20.0, 22.0, precond=B.PDCA_JACOBI_PERTURBED, laplacian=lap)
+    lay = gpu.layout()
+    assert lay["split_len"] == 8 and lay["split_rows"] > n // 2, lay
+    run_parity(gpu, ref, 4, 3)
+
+
+def test_split_power_method(B):
+    """Richardson's lambda_max estimate on a graph with hub rows (automatic
+    split), against the oracle's power method."""
+    rp, col, w = banded_graph(20_000, 8, 3_000, seed=5, hubs=(700, 9_000, 15_000), hub_deg=900)
+    n = rp.size - 1
+    g = B.Problem(rp, col, w, 1, np.zeros(n, np.uint8), np.zeros(n, np.int32),
+                  B.make_params(precond=B.PDCA_RICHARDSON))
+    assert g.layout()["split_rows"] >= 3
+    used, est = g.lambda_max()
+    lam = oracle.Problem(rp, col, w, 1, np.zeros(n, np.uint8), np.zeros(n, np.int32), 1, 1, 1).power_max_eig(150)
+    assert abs(est - lam) <= 2e-5 * lam
+
+
 def test_hub_rows(B):
     """A star-like hub (degree n-1) next to short rows: very uneven slices."""
     n = 700
@@ -278,6 +311,7 @@ def test_hub_rows(B):
     lab = np.zeros(n, np.int32)
     lab[400] = 1
     gpu, ref = make_pair(B, rp, col, ww, 1, mask, lab, 1.0, 10.0, 12.0, B.PDCA_JACOBI_PERTURBED)
+    assert gpu.layout()["split_rows"] == 1     # the hub continues in the overflow CSR
     run_parity(gpu, ref, 5, 5)
 
 

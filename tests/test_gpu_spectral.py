@@ -96,6 +96,22 @@ def test_second_eigenpair(B, case, lap):
     np.testing.assert_array_equal(g.get_u(), u0)
 
 
+@pytest.mark.parametrize("lap", [0, 1])
+def test_second_eigenpair_split_rows(B, lap):
+    """Rows longer than 8 entries continue in the overflow CSR (forced split
+    length): the block SpMM adds their pre-pass sums."""
+    rp, col, w = random_graph(3000, 14, seed=43)
+    lam_ref, v_ref = oracle.second_eigenpair(rp, col, w, lap)
+    g = unsup_problem(B, rp, col, w, lap=lap, row_split=8)
+    assert g.layout()["split_rows"] > 0
+    lam, u0, its = g.spectral_init(max_iters=3000, tol=TOL)
+    assert abs(lam - lam_ref) <= 1e-5 + 1e-4 * abs(lam_ref)
+    gap = gap_of(rp, col, w, lap)
+    d, _ = oracle.degrees(rp, col, w)
+    spec = 2.0 if lap == 0 else 2.0 * d.max()
+    assert_same_init(u0, oracle.spectral_init(v_ref), max(10 * TOL * spec / gap, 1e-5))
+
+
 def test_two_cliques_unsupervised_split(B):
     """The unsupervised model started from u^0 separates two weakly joined
     cliques exactly."""
