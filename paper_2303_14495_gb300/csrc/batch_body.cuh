@@ -1,6 +1,7 @@
-// Batched pass kernels, shared by batch_kernels.cu (L_s instances) and
-// batch_kernels_un.cu (L = D - W instances), compiled separately so the two
-// sets build in parallel.  A launch holds problems of one K and one Laplacian.
+// Batched pass kernels, shared by the four translation units that
+// instantiate them (L_s or L = D - W, K <= 8 or K > 8), compiled separately
+// so the sets build in parallel.  A launch holds problems of one K and one
+// Laplacian.
 #pragma once
 #include "device_common.cuh"
 
@@ -79,18 +80,26 @@ cudaError_t batch_k(const BatchTable &t, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <bool UN>
-cudaError_t batch_all(int K, const BatchTable &t, cudaStream_t st) {
-    switch (K) {
-    case 1: return batch_k<1, UN>(t, st); case 2: return batch_k<2, UN>(t, st);
-    case 3: return batch_k<3, UN>(t, st); case 4: return batch_k<4, UN>(t, st);
-    case 5: return batch_k<5, UN>(t, st); case 6: return batch_k<6, UN>(t, st);
-    case 7: return batch_k<7, UN>(t, st); case 8: return batch_k<8, UN>(t, st);
-    case 9: return batch_k<9, UN>(t, st); case 10: return batch_k<10, UN>(t, st);
-    case 11: return batch_k<11, UN>(t, st); case 12: return batch_k<12, UN>(t, st);
-    case 13: return batch_k<13, UN>(t, st); case 14: return batch_k<14, UN>(t, st);
-    case 15: return batch_k<15, UN>(t, st); case 16: return batch_k<16, UN>(t, st);
-    default: return cudaErrorInvalidValue;
+// K <= 8 (LO) or K > 8: the instance sets compile in separate translation
+// units.
+template <bool UN, bool LO>
+cudaError_t batch_set(int K, const BatchTable &t, cudaStream_t st) {
+    if constexpr (LO) {
+        switch (K) {
+        case 1: return batch_k<1, UN>(t, st); case 2: return batch_k<2, UN>(t, st);
+        case 3: return batch_k<3, UN>(t, st); case 4: return batch_k<4, UN>(t, st);
+        case 5: return batch_k<5, UN>(t, st); case 6: return batch_k<6, UN>(t, st);
+        case 7: return batch_k<7, UN>(t, st); case 8: return batch_k<8, UN>(t, st);
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (K) {
+        case 9: return batch_k<9, UN>(t, st); case 10: return batch_k<10, UN>(t, st);
+        case 11: return batch_k<11, UN>(t, st); case 12: return batch_k<12, UN>(t, st);
+        case 13: return batch_k<13, UN>(t, st); case 14: return batch_k<14, UN>(t, st);
+        case 15: return batch_k<15, UN>(t, st); case 16: return batch_k<16, UN>(t, st);
+        default: return cudaErrorInvalidValue;
+        }
     }
 }
 

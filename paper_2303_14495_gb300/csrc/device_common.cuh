@@ -346,7 +346,9 @@ __device__ __forceinline__ void fma_entry_group(float (&acc)[K], const CG &c, co
 
 // The gather proper: while a lane works on two entry groups the next two are
 // in flight; products are added in entry order.
-template <int K, bool C16, class WT, class XT>
+// OV = false leaves out the overflow sums (problems without split rows; the
+// check alone costs the FP32 sweep about 3% on GB300).
+template <int K, bool C16, class WT, class XT, bool OV = true>
 __device__ __forceinline__ void stream_gather(const SellView &A, EntryStream<C16, WT> &s, uint32_t info, int r,
                                               const XT *__restrict__ x, float (&acc)[K]) {
 #pragma unroll
@@ -371,14 +373,14 @@ __device__ __forceinline__ void stream_gather(const SellView &A, EntryStream<C16
         s.c1 = n1;
         s.w1 = nw1;
     }
-    add_overflow<K>(A, r, info, acc);
+    if constexpr (OV) add_overflow<K>(A, r, info, acc);
 }
 
 // The gather without look-ahead: each step loads two entry groups, then
 // their eight rows, then adds the products in entry order.  It holds fewer
 // registers than stream_gather; the mixed-precision passes use it and keep
 // six blocks per SM.
-template <int K, bool C16, class WT, class XT>
+template <int K, bool C16, class WT, class XT, bool OV = true>
 __device__ __forceinline__ void short_gather(const SellView &A, int slice, int lane, uint32_t info, int r,
                                              const XT *__restrict__ x, float (&acc)[K]) {
     using CG = typename ColFmt<C16>::G;
@@ -415,7 +417,7 @@ __device__ __forceinline__ void short_gather(const SellView &A, int slice, int l
         const float4 wa = wgroup<WT>(ld_stream(wp + 32 * g));
         fma_entry_group<K, XT>(acc, ca, wa, g, b, x);
     }
-    add_overflow<K>(A, r, info, acc);
+    if constexpr (OV) add_overflow<K>(A, r, info, acc);
 }
 
 // Column format of the slices one block handles.  The format is decided per
@@ -892,7 +894,7 @@ __device__ __forceinline__ void load_own_row(const float *__restrict__ p, float 
 // FP32 sweep of one slice: the loads that depend on nothing (the row tag and
 // length, the first two entry groups, the own rows of v^s and u^t) first,
 // then the pipelined gather, then the update.
-template <int K, bool PROJECT, bool UN, bool C16>
+template <int K, bool PROJECT, bool UN, bool C16, bool OV = true>
 __device__ __forceinline__ void fp32_sweep_slice(const SellView &A, const Coeffs &cf, int slice, int lane,
                                                  const float *__restrict__ v_src, const float *__restrict__ u_t,
                                                  float *__restrict__ v_dst) {
@@ -910,7 +912,7 @@ __device__ __forceinline__ void fp32_sweep_slice(const SellView &A, const Coeffs
         load_own_row<K>(u_t + (size_t)r * K, u);
     }
     float acc[K];
-    stream_gather<K, C16, float, float>(A, s, info, r, v_src, acc);
+    stream_gather<K, C16, float, float, OV>(A, s, info, r, v_src, acc);
     sweep_update<K, PROJECT, UN>(cf, info, a, acc, v, u, v_dst + (size_t)r * K, A.stream_rows != 0);
 }
 
@@ -918,7 +920,7 @@ __device__ __forceinline__ void fp32_sweep_slice(const SellView &A, const Coeffs
 // weights and the FP32 iterate (the FP32 residual correction), stored in
 // FP32, and e^1 = G^-1 r in 16-bit storage (or, with a single sweep,
 // u^{t+1} = u^t + e^1).
-template <int K, class HT, bool LAST, bool PROJECT, bool UN, bool C16>
+template <int K, class HT, bool LAST, bool PROJECT, bool UN, bool C16, bool OV = true>
 __device__ __forceinline__ void mixed_residual_slice(const SellView &A, const Coeffs &cf, int slice, int lane,
                                                      const float *__restrict__ u, float *__restrict__ r_out,
                                                      HT *__restrict__ e_out, float *__restrict__ u_out) {
@@ -926,7 +928,7 @@ __device__ __forceinline__ void mixed_residual_slice(const SellView &A, const Co
     const uint32_t info = ld_stream(A.rowinfo + r);
     const float a = UN ? __ldg(A.self + r) : 1.0f;
     float acc[K];
-    short_gather<K, C16, float, float>(A, slice, lane, info, r, u, acc);
+    short_gather<K, C16, float, float, OV>(A, slice, lane, info, r, u, acc);
     float x[K];
     load_row<K>(u + (size_t)r * K, x);
     const uint32_t tag = info & 0xFFu;
@@ -954,7 +956,7 @@ __device__ __forceinline__ void mixed_residual_slice(const SellView &A, const Co
 // Mixed precision correction sweep with BF16 weights: e' = e + G^-1 (r - T e)
 // (r in FP32, e in 16-bit storage); the last one writes u^{t+1} = u^t + e' in
 // FP32 (projected for K >= 2).
-template <int K, class HT, bool LAST, bool PROJECT, bool UN, bool C16>
+template <int K, class HT, bool LAST, bool PROJECT, bool UN, bool C16, bool OV = true>
 __device__ __forceinline__ void mixed_sweep_slice(const SellView &A, const Coeffs &cf, int slice, int lane,
                                                   const HT *__restrict__ e_src, const float *__restrict__ rr,
                                                   HT *__restrict__ e_dst, const float *__restrict__ u,
@@ -963,7 +965,7 @@ __device__ __forceinline__ void mixed_sweep_slice(const SellView &A, const Coeff
     const uint32_t info = ld_stream(A.rowinfo + r);
     const float a = UN ? __ldg(A.self + r) : 1.0f;
     float acc[K];
-    short_gather<K, C16, __nv_bfloat16, HT>(A, slice, lane, info, r, e_src, acc);
+    short_gather<K, C16, __nv_bfloat16, HT, OV>(A, slice, lane, info, r, e_src, acc);
     float e[K], res[K];
     load_row_t<K, HT>(e_src + (size_t)r * K, e);
     load_own_row<K>(rr + (size_t)r * K, res);   // the residual row: read by this lane only

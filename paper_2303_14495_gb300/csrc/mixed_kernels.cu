@@ -18,13 +18,19 @@
 
 namespace pdca {
 
+// this unit: L_s with FP16 correction storage; mixed_kernels_*.cu the other sets
+PDCA_MIXED_SET(mixed_ls_f16, false, __half)
+
 cudaError_t launch_mixed_residual(int K, bool bf16u, bool last, bool project, const SellView &A,
                                   const Coeffs &cf, const float *u, void *r, void *e, float *u_out,
                                   cudaStream_t st) {
     if (A.n_slices <= 0) return cudaSuccess;
     count_launches(1);
-    if (A.self) return launch_mixed_residual_un(K, bf16u, last, project, A, cf, u, r, e, u_out, st);
-    return mixed_residual_all<false>(K, bf16u, last, project, A, cf, u, r, e, u_out, st);
+    if (A.self)
+        return bf16u ? mixed_un_b16_residual(K, last, project, A, cf, u, r, e, u_out, st)
+                     : mixed_un_f16_residual(K, last, project, A, cf, u, r, e, u_out, st);
+    return bf16u ? mixed_ls_b16_residual(K, last, project, A, cf, u, r, e, u_out, st)
+                 : mixed_ls_f16_residual(K, last, project, A, cf, u, r, e, u_out, st);
 }
 
 cudaError_t launch_mixed_sweep(int K, bool bf16u, bool last, bool project, const SellView &A, const Coeffs &cf,
@@ -32,8 +38,11 @@ cudaError_t launch_mixed_sweep(int K, bool bf16u, bool last, bool project, const
                                cudaStream_t st) {
     if (A.n_slices <= 0) return cudaSuccess;
     count_launches(1);
-    if (A.self) return launch_mixed_sweep_un(K, bf16u, last, project, A, cf, e_src, r, e_dst, u, u_out, st);
-    return mixed_sweep_all<false>(K, bf16u, last, project, A, cf, e_src, r, e_dst, u, u_out, st);
+    if (A.self)
+        return bf16u ? mixed_un_b16_sweep(K, last, project, A, cf, e_src, r, e_dst, u, u_out, st)
+                     : mixed_un_f16_sweep(K, last, project, A, cf, e_src, r, e_dst, u, u_out, st);
+    return bf16u ? mixed_ls_b16_sweep(K, last, project, A, cf, e_src, r, e_dst, u, u_out, st)
+                 : mixed_ls_f16_sweep(K, last, project, A, cf, e_src, r, e_dst, u, u_out, st);
 }
 
 }  // namespace pdca

@@ -49,7 +49,7 @@ struct Layout {
     size_t o_hoff, o_hidx;
     size_t o_ovrp, o_ovcol, o_ovw, o_ovwb, o_ovidx, o_ovacc;   // overflow CSR and its pre-pass sums
     size_t o_mr, o_me[2];              // mixed precision: r (FP32) and the two corrections (16-bit)
-    size_t o_srp, o_scol, o_sw, o_sdeg, o_sisd, o_smask, o_slab, o_scls, o_spow, o_status;
+    size_t o_srp, o_scol, o_sw, o_sdeg, o_sisd, o_smask, o_slab, o_scls, o_status;
     size_t persistent = 0, total = 0;
 };
 
@@ -355,8 +355,6 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     L.o_smask = take(nn);
     L.o_slab = take(4 * nn);
     L.o_scls = take(4 * np);
-    // the power method on the CSR input (Richardson without a given lambda_max)
-    L.o_spow = take(prm.precond == PDCA_RICHARDSON && prm.lambda_max <= 0.0 ? power_csr_scratch_bytes(n) : 0);
     L.o_status = take(16);
     L.total = o;
     return PDCA_OK;
@@ -1006,13 +1004,6 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
         st = feasible(prm, omega, prm.lambda_max, h->dmax);
         if (st != PDCA_OK) return fail(st);
     }
-    // lambda_max by the power method on the CSR input: queued now, it runs on
-    // the device while the host computes the renumbering
-    const bool power = prm.precond == PDCA_RICHARDSON && prm.lambda_max <= 0.0;
-    if (power && launch_power_csr(n, s_rp, s_col, s_w, s_isd, s_deg, prm.laplacian == PDCA_LAP_UNNORMALIZED,
-                                  prm.power_iters, W + L.o_spow, h->scal, h->scal + 1, sm) != cudaSuccess)
-        return fail(PDCA_ERR_CUDA);
-
     if (L.host_order) {
         st = host_renumber(h, rp, job);
         if (st != PDCA_OK) return fail(st);
@@ -1058,12 +1049,8 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
         if (prm.lambda_max > 0) {
             h->lambda_used = prm.lambda_max;
         } else {
-            double lam_h = 0.0;
-            if (cudaMemcpyAsync(&lam_h, h->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
-                cudaStreamSynchronize(sm) != cudaSuccess)
-                return fail(PDCA_ERR_CUDA);
-            h->lambda_est = lam_h;
-            h->lambda_used = std::min(lambda_bound(h), 1.001 * lam_h);
+            st = power_method(h);
+            if (st != PDCA_OK) return fail(st);
         }
         st = feasible(prm, omega, h->lambda_used, h->dmax);
         if (st != PDCA_OK) return fail(st);

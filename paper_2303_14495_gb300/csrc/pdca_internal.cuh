@@ -183,15 +183,6 @@ cudaError_t launch_power_spmv(const SellView &A, const TileView *T, const float 
                               float *y, double *partials, unsigned *ticket, double *lambda, cudaStream_t st);
 cudaError_t launch_power_finalize(const double *partials, int n_parts, double *scale,
                                   double *lambda, cudaStream_t st);
-// The power method on the caller's CSR graph (power_csr.cu): power_iters + 1
-// products from x0_i = 1 + 0.5 sin(i + 1); *scale and *lambda (device) hold
-// 1/||y|| and the Rayleigh quotient when the launches complete.  isd (L_s)
-// or deg (L, un = true) are the validation kernel's FP64 arrays.  scratch:
-// power_csr_scratch_bytes(n) device bytes.
-size_t power_csr_scratch_bytes(int32_t n);
-cudaError_t launch_power_csr(int32_t n, const int64_t *rp, const int32_t *col, const float *w, const double *isd,
-                             const double *deg, bool un, int32_t iters, void *scratch, double *scale, double *lambda,
-                             cudaStream_t st);
 cudaError_t launch_labels(int K, int32_t n, const float *u, const int32_t *perm,
                           int32_t *out, cudaStream_t st);
 
@@ -210,13 +201,18 @@ cudaError_t launch_mixed_residual(int K, bool bf16u, bool last, bool project, co
 cudaError_t launch_mixed_sweep(int K, bool bf16u, bool last, bool project, const SellView &A, const Coeffs &cf,
                                const void *e_src, const void *r, void *e_dst, const float *u, float *u_out,
                                cudaStream_t st);
-// the instances for the unnormalized Laplacian (mixed_kernels_un.cu)
-cudaError_t launch_mixed_residual_un(int K, bool bf16u, bool last, bool project, const SellView &A,
-                                     const Coeffs &cf, const float *u, void *r, void *e, float *u_out,
-                                     cudaStream_t st);
-cudaError_t launch_mixed_sweep_un(int K, bool bf16u, bool last, bool project, const SellView &A,
-                                  const Coeffs &cf, const void *e_src, const void *r, void *e_dst, const float *u,
-                                  float *u_out, cudaStream_t st);
+// the instance sets (mixed_kernels*.cu): L_s or L = D - W, FP16 or BF16 e
+#define PDCA_MIXED_DECL(NAME)                                                                                    \
+    cudaError_t NAME##_residual(int K, bool last, bool project, const SellView &A, const Coeffs &cf,             \
+                                const float *u, void *r, void *e, float *u_out, cudaStream_t st);               \
+    cudaError_t NAME##_sweep(int K, bool last, bool project, const SellView &A, const Coeffs &cf,                \
+                             const void *e_src, const void *r, void *e_dst, const float *u, float *u_out,        \
+                             cudaStream_t st);
+PDCA_MIXED_DECL(mixed_ls_f16)
+PDCA_MIXED_DECL(mixed_ls_b16)
+PDCA_MIXED_DECL(mixed_un_f16)
+PDCA_MIXED_DECL(mixed_un_b16)
+#undef PDCA_MIXED_DECL
 cudaError_t launch_permute_out(int K, int32_t n, const float *u, const int32_t *perm,
                                float *out, cudaStream_t st);
 cudaError_t launch_permute_in(int K, int32_t n, int32_t n_pad, const float *in,
@@ -271,7 +267,11 @@ struct BatchOvTable {
 cudaError_t launch_batch_overflow(int K, const BatchOvTable &t, cudaStream_t st);
 // un: the table holds problems on the unnormalized Laplacian (A.self set).
 cudaError_t launch_batch_pass(int K, bool un, const BatchTable &t, cudaStream_t st);
-cudaError_t launch_batch_pass_un(int K, const BatchTable &t, cudaStream_t st);
+// the instance sets (batch_kernels*.cu): L_s or L, K <= 8 or K > 8
+cudaError_t batch_pass_ls_lo(int K, const BatchTable &t, cudaStream_t st);
+cudaError_t batch_pass_ls_hi(int K, const BatchTable &t, cudaStream_t st);
+cudaError_t batch_pass_un_lo(int K, const BatchTable &t, cudaStream_t st);
+cudaError_t batch_pass_un_hi(int K, const BatchTable &t, cudaStream_t st);
 
 // --- preparation (prep_kernels.cu) -----------------------------------------
 // status[0]: kBadGraph | kNotSymmetric | kIsolated bits; status[2..3]: the

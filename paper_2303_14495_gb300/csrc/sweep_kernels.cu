@@ -46,14 +46,16 @@ using namespace dev;
 // consecutive slices (32 = one renumbering block of 1024 rows at the usual
 // iters = 4) and its warps take them from a shared queue (the same slice
 // body as the batched kernel)
-template <int K, bool PROJECT, bool UN>
+// (OV: the problem has split rows whose overflow sums a pre-pass formed)
+template <int K, bool PROJECT, bool UN, bool OV>
 __global__ void __launch_bounds__(kBlockThreads, PDCA_SWEEP_MIN_BLOCKS)
 sweep_kernel(const SellView A, const Coeffs cf, const float *__restrict__ v_src,
              const float *__restrict__ u_t, float *__restrict__ v_dst, int iters) {
     __shared__ int next_slot;
     const int count = kWarpsPerBlock * iters;
     for_block_slices_fmt(A, blockIdx.x * count, count, &next_slot, [&](int slice, auto fmt) {
-        fp32_sweep_slice<K, PROJECT, UN, decltype(fmt)::value>(A, cf, slice, threadIdx.x & 31, v_src, u_t, v_dst);
+        fp32_sweep_slice<K, PROJECT, UN, decltype(fmt)::value, OV>(A, cf, slice, threadIdx.x & 31, v_src, u_t,
+                                                                   v_dst);
     });
 }
 
@@ -441,13 +443,17 @@ cudaError_t sweep_k(bool project, const SellView &A, const TileView *T, const Co
     const int groups = (A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const int iters = sweep_iters(A.n_slices);
     const int blocks = (groups + iters - 1) / iters;
+    const bool ov = A.ov_index != nullptr;
+#define PDCA_SWEEP(PR, UNL, OVL) \
+    sweep_kernel<K, PR, UNL, OVL><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst, iters)
     if (A.self) {
-        if (project && P) sweep_kernel<K, P, true><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst, iters);
-        else sweep_kernel<K, false, true><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst, iters);
+        if (project && P) { if (ov) PDCA_SWEEP(P, true, true); else PDCA_SWEEP(P, true, false); }
+        else { if (ov) PDCA_SWEEP(false, true, true); else PDCA_SWEEP(false, true, false); }
     } else {
-        if (project && P) sweep_kernel<K, P, false><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst, iters);
-        else sweep_kernel<K, false, false><<<blocks, kBlockThreads, 0, st>>>(A, cf, v_src, u_t, v_dst, iters);
+        if (project && P) { if (ov) PDCA_SWEEP(P, false, true); else PDCA_SWEEP(P, false, false); }
+        else { if (ov) PDCA_SWEEP(false, false, true); else PDCA_SWEEP(false, false, false); }
     }
+#undef PDCA_SWEEP
     return cudaGetLastError();
 }
 

@@ -173,15 +173,17 @@ def test_tiling_with_oversized_halos(B):
     """gmm70k (K = 10, no spatial locality): most tile halos exceed the shared
     memory budget; AUTO uses the plain kernels, ON still tiles (oversized
     tiles gather through their halo lists) and gives the same bits as the
-    plain kernels with int32 columns (whose entries keep the tiled form's
-    order; 16-bit columns band the entries of rows that reach the second
-    65536-node chunk)."""
+    plain kernels with int32 columns and whole rows (whose entries keep the
+    tiled form's order; 16-bit columns band the entries of rows that reach
+    the second 65536-node chunk, and the automatic split length moves the
+    hub rows' tails to the overflow CSR)."""
     wl = make_workload("gmm70k")
     g = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels,
                   B.params_from_workload(wl.params))
     assert not g.layout()["tiled"]
     g = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels,
-                  B.params_from_workload(wl.params, columns=B.PDCA_COLUMNS_32))
+                  B.params_from_workload(wl.params, columns=B.PDCA_COLUMNS_32, row_split=2044))
+    assert g.layout()["split_rows"] == 0      # whole rows, as in the tiled form
     t = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels,
                   B.params_from_workload(wl.params, tiling=2))
     assert t.layout()["tiled"]
