@@ -351,37 +351,51 @@ def run_reference(args, wl, world, rank):
 def run_serving(args, local):
     """Serving under mixed load: the same seeded request mix served by
     continuous batching in mixed precision and by sequential per-problem
-    FP32 solves, on prepared (resident) graph operators."""
+    FP32 solves, on prepared (resident) graph operators, at two arrival
+    rates.  The batching loop's slot count and passes per tick are tuned on
+    a mix of the same size and rate drawn with another seed."""
     import torch
     from gen import serving_mix
     from paper_2303_14495_gb300 import binding as B, serving
     t0 = time.perf_counter()
     pool = serving_mix.templates(device=f"cuda:{local}")
-    reqs = serving_mix.requests(pool, n_requests=args.serving_requests, rate=args.serving_rate)
+    t_pool = time.perf_counter() - t0
     stream = torch.cuda.Stream()
     bm = serving.prepare(pool, B.PDCA_MIXED_BF16W_FP16U, stream)
     bf = serving.prepare(pool, B.PDCA_FP32, stream)
-    serving.serve_batched(bm, reqs[:32], max_slots=16)           # warm-up
-    serving.serve_sequential(bf, reqs[:8])
+    warm = serving_mix.requests(pool, n_requests=32, rate=args.serving_rate, seed=11)
+    serving.serve_batched(bm, warm, max_slots=16)           # warm-up
+    serving.serve_sequential(bf, warm[:8])
     tuned = None
     slots, ppt = args.serving_slots, 4
     if not args.no_autotune:
-        # slots and passes per tick from a replay of the first 128 requests
         from paper_2303_14495_gb300 import autotune
-        pick, table = autotune.tune_serving(bm, reqs[:128], slots=(32, 64, 128), passes=(2, 4, 8))
+        sample = serving_mix.requests(pool, n_requests=args.serving_requests, rate=args.serving_rate, seed=12)
+        pick, table = autotune.tune_serving(bm, sample, slots=(32, 64, 128), passes=(2, 4, 8))
         slots, ppt = pick["max_slots"], pick["passes_per_tick"]
-        tuned = {"pick": pick, "sample": "first 128 requests of the mix",
+        tuned = {"pick": pick, "sample": (f"{len(sample)} requests at {args.serving_rate:g}/s drawn with another "
+                                          f"seed (same sizes, kinds and rate as the measured mix)"),
                  "table": [{k: r[k] for k in ("max_slots", "passes_per_tick", "problems_per_s", "p50_ms", "p99_ms")}
                            for r in table]}
-    batched, _ = serving.serve_batched(bm, reqs, max_slots=slots, passes_per_tick=ppt)
-    seq, _ = serving.serve_sequential(bf, reqs)
+    rates = {}
+    for rate in sorted({args.serving_rate_low, args.serving_rate}):
+        reqs = serving_mix.requests(pool, n_requests=args.serving_requests, rate=rate)
+        batched, _ = serving.serve_batched(bm, reqs, max_slots=slots, passes_per_tick=ppt)
+        seq, _ = serving.serve_sequential(bf, reqs)
+        rates[f"{rate:g}/s"] = {"batched_mixed": dict(batched.summary(), max_slots=slots, passes_per_tick=ppt),
+                                "sequential_fp32": seq.summary()}
+    main = rates[f"{args.serving_rate:g}/s"]
+    pts = [f"{n}x{d}" for n, d in serving_mix.POINT_SIZES]
     return {
-        "mix": (f"{len(reqs)} Poisson requests at {args.serving_rate:g}/s; image graphs (window k-NN, 3x3 "
-                f"patches) and Gaussian-mixture k-NN graphs alternating; N log-uniform in [4Ki, 1Mi] mapped "
-                f"to {len(pool)} resident graph templates; K in {{2, 5, 10}}"),
-        "batched_mixed": dict(batched.summary(), max_slots=slots, passes_per_tick=ppt),
-        "sequential_fp32": seq.summary(),
+        "mix": (f"{args.serving_requests} Poisson requests per rate; image graphs (window k-NN, 3x3 patches, "
+                f"{serving_mix.IMAGE_SIDES[0]}^2 to {serving_mix.IMAGE_SIDES[-1]}^2 pixels) and Gaussian-mixture "
+                f"k-NN graphs (points x dims: {', '.join(pts)}) alternating; N log-uniform in [4Ki, 1Mi] mapped to "
+                f"the nearest of {len(pool)} resident graph templates; K in {{2, 5, 10}}"),
+        "batched_mixed": main["batched_mixed"],
+        "sequential_fp32": main["sequential_fp32"],
+        "rates": rates,
         "autotune": tuned,
+        "template_build_s": t_pool,
         "wall_s": time.perf_counter() - t0,
     }
 
@@ -568,6 +582,16 @@ def run_ours(args, wl, world, rank, local):
         tuned_layout = {"pick": next(r["name"] for r in table if r.get("params") == best),
                         "table": [{"name": r["name"], "ms_per_sweep": r.get("ms_per_sweep"),
                                    "create_ms": r.get("create_ms"), "refused": r.get("refused")} for r in table]}
+        # the kernel shape on the chosen layout, and the inner sweep count
+        best_s, table_s = autotune.tune_shape(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, best,
+                                              sweeps=p["inner"], repeats=3, device=dev)
+        tuned_layout["shape"] = {"pick": next(r["name"] for r in table_s if r.get("params") == best_s),
+                                 "table": [{"name": r["name"], "ms_per_sweep": r.get("ms_per_sweep"),
+                                            "refused": r.get("refused")} for r in table_s]}
+        prm_s = B.make_params(**best_s)
+        make = lambda: B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm_s, device=dev)
+        m_best, table_m = autotune.tune_sweeps(make, candidates=(2, 4, 8), target=1e-3, max_outer=32)
+        tuned_layout["inner_sweeps"] = {"pick": m_best, "target_rel_residual": 1e-3, "table": table_m}
         torch.cuda.synchronize(dev)
 
     cpu = None
@@ -654,6 +678,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=512)
     ap.add_argument("--serving-rate", type=float, default=1000.0)
+    ap.add_argument("--serving-rate-low", type=float, default=500.0,
+                    help="second arrival rate, below the batched form's capacity")
     ap.add_argument("--serving-slots", type=int, default=64)
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the layout and serving autotuners (informational sections)")

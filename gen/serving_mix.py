@@ -46,9 +46,10 @@ class Request:
 
 
 IMAGE_SIDES = (64, 128, 256, 512, 1024)           # 4 Ki .. 1 Mi pixels
-# point clouds stop at 256 Ki nodes: an exact k-NN graph of 1 Mi points costs
-# minutes to build, so requests above that reuse the 256 Ki template
-POINT_SIZES = ((4096, 256), (16384, 128), (65536, 64), (262144, 64))
+# point clouds from 4 Ki to 1 Mi points, dims from 784 (the small ones) down
+# to 64 (the largest: an exact k-NN graph of 1 Mi points in 784 dims would
+# cost minutes to build for every run)
+POINT_SIZES = ((4096, 784), (16384, 784), (65536, 256), (262144, 128), (1048576, 64))
 
 
 def _image_template(side: int, device: str) -> Template:
@@ -61,7 +62,7 @@ def _image_template(side: int, device: str) -> Template:
 def _point_template(n: int, dim: int, device: str) -> Template:
     rng = np.random.default_rng(SEED_BASE + 60 + n)
     X, gt = gmm_points(n // 10, 10, dim, 0.15, rng)
-    rp, col, w = knn_graph_points(X, 10, 7, device=device, chunk=4096)
+    rp, col, w = knn_graph_points(X, 10, 7, device=device, chunk=4096 if n <= 262144 else 2048)
     return Template("points", X.shape[0], rp, col, w, gt)
 
 
@@ -72,7 +73,7 @@ def templates(device: str = "cpu", max_n: int = 1 << 20, cache: bool = True) -> 
     specs = [("image", s, 0) for s in IMAGE_SIDES if s * s <= max_n] + \
             [("points", n, d) for n, d in POINT_SIZES if n <= max_n]
     for kind, a, b in specs:
-        path = os.path.join(_cache_dir(), f"serving_{kind}_{a}_{b}_v2.npz")
+        path = os.path.join(_cache_dir(), f"serving_{kind}_{a}_{b}_v3.npz")
         if cache and os.path.exists(path):
             z = np.load(path)
             out.append(Template(kind, int(z["n"]), z["row_ptr"], z["col"], z["w"], z["gt"]))

@@ -284,10 +284,11 @@ def knn_graph_points(X: np.ndarray, k: int, scale_nn: int = 7, chunk: int = 2048
         cand.sort(axis=1)
         diff = Xd[cand] - Xd[s:e, None, :]
         exact = np.einsum("rcd,rcd->rc", diff, diff)
-        for r in range(e - s):
-            order = np.lexsort((cand[r], exact[r]))[:k]
-            nbr[s + r] = cand[r][order]
-            nd2[s + r] = exact[r][order]
+        # candidates ascending in index, so a stable sort by distance breaks
+        # ties by the lower index
+        order = np.argsort(exact, axis=1, kind="stable")[:, :k]
+        nbr[s:e] = np.take_along_axis(cand, order, axis=1)
+        nd2[s:e] = np.take_along_axis(exact, order, axis=1)
     sig = np.sqrt(nd2[:, scale_nn - 1])
     src = np.repeat(np.arange(n, dtype=np.int64), k)
     dst = nbr.reshape(-1)

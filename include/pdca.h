@@ -191,6 +191,11 @@ typedef struct {
                             multiple of 4, at most 2044.  Rows longer than 2044 are
                             always split.  Arithmetic: the row's overflow sum is
                             added after its sliced entries                          */
+    int32_t block_slices;/* slices one block of the plain sweep, energy and mixed
+                            kernels takes from its queue: 8, 16 or 32 (a launch
+                            shape; sums are formed the same way), 0 = automatic
+                            (32 on large graphs, fewer when the graph is too
+                            small to keep every SM busy for several waves)    */
 } pdca_params;
 
 typedef struct pdca_problem pdca_problem;

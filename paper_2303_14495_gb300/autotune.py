@@ -6,6 +6,15 @@ library's sweep profiler (CUDA events around every sweep launch) and returns
 the fastest parameters.  Layouts change the order of the floating-point sums
 only, so every candidate solves the same problem.
 
+``tune_shape`` then times the kernels' own shape on the chosen layout: the
+column format (16-bit where it fits, or int32), the slices one block takes
+from its queue (8, 16 or 32) and the split length of long rows.
+
+``tune_sweeps`` picks the number of inner sweeps per outer step: for each
+candidate it counts the outer steps needed to bring the relative residual of
+the DCA system down to a target, times them, and keeps the candidate with
+the largest residual reduction per millisecond.
+
 ``tune_serving`` replays a sample of a request mix through the continuous
 batching loop for each (slot count, passes per tick) pair and returns the
 pair with the lowest p99 latency among those within 5% of the best
@@ -36,6 +45,19 @@ DEFAULT_LAYOUTS: List[Tuple[str, dict]] = [
     ("caller order, auto window", dict(reorder=B.PDCA_REORDER_NONE, sort_window=0, tiling=B.PDCA_TILING_OFF,
                                        entry_order=B.PDCA_ENTRIES_SPREAD)),
 ]
+
+
+def shape_candidates(max_degree: int) -> List[Tuple[str, dict]]:
+    """Kernel-shape candidates: column format x slices per block range, and,
+    on graphs with rows longer than 64 entries, a split length of 64."""
+    out = []
+    for cols, cname in ((B.PDCA_COLUMNS_AUTO, "16-bit columns"), (B.PDCA_COLUMNS_32, "int32 columns")):
+        for bs in (32, 16, 8):
+            out.append((f"{cname}, {bs} slices per block", dict(columns=cols, block_slices=bs)))
+    if max_degree > 64:
+        out.append(("16-bit columns, 32 slices per block, split at 64",
+                    dict(columns=B.PDCA_COLUMNS_AUTO, block_slices=32, row_split=64)))
+    return out
 
 
 def tune_layout(row_ptr, col, w, K, fid_mask, fid_labels, base: dict,
@@ -80,6 +102,55 @@ def tune_layout(row_ptr, col, w, K, fid_mask, fid_labels, base: dict,
     if not timed:
         raise ValueError("tune_layout: the library refused every candidate layout for these parameters")
     return timed[0]["params"], timed + [r for r in rows if "refused" in r]
+
+
+def tune_shape(row_ptr, col, w, K, fid_mask, fid_labels, base: dict, sweeps: int = 8, repeats: int = 3,
+               device="cuda"):
+    """Fastest kernel shape for this graph on the layout in ``base``; same
+    return form as ``tune_layout``."""
+    import numpy as np
+    max_degree = int(np.max(np.diff(np.asarray(row_ptr)))) if len(row_ptr) > 1 else 0
+    return tune_layout(row_ptr, col, w, K, fid_mask, fid_labels, base, candidates=shape_candidates(max_degree),
+                       sweeps=sweeps, repeats=repeats, device=device)
+
+
+def tune_sweeps(make_problem, candidates: Sequence[int] = (2, 4, 5, 8, 10), target: float = 1e-3,
+                max_outer: int = 200):
+    """Inner sweeps per outer step by residual reduction per millisecond.
+
+    ``make_problem()`` returns a fresh ``binding.Problem``.  For each
+    candidate m the problem runs outer steps of m sweeps (one CUDA-event
+    timed ``solve`` with per-step traces) until the relative residual
+    ||b^t - T u^{t+1}|| / ||b^t|| of an outer step falls below ``target`` or
+    ``max_outer`` steps are spent.  Returns (best m, table); the table has,
+    per m, the outer steps used, the milliseconds and -log10(residual
+    reduction) per millisecond."""
+    import math
+    import torch
+    table = []
+    for m in candidates:
+        g = make_problem()
+        g.solve(1, m)                       # warm-up (also the first residual)
+        g.set_u(None)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(g.stream)
+        _, r = g.solve(max_outer, m, trace=True)
+        e1.record(g.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        r = [float(x) for x in r]
+        hit = next((i for i, x in enumerate(r) if x <= target), len(r) - 1)
+        ms_to = ms * (hit + 1) / max(len(r), 1)
+        gain = -math.log10(max(r[hit], 1e-300) / max(r[0], 1e-300)) if r[0] > 0 else 0.0
+        table.append({"inner": int(m), "outer_steps": hit + 1, "reached": r[hit], "ms": ms_to,
+                      "decades_per_ms": gain / max(ms_to, 1e-9)})
+        g.close()
+    ok = [t for t in table if t["reached"] <= target] or table
+    best = min(ok, key=lambda t: t["ms"]) if any(t["reached"] <= target for t in table) else \
+        max(table, key=lambda t: t["decades_per_ms"])
+    return best["inner"], table
 
 
 def tune_serving(bases, requests, precision: int = B.PDCA_MIXED_BF16W_FP16U,

@@ -67,7 +67,7 @@ class pdca_params(C.Structure):
         ("power_iters", C.c_int32), ("precision", C.c_int32),
         ("sort_window", C.c_int32), ("reorder", C.c_int32), ("tiling", C.c_int32),
         ("entry_order", C.c_int32), ("step_k", C.c_double), ("columns", C.c_int32),
-        ("row_split", C.c_int32),
+        ("row_split", C.c_int32), ("block_slices", C.c_int32),
     ]
 
 
@@ -156,7 +156,7 @@ def make_params(eps=1.0, c=3.0, eta=1.0, precond=PDCA_JACOBI_PERTURBED, damping=
                 lambda_max=0.0, power_iters=150, laplacian=PDCA_LAP_NORMALIZED,
                 precision=PDCA_FP32, sort_window=0, reorder=PDCA_REORDER_BFS,
                 tiling=PDCA_TILING_AUTO, step_k=0.0, entry_order=PDCA_ENTRIES_SPREAD,
-                columns=PDCA_COLUMNS_AUTO, row_split=0) -> pdca_params:
+                columns=PDCA_COLUMNS_AUTO, row_split=0, block_slices=0) -> pdca_params:
     p = pdca_params()
     lib().pdca_default_params(C.byref(p))
     p.eps, p.c, p.eta = float(eps), float(c), float(eta)
@@ -167,6 +167,7 @@ def make_params(eps=1.0, c=3.0, eta=1.0, precond=PDCA_JACOBI_PERTURBED, damping=
     p.entry_order = int(entry_order)
     p.columns = int(columns)
     p.row_split = int(row_split)
+    p.block_slices = int(block_slices)
     return p
 
 

@@ -38,7 +38,7 @@ mixed_sweep_kernel(const SellView A, const Coeffs cf, const HT *__restrict__ e_s
 template <int K, class HT, bool UN, bool OV>
 cudaError_t residual_ku(bool last, bool project, const SellView &A, const Coeffs &cf, const float *u, void *r,
                         void *e, float *u_out, cudaStream_t st) {
-    const int iters = sweep_iters(A.n_slices);
+    const int iters = view_iters(A);
     const int blocks = (A.n_slices + kWarpsPerBlock * iters - 1) / (kWarpsPerBlock * iters);
     float *rh = static_cast<float *>(r);
     HT *eh = static_cast<HT *>(e);
@@ -55,7 +55,7 @@ cudaError_t residual_ku(bool last, bool project, const SellView &A, const Coeffs
 template <int K, class HT, bool UN, bool OV>
 cudaError_t sweep_ku(bool last, bool project, const SellView &A, const Coeffs &cf, const void *e_src,
                      const void *r, void *e_dst, const float *u, float *u_out, cudaStream_t st) {
-    const int iters = sweep_iters(A.n_slices);
+    const int iters = view_iters(A);
     const int blocks = (A.n_slices + kWarpsPerBlock * iters - 1) / (kWarpsPerBlock * iters);
     const HT *es = static_cast<const HT *>(e_src);
     const float *rh = static_cast<const float *>(r);

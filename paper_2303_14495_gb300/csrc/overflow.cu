@@ -6,7 +6,7 @@
 // hundred entries) is as slow as its longest row.  Past the split length the
 // entries are kept in a CSR of their own, and this pre-pass reduces each
 // such row with one warp: the lanes take consecutive entries (coalesced
-// column and weight loads, two gathers in flight per lane), then a fixed
+// column and weight loads, four gathers in flight per lane), then a fixed
 // butterfly of shuffles adds the 32 partial sums.  The result, K floats per
 // row, is added by the sweep-like kernel that runs next (add_overflow), after
 // the row's sliced entries.  Fixed assignment and fixed summation order:
@@ -36,16 +36,20 @@ __device__ __forceinline__ void ov_row_sum(const OverflowView &O, int wkind, int
     for (int k = 0; k < K; ++k) acc[k] = 0.0f;
     const int64_t e0 = O.rp[q], e1 = O.rp[q + 1];
     int64_t e = e0 + lane;
-    for (; e + 32 < e1; e += 64) {
-        const int32_t ca = __ldg(O.col + e), cb = __ldg(O.col + e + 32);
-        const float wa = ov_weight(O, wkind, e), wb = ov_weight(O, wkind, e + 32);
-        float ra[K], rb[K];
-        load_row_t<K, XT>(x + (size_t)ca * K, ra);
-        load_row_t<K, XT>(x + (size_t)cb * K, rb);
-        fma_row<K>(acc, wa, ra);
-        fma_row<K>(acc, wb, rb);
+    for (; e + 96 < e1; e += 128) {   // four gathers in flight per lane
+        int32_t c[4];
+        float wv[4], rr[4][K];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            c[m] = __ldg(O.col + e + 32 * m);
+            wv[m] = ov_weight(O, wkind, e + 32 * m);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) load_row_t<K, XT>(x + (size_t)c[m] * K, rr[m]);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) fma_row<K>(acc, wv[m], rr[m]);
     }
-    if (e < e1) {
+    for (; e < e1; e += 32) {
         const int32_t ca = __ldg(O.col + e);
         const float wa = ov_weight(O, wkind, e);
         float ra[K];

@@ -139,6 +139,8 @@ pdca_status check_params(const pdca_params &p) {
     if (p.entry_order != PDCA_ENTRIES_SPREAD && p.entry_order != PDCA_ENTRIES_CSR) return PDCA_ERR_INVALID_ARG;
     if (p.columns != PDCA_COLUMNS_AUTO && p.columns != PDCA_COLUMNS_32) return PDCA_ERR_INVALID_ARG;
     if (p.row_split < 0) return PDCA_ERR_INVALID_ARG;
+    if (p.block_slices != 0 && p.block_slices != 8 && p.block_slices != 16 && p.block_slices != 32)
+        return PDCA_ERR_INVALID_ARG;
     return PDCA_OK;
 }
 
@@ -437,6 +439,7 @@ struct pdca_problem {
         A.n = L.n;
         // three n_pad x K FP32 iterates above half of the 129 MB L2
         A.stream_rows = 3.0 * 4.0 * (double)L.n_pad * (double)L.K > 64.0 * (1 << 20) ? 1 : 0;
+        A.block_iters = prm.block_slices / kWarpsPerBlock;   // 0: automatic
         return A;
     }
     int spare() const { return has_prev ? 3 - cur - prev : (cur + 1) % 3; }
@@ -853,6 +856,7 @@ void pdca_default_params(pdca_params *p) {
     p->step_k = 0.0;
     p->columns = PDCA_COLUMNS_AUTO;
     p->row_split = 0;
+    p->block_slices = 0;
 }
 
 const char *pdca_status_string(pdca_status s) {

@@ -76,6 +76,7 @@ struct SellView {
     int32_t n_slices;
     int32_t n;                 // real rows; rows >= n are padding
     int32_t stream_rows;       // 1: the iterates exceed L2, store rows with st.global.cs
+    int32_t block_iters;       // slice groups of 8 per block range (1, 2, 4); 0 = sweep_iters(n_slices)
 };
 
 // The overflow CSR of the rows longer than the split length (entries past
@@ -112,6 +113,8 @@ inline int sweep_iters(int32_t n_slices) {
     return it >= 4 && PDCA_SWEEP_MAX_ITERS >= 4 ? 4 : (it >= 2 && PDCA_SWEEP_MAX_ITERS >= 2 ? 2 : 1);
 }
 static_assert(PDCA_SWEEP_MAX_ITERS * 8 <= kFmtGroupSlices, "a queue range must fit in one format group");
+// the block range of a problem's queue kernels (a layout choice, pdca_params.block_slices)
+inline int view_iters(const SellView &A) { return A.block_iters > 0 ? A.block_iters : sweep_iters(A.n_slices); }
 
 // Tiled form of the operator: tiles of kTileSlices slices; each tile lists
 // the distinct rows its entries reference (its halo, sorted), and every entry
@@ -218,9 +221,9 @@ cudaError_t launch_permute_out(int K, int32_t n, const float *u, const int32_t *
 cudaError_t launch_permute_in(int K, int32_t n, int32_t n_pad, const float *in,
                               const int32_t *perm, float *u, cudaStream_t st);
 int energy_blocks(int32_t n_slices);
-// blocks of the kernels whose block takes sweep_iters() groups of 8 slices
+// blocks of the kernels whose block takes view_iters() groups of 8 slices
 // from a queue (<= energy_blocks)
-int queue_blocks(int32_t n_slices);
+int queue_blocks(const SellView &A);
 
 // --- batched passes (batch_kernels.cu) -------------------------------------
 // One problem's pass inside a batched launch.  A launch advances every

@@ -441,7 +441,7 @@ cudaError_t sweep_k(bool project, const SellView &A, const TileView *T, const Co
     }
     // keep at least 4 waves of resident blocks
     const int groups = (A.n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    const int iters = sweep_iters(A.n_slices);
+    const int iters = view_iters(A);
     const int blocks = (groups + iters - 1) / iters;
     const bool ov = A.ov_index != nullptr;
 #define PDCA_SWEEP(PR, UNL, OVL) \
@@ -466,8 +466,8 @@ cudaError_t energy_k(const SellView &A, const TileView *T, const Coeffs &cf, con
         if (e != cudaSuccess) return e;
         energy_tiled_kernel<K><<<T->n_tiles, kTileThreads, sm, st>>>(A, *T, cf, u, u_prev, partials);
     } else {
-        const int iters = sweep_iters(A.n_slices);
-        energy_kernel<K><<<queue_blocks(A.n_slices), kBlockThreads, 0, st>>>(A, cf, u, u_prev, partials, iters);
+        const int iters = view_iters(A);
+        energy_kernel<K><<<queue_blocks(A), kBlockThreads, 0, st>>>(A, cf, u, u_prev, partials, iters);
     }
     return cudaGetLastError();
 }
@@ -482,12 +482,12 @@ cudaError_t labels_k(int32_t n, const float *u, const int32_t *perm, int32_t *ou
 
 int energy_blocks(int32_t n_slices) { return (n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock; }
 
-int queue_blocks(int32_t n_slices) {
-    const int per_block = kWarpsPerBlock * sweep_iters(n_slices);
-    return (n_slices + per_block - 1) / per_block;
+int queue_blocks(const SellView &A) {
+    const int per_block = kWarpsPerBlock * view_iters(A);
+    return (A.n_slices + per_block - 1) / per_block;
 }
 
-int reduce_parts(const SellView &A, const TileView *T) { return T ? T->n_tiles : queue_blocks(A.n_slices); }
+int reduce_parts(const SellView &A, const TileView *T) { return T ? T->n_tiles : queue_blocks(A); }
 
 
 #define PDCA_DISPATCH_K(K, CALL)                                                      \
@@ -544,8 +544,8 @@ cudaError_t launch_power_spmv(const SellView &A, const TileView *T, const float 
         power_spmv_tiled_kernel<<<T->n_tiles, kTileThreads, sm, st>>>(A, *T, x, scale, y, partials, ticket,
                                                                         lambda);
     } else {
-        const int iters = sweep_iters(A.n_slices);
-        const int blocks = queue_blocks(A.n_slices);
+        const int iters = view_iters(A);
+        const int blocks = queue_blocks(A);
         power_spmv_kernel<<<blocks, kBlockThreads, 0, st>>>(A, x, scale, y, partials, ticket, lambda, iters);
     }
     return cudaGetLastError();

@@ -64,3 +64,43 @@ def test_tune_serving(B):
     row = next(r for r in table if (r["max_slots"], r["passes_per_tick"]) == (pick["max_slots"],
                                                                               pick["passes_per_tick"]))
     assert row["problems_per_s"] >= 0.95 * best_tp
+
+
+def test_tune_shape_and_block_ranges(B):
+    """The shape tuner times every candidate; slices per block range change
+    the launch only, so the iterates are the same bits for 8, 16 and 32."""
+    from paper_2303_14495_gb300 import autotune
+    wl = make_workload("gmm70k", n_per=2000, dim=64)      # hub rows: the split candidate is offered
+    p = wl.params
+    base = dict(eps=p["eps"], c=p["c"], eta=p["eta"], precond=p["precond"], damping=p["damping"] or 0.5)
+    best, table = autotune.tune_shape(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, base,
+                                      sweeps=4, repeats=2)
+    timed = [r for r in table if "ms_per_sweep" in r]
+    maxdeg = int(np.max(np.diff(wl.row_ptr)))
+    assert len(timed) == len(autotune.shape_candidates(maxdeg))
+    assert best == timed[0]["params"]
+    us = []
+    for bs in (8, 16, 32):
+        g = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels,
+                      B.params_from_workload(p, block_slices=bs))
+        g.solve(3, 5)
+        us.append(g.get_u())
+    np.testing.assert_array_equal(us[0], us[1])
+    np.testing.assert_array_equal(us[0], us[2])
+    with pytest.raises(B.PdcaError, match="INVALID_ARG"):
+        B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels,
+                  B.params_from_workload(p, block_slices=12))
+
+
+def test_tune_sweeps(B):
+    """Inner sweep counts by residual reduction per millisecond: every
+    candidate is timed, the pick reaches the target residual."""
+    from paper_2303_14495_gb300 import autotune
+    wl = make_workload("ellipses256", size=96)
+    p = wl.params
+    prm = B.params_from_workload(p)
+    make = lambda: B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm)
+    m, table = autotune.tune_sweeps(make, candidates=(2, 5, 10), target=1e-2, max_outer=60)
+    assert [t["inner"] for t in table] == [2, 5, 10]
+    row = next(t for t in table if t["inner"] == m)
+    assert row["reached"] <= 1e-2 and all(t["ms"] > 0 for t in table)
