@@ -11,9 +11,9 @@ column format (16-bit where it fits, or int32), the slices one block takes
 from its queue (8, 16 or 32) and the split length of long rows.
 
 ``tune_sweeps`` picks the number of inner sweeps per outer step: for each
-candidate it counts the outer steps needed to bring the relative residual of
-the DCA system down to a target, times them, and keeps the candidate with
-the largest residual reduction per millisecond.
+candidate it finds the number of outer steps that brings the iterate within
+a relative distance of a long reference solve, times that solve, and keeps
+the candidate that gets there first.
 
 ``tune_serving`` replays a sample of a request mix through the continuous
 batching loop for each (slot count, passes per tick) pair and returns the
@@ -115,41 +115,52 @@ def tune_shape(row_ptr, col, w, K, fid_mask, fid_labels, base: dict, sweeps: int
 
 
 def tune_sweeps(make_problem, candidates: Sequence[int] = (2, 4, 5, 8, 10), target: float = 1e-3,
-                max_outer: int = 200):
-    """Inner sweeps per outer step by residual reduction per millisecond.
+                max_outer: int = 64, ref_outer: int = 256):
+    """Inner sweeps per outer step by time to the solution.
 
-    ``make_problem()`` returns a fresh ``binding.Problem``.  For each
-    candidate m the problem runs outer steps of m sweeps (one CUDA-event
-    timed ``solve`` with per-step traces) until the relative residual
-    ||b^t - T u^{t+1}|| / ||b^t|| of an outer step falls below ``target`` or
-    ``max_outer`` steps are spent.  Returns (best m, table); the table has,
-    per m, the outer steps used, the milliseconds and -log10(residual
-    reduction) per millisecond."""
+    ``make_problem()`` returns a fresh ``binding.Problem``.  A reference
+    iterate u* comes from ``ref_outer`` outer steps with the largest
+    candidate.  For each candidate m the problem is solved from u^0 with
+    T = 1, 2, 4, ... outer steps (each solve timed with CUDA events) until
+    ||u^T - u*|| / ||u*|| <= ``target`` or T exceeds ``max_outer``.  Returns
+    (m with the shortest time to the target, table); the table has, per m,
+    the outer steps, the milliseconds of that solve, the error reached and
+    the decades of error reduced per millisecond."""
     import math
+    import numpy as np
     import torch
+    g = make_problem()
+    g.solve(ref_outer, max(candidates))
+    u_ref = g.get_u().astype(np.float64)
+    g.close()
+    nrm = max(float(np.linalg.norm(u_ref)), 1e-300)
     table = []
     for m in candidates:
         g = make_problem()
-        g.solve(1, m)                       # warm-up (also the first residual)
-        g.set_u(None)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(g.stream)
-        _, r = g.solve(max_outer, m, trace=True)
-        e1.record(g.stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        r = [float(x) for x in r]
-        hit = next((i for i, x in enumerate(r) if x <= target), len(r) - 1)
-        ms_to = ms * (hit + 1) / max(len(r), 1)
-        gain = -math.log10(max(r[hit], 1e-300) / max(r[0], 1e-300)) if r[0] > 0 else 0.0
-        table.append({"inner": int(m), "outer_steps": hit + 1, "reached": r[hit], "ms": ms_to,
-                      "decades_per_ms": gain / max(ms_to, 1e-9)})
+        e0_err = float(np.linalg.norm(g.get_u().astype(np.float64) - u_ref)) / nrm
+        g.solve(1, m)                       # warm-up
+        row = None
+        T = 1
+        while T <= max_outer:
+            g.set_u(None)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(g.stream)
+            g.solve(T, m)
+            b.record(g.stream)
+            torch.cuda.synchronize()
+            err = float(np.linalg.norm(g.get_u().astype(np.float64) - u_ref)) / nrm
+            ms = a.elapsed_time(b)
+            row = {"inner": int(m), "outer_steps": T, "ms": ms, "rel_error": err,
+                   "decades_per_ms": math.log10(max(e0_err, 1e-300) / max(err, 1e-300)) / max(ms, 1e-9)}
+            if err <= target:
+                break
+            T *= 2
         g.close()
-    ok = [t for t in table if t["reached"] <= target] or table
-    best = min(ok, key=lambda t: t["ms"]) if any(t["reached"] <= target for t in table) else \
-        max(table, key=lambda t: t["decades_per_ms"])
+        table.append(row)
+    hit = [t for t in table if t["rel_error"] <= target]
+    best = min(hit, key=lambda t: t["ms"]) if hit else max(table, key=lambda t: t["decades_per_ms"])
     return best["inner"], table
 
 
