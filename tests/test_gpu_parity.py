@@ -70,7 +70,8 @@ def run_parity(gpu, ref, outer, inner, check_energy=True):
         if check_energy:
             F, rel = gpu.energy()
             assert abs(F - e_ref[0]) <= TOL_F * abs(e_ref[0]), (t, F, e_ref[0])
-            RES_SEEN.append(abs(rel - r_ref[0]) / max(abs(r_ref[0]), 1e-30))
+            if abs(r_ref[0]) > 1e-6:
+                RES_SEEN.append(abs(rel - r_ref[0]) / abs(r_ref[0]))
             assert abs(rel - r_ref[0]) <= 1e-3 * abs(r_ref[0]) + 1e-7, (t, rel, r_ref[0])
     lab = gpu.labels()
     bad = label_mismatch(lab, u_ref, gpu.K)
@@ -581,8 +582,9 @@ def test_zz_residual_report(B):
     """Largest relative difference of the reported residual from the oracle's
     over the parity cases above (printed; bounded by their 1e-3 check)."""
     if RES_SEEN:
-        print(f"residual vs oracle: max rel diff {max(RES_SEEN):.2e} over {len(RES_SEEN)} steps, "
-              f"median {float(np.median(RES_SEEN)):.2e}")
+        print(f"residual vs oracle (steps with residual > 1e-6): max rel diff {max(RES_SEEN):.2e}, "
+              f"99th percentile {float(np.percentile(RES_SEEN, 99)):.2e}, median {float(np.median(RES_SEEN)):.2e} "
+              f"over {len(RES_SEEN)} steps")
 
 
 def test_native_library_loaded(B):
