@@ -590,9 +590,8 @@ def run_ours(args, wl, world, rank, local):
                                             "refused": r.get("refused")} for r in table_s]}
         prm_s = B.make_params(**best_s)
         make = lambda: B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm_s, device=dev)
-        m_best, table_m = autotune.tune_sweeps(make, candidates=(2, 4, 8), target=1e-3, max_outer=32,
-                                               ref_outer=64)
-        tuned_layout["inner_sweeps"] = {"pick": m_best, "target_rel_error_vs_reference": 1e-3, "table": table_m}
+        m_best, table_m = autotune.tune_sweeps(make, candidates=(2, 4, 8), tol=1e-4, max_outer=16)
+        tuned_layout["inner_sweeps"] = {"pick": m_best, "tol_outer_step_change": 1e-4, "table": table_m}
         torch.cuda.synchronize(dev)
 
     cpu = None
