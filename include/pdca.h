@@ -282,6 +282,29 @@ pdca_status pdca_solve(pdca_problem *h, int32_t outer_iters, int32_t inner_sweep
  * Returns NONFINITE if u holds NaN/Inf.  Synchronises. */
 pdca_status pdca_energy(pdca_problem *h, double *F, double *rel_residual);
 
+/* The BFS-block renumbering of PDCA_REORDER_BFS: a permutation of the nodes
+ * (structure only, none of the method's arithmetic).  order[p] = the node
+ * placed at position p.  Inside chunks of 65536 consecutive nodes (edges
+ * leaving a chunk are ignored) nodes are grouped into blocks of 1024 by
+ * breadth-first search: a search starts at the lowest node not yet placed
+ * and places nodes in FIFO visiting order until the block is full (nodes it
+ * queued but did not place become free again); a search that runs dry is
+ * followed by the next one in the same block.  Then nodes are sorted by
+ * degree (descending, ties in place order) inside windows of sort_window
+ * positions (a power of two from 32 to 1024; 0 = 1024).
+ *   device = 1: the CUDA kernels pdca_create runs (row_ptr, col, order in
+ *     device memory); work on `stream` (NULL: the legacy default stream),
+ *     which the call synchronises; 16 bytes per node of scratch are
+ *     allocated and freed inside the call.
+ *   device = 0: the host implementation (host pointers), which pdca_create
+ *     runs for PDCA_TILING_ON.
+ * Both give the same order.  row_ptr (n + 1 entries) must start at 0 and not
+ * decrease (else PDCA_ERR_INVALID_ARG); columns outside [0, n) are skipped,
+ * nothing else of the graph is checked.  PDCA_ERR_OOM: no memory for the
+ * scratch; PDCA_ERR_CUDA: a CUDA error. */
+pdca_status pdca_locality_order(const int64_t *row_ptr, const int32_t *col, int32_t n, int32_t sort_window,
+                                int32_t device, int32_t *order, void *stream);
+
 /* Copy the iterate to u_out (n x K float32, original node order, host or device). */
 pdca_status pdca_get_u(pdca_problem *h, float *u_out);
 

@@ -30,6 +30,7 @@ STATUS_NAMES = {
     6: "PDCA_ERR_OOM", 7: "PDCA_ERR_CUDA", 8: "PDCA_ERR_TIMEOUT", 9: "PDCA_ERR_BAD_GRAPH",
     10: "PDCA_ERR_TOO_LARGE", 11: "PDCA_ERR_NOT_CONVERGED",
 }
+globals().update({name: code for code, name in STATUS_NAMES.items()})   # PDCA_ERR_* constants
 PDCA_STATIC_MAX_N = 1 << 20
 PDCA_LAP_NORMALIZED, PDCA_LAP_UNNORMALIZED = 0, 1
 PDCA_JACOBI_DAMPED, PDCA_JACOBI_PERTURBED, PDCA_RICHARDSON = 0, 1, 2
@@ -49,7 +50,7 @@ EXPORTS = [
     "pdca_batch_destroy", "pdca_workspace_size_like", "pdca_create_like",
     "pdca_spectral_workspace_size", "pdca_spectral_init",
     "pdca_image_graph_workspace_size", "pdca_image_graph",
-    "pdca_point_graph_workspace_size", "pdca_point_graph", "pdca_graph_enable",
+    "pdca_point_graph_workspace_size", "pdca_point_graph", "pdca_graph_enable", "pdca_locality_order",
 ]
 
 
@@ -125,6 +126,7 @@ def lib():
                 "pdca_graph_enable": (C.c_int, [vp, i32]),
                 "pdca_point_graph": (C.c_int, [vp, i64, i32, i32, i32, vp, C.c_size_t, vp, vp, vp, i64,
                                                C.POINTER(i64), vp]),
+                "pdca_locality_order": (C.c_int, [vp, vp, i32, i32, i32, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -245,6 +247,14 @@ def pdca_layout(h):
     return st, dict(sell_entries=e.value, n_slices=s.value, sort_window=w.value, tiled=bool(t.value),
                     halo_rows=hr.value, max_halo=mh.value, slices16=s16.value, split_len=sl.value,
                     split_rows=sr.value)
+
+
+def pdca_locality_order(row_ptr, col, n: int, sort_window: int, device: bool, order, stream=0) -> int:
+    """The BFS-block renumbering (order[p] = node at position p); device=True:
+    the CUDA kernels (device arrays, ``stream`` a raw CUDA stream handle),
+    else the host implementation (host arrays)."""
+    return lib().pdca_locality_order(_ptr(row_ptr), _ptr(col), int(n), int(sort_window), 1 if device else 0,
+                                     _ptr(order), C.c_void_p(int(stream)))
 
 
 def pdca_profile_enable(h, on: bool) -> int:

@@ -38,7 +38,8 @@ bool is_device_ptr(const void *p) {
 // row lengths; computed on the host from row_ptr.
 struct Layout {
     int32_t n = 0, K = 0, n_pad = 0, n_slices = 0, sigma = 0, n_tiles = 0;
-    bool host_order = false;           // renumbering computed on the host (BFS blocks)
+    bool host_order = false;           // BFS-block renumbering (widths known only at create)
+    bool device_order = false;         // ... computed by the device kernels (else on a host thread)
     int64_t nnz = 0, sell_entries = 0, sell_cap = 0, halo_cap = 0;
     int32_t split = 0;                 // split length T (rows longer than T use the overflow CSR)
     int32_t n_ov = 0;                  // rows longer than T
@@ -49,7 +50,9 @@ struct Layout {
     size_t o_hoff, o_hidx;
     size_t o_ovrp, o_ovcol, o_ovw, o_ovwb, o_ovidx, o_ovacc;   // overflow CSR and its pre-pass sums
     size_t o_mr, o_me[2];              // mixed precision: r (FP32) and the two corrections (16-bit)
-    size_t o_srp, o_scol, o_sw, o_sdeg, o_sisd, o_smask, o_slab, o_scls, o_status;
+    size_t o_srp, o_scol, o_sw, o_sdeg, o_sisd, o_smask, o_slab, o_scls, o_sscan = 0, o_skey = 0, o_sbfs = 0,
+        o_sinfo = 0, o_status;
+    bool power_copy = false;           // the create-time power method runs on a copy, beside the entry order
     size_t persistent = 0, total = 0;
 };
 
@@ -291,6 +294,7 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     if (prm.reorder == PDCA_REORDER_BFS) {
         // the widths depend on the renumbering (computed at create); size for the bound
         L.host_order = true;
+        L.device_order = prm.tiling != PDCA_TILING_ON;   // the tiles' halos are built on the host
         L.sigma = sigma_req && sigma_req <= kBfsBlock ? sigma_req : kBfsBlock;
         L.sell_entries = 0;
         L.sell_cap = sell_bound(rp, n, L.sigma, max_deg);
@@ -350,13 +354,23 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     L.persistent = o;
     // create-time staging of the CSR input
     L.o_srp = take(8 * (nn + 1));
-    L.o_scol = take(4 * (size_t)L.nnz);
-    L.o_sw = take(4 * (size_t)L.nnz);
+    // the power method overlapping the entry order and the column
+    // compression reads a copy of the packed columns, weights and row words
+    // here (the CSR staging is dead by then)
+    L.power_copy = prm.precond == PDCA_RICHARDSON && prm.lambda_max <= 0 && prm.tiling != PDCA_TILING_ON &&
+                   (prm.entry_order == PDCA_ENTRIES_SPREAD || prm.columns == PDCA_COLUMNS_AUTO);
+    const size_t stage = L.power_copy ? std::max<size_t>((size_t)L.nnz, P) : (size_t)L.nnz;
+    L.o_scol = take(4 * stage);
+    L.o_sw = take(4 * stage);
+    L.o_sinfo = take(L.power_copy ? 4 * np : 0);
     L.o_sdeg = take(8 * nn);
     L.o_sisd = take(8 * nn);
     L.o_smask = take(nn);
     L.o_slab = take(4 * nn);
     L.o_scls = take(4 * np);
+    L.o_sscan = take(L.host_order ? 8 * (size_t)order_layout_scan_words(L.n_slices) : 0);
+    L.o_skey = take(L.device_order ? 8 * nn : 0);
+    L.o_sbfs = take(L.device_order ? 16 : 0);
     L.o_status = take(16);
     L.total = o;
     return PDCA_OK;
@@ -400,6 +414,7 @@ struct pdca_problem {
     bool has_prev = false;
     bool prof = false;
     bool tiled = false;
+    bool slice_off_on_device = false;   // slice_off computed by the device renumbering
     TileView tv{};
     int64_t halo_rows = 0;
     bool mixed = false, bf16u = false;
@@ -561,27 +576,60 @@ double lambda_bound(const pdca_problem *h) {
     return h->prm.laplacian == PDCA_LAP_UNNORMALIZED ? 2.0 * h->dmax : 2.0;
 }
 
-pdca_status power_method(pdca_problem *h) {
-    const SellView A = h->view();
+// Enqueue the power method on stream st over the operator view A (tiles T);
+// the estimate lands in scal[1].
+pdca_status power_launch(pdca_problem *h, const SellView &A, const TileView *T, cudaStream_t st) {
     float *x = h->U[1], *y = h->U[2];
     double *scale = h->scal, *lam = h->scal + 1;
     unsigned *ticket = reinterpret_cast<unsigned *>(h->scal + 2);
-    PDCA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned), h->stream));
-    PDCA_TRY(launch_power_init(A, h->perm, x, h->partials, h->stream));
-    PDCA_TRY(launch_power_finalize(h->partials, energy_blocks(A.n_slices), scale, lam, h->stream));
+    PDCA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
+    PDCA_TRY(launch_power_init(A, h->perm, x, h->partials, st));
+    PDCA_TRY(launch_power_finalize(h->partials, energy_blocks(A.n_slices), scale, lam, st));
     for (int it = 0; it <= h->prm.power_iters; ++it) {
         // the SpMV's last block reduces the partials and updates scale / lambda
-        PDCA_TRY(overflow_pass(h, 1, kOvW32, kOvX32, x));
-        PDCA_TRY(launch_power_spmv(A, h->tiles(), x, scale, y, h->partials, ticket, lam, h->stream));
+        if (h->ov.n_rows > 0) PDCA_TRY(launch_overflow(1, kOvW32, kOvX32, h->ov, x, h->ov_acc, st));
+        PDCA_TRY(launch_power_spmv(A, T, x, scale, y, h->partials, ticket, lam, st));
         std::swap(x, y);
     }
+    return PDCA_OK;
+}
+
+// The estimate, once the power method's work on st is done.
+pdca_status power_read(pdca_problem *h, cudaStream_t st) {
     double lam_h = 0.0;
-    PDCA_TRY(cudaMemcpyAsync(&lam_h, lam, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    PDCA_TRY(cudaStreamSynchronize(h->stream));
+    PDCA_TRY(cudaMemcpyAsync(&lam_h, h->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PDCA_TRY(cudaStreamSynchronize(st));
     h->lambda_est = lam_h;
     h->lambda_used = std::min(lambda_bound(h), 1.001 * lam_h);
     return PDCA_OK;
 }
+
+pdca_status power_method(pdca_problem *h) {
+    pdca_status st = power_launch(h, h->view(), h->tiles(), h->stream);
+    return st != PDCA_OK ? st : power_read(h, h->stream);
+}
+
+// A stream of its own for work that overlaps the caller's stream at create
+// time; synchronised and released on scope exit (also on the error paths,
+// before the caller may reuse the workspace).
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t in = nullptr, out = nullptr;
+    ~SideStream() {
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+        if (in) cudaEventDestroy(in);
+        if (out) cudaEventDestroy(out);
+    }
+    cudaError_t open() {
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&in, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&out, cudaEventDisableTiming);
+        return e;
+    }
+};
 
 // Host symbolic analysis (BFS-block renumbering, degree sort, halo lists),
 // then upload of perm / iperm / halo arrays and the exact slice offsets.
@@ -616,15 +664,15 @@ struct OrderJob {
 
 // The overflow CSR's row offsets (rows longer than the split length, in new
 // row order) and the overflow row of every such row, uploaded; the pack
-// kernel fills the columns and weights.  perm: new row -> old row (n_pad,
-// -1 on padding).
-pdca_status build_overflow(pdca_problem *h, const int64_t *rp, const int32_t *perm) {
+// kernel fills the columns and weights.  perm: new row -> old row for the
+// first `rows` rows (-1 on padding); the rows after them are padding.
+pdca_status build_overflow(pdca_problem *h, const int64_t *rp, const int32_t *perm, int32_t rows) {
     Layout &L = h->L;
     if (L.n_ov == 0) return PDCA_OK;
     std::vector<int64_t> orp((size_t)L.n_ov + 1, 0);
     std::vector<int32_t> idx((size_t)L.n_pad, -1);
     int32_t q = 0;
-    for (int32_t r = 0; r < L.n_pad; ++r) {
+    for (int32_t r = 0; r < rows; ++r) {
         const int32_t old = perm[r];
         if (old < 0) continue;
         const int64_t d = rp[old + 1] - rp[old];
@@ -643,12 +691,57 @@ pdca_status build_overflow(pdca_problem *h, const int64_t *rp, const int32_t *pe
     return PDCA_OK;
 }
 
+// The device's BFS-block order of the nodes into iperm's storage, enqueued
+// on st (structure only: it reads row_ptr, already checked on the host, and
+// skips columns outside [0, n), so it may run beside the validation).
+cudaError_t device_order_launch(pdca_problem *h, cudaStream_t st) {
+    Layout &L = h->L;
+    const int64_t *d_rp = reinterpret_cast<const int64_t *>(h->ws + L.o_srp);
+    const int32_t *d_col = reinterpret_cast<const int32_t *>(h->ws + L.o_scol);
+    int32_t *queue = reinterpret_cast<int32_t *>(h->ws + L.o_scls);   // rowcls later
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(h->ws + L.o_skey);
+    uint32_t *err = reinterpret_cast<uint32_t *>(h->ws + L.o_sbfs);
+    cudaError_t e = cudaMemsetAsync(err, 0, 4, st);
+    if (e != cudaSuccess) return e;
+    return launch_bfs_blocks(L.n, kBfsBlock, kBfsChunk, d_rp, d_col, queue, key, h->iperm, err, st);
+}
+
+// The renumbering (perm, iperm, slice offsets) from that order, on the
+// handle's stream (which must follow the order's work): degree sort, perm,
+// iperm and offsets on the device; the offsets, and the order where rows
+// overflow, come back to the host.
+pdca_status device_renumber(pdca_problem *h, const int64_t *rp) {
+    Layout &L = h->L;
+    const int32_t n = L.n;
+    cudaStream_t st = h->stream;
+    const int64_t *d_rp = reinterpret_cast<const int64_t *>(h->ws + L.o_srp);
+    uint32_t *err = reinterpret_cast<uint32_t *>(h->ws + L.o_sbfs);
+    int32_t *count = reinterpret_cast<int32_t *>(h->ws + L.o_scls);
+    int64_t *tmp = reinterpret_cast<int64_t *>(h->ws + L.o_sscan);
+    uint32_t err_h = 0;
+    PDCA_TRY(cudaMemcpyAsync(&err_h, err, 4, cudaMemcpyDeviceToHost, st));
+    PDCA_TRY(cudaStreamSynchronize(st));
+    if (err_h) return PDCA_ERR_CUDA;   // the order is not a permutation; never expected
+    PDCA_TRY(launch_order_sort(n, L.sigma, d_rp, h->iperm, h->perm, st));
+    PDCA_TRY(launch_order_layout(n, L.n_pad, L.split, d_rp, h->perm, h->iperm, count, tmp, h->slice_off, st));
+    L.slice_off.resize((size_t)L.n_slices + 1);
+    PDCA_TRY(cudaMemcpyAsync(L.slice_off.data(), h->slice_off, 8 * L.slice_off.size(), cudaMemcpyDeviceToHost, st));
+    std::vector<int32_t> perm_h(L.n_ov > 0 ? (size_t)n : 0);
+    if (L.n_ov > 0) PDCA_TRY(cudaMemcpyAsync(perm_h.data(), h->perm, 4 * (size_t)n, cudaMemcpyDeviceToHost, st));
+    PDCA_TRY(cudaStreamSynchronize(st));
+    L.sell_entries = L.slice_off.back();
+    if (L.sell_entries > L.sell_cap) return PDCA_ERR_CUDA;   // the bound is a theorem; never expected
+    h->slice_off_on_device = true;
+    return build_overflow(h, rp, perm_h.data(), L.n_ov > 0 ? n : 0);
+}
+
 pdca_status host_renumber(pdca_problem *h, const int64_t *rp, OrderJob &job) {
     Layout &L = h->L;
     const int32_t n = L.n;
     job.join();
     const int32_t *hc = job.hc;
     const std::vector<int32_t> &order = job.order;
+    h->tiled = false;
     std::vector<int32_t> perm((size_t)L.n_pad, -1), iperm((size_t)n);
     const int64_t chunks = ((int64_t)n + 65535) / 65536;
     host_parallel_for(chunks, [&](int64_t c) {
@@ -678,10 +771,10 @@ pdca_status host_renumber(pdca_problem *h, const int64_t *rp, OrderJob &job) {
         L.slice_off[(size_t)s + 1] = L.slice_off[(size_t)s] + width[(size_t)s] * kSliceRows;
     L.sell_entries = L.slice_off.back();
     if (L.sell_entries > L.sell_cap) return PDCA_ERR_CUDA;   // the bound is a theorem; never expected
-    h->tiled = false;
-    // On every workload measured on GB300 the plain kernels were faster than
-    // the shared-memory tiles, so AUTO uses them; ON builds the tiles.
-    if (h->prm.tiling == PDCA_TILING_ON) {
+    // PDCA_TILING_ON (on every workload measured on GB300 the plain kernels
+    // were faster than the shared-memory tiles, so AUTO uses the plain ones):
+    // the tiles' halo lists on the host
+    {
         std::vector<int64_t> hoff;
         std::vector<int32_t> hidx;
         int32_t mx = 0;
@@ -696,7 +789,7 @@ pdca_status host_renumber(pdca_problem *h, const int64_t *rp, OrderJob &job) {
         (void)over;
         const bool fits = mx >= 1 && mx <= 65536 && (int64_t)hidx.size() <= L.halo_cap &&
                           (int32_t)hoff.size() == L.n_tiles + 1;
-        if (!fits && h->prm.tiling == PDCA_TILING_ON) return PDCA_ERR_INVALID_ARG;
+        if (!fits) return PDCA_ERR_INVALID_ARG;
         if (fits) {
             int64_t *d_hoff = reinterpret_cast<int64_t *>(h->ws + L.o_hoff);
             int32_t *d_hidx = reinterpret_cast<int32_t *>(h->ws + L.o_hidx);
@@ -718,7 +811,7 @@ pdca_status host_renumber(pdca_problem *h, const int64_t *rp, OrderJob &job) {
     PDCA_TRY(cudaMemcpyAsync(h->perm, perm.data(), 4 * perm.size(), cudaMemcpyHostToDevice, h->stream));
     PDCA_TRY(cudaMemcpyAsync(h->iperm, iperm.data(), 4 * iperm.size(), cudaMemcpyHostToDevice, h->stream));
     PDCA_TRY(cudaStreamSynchronize(h->stream));
-    return build_overflow(h, rp, perm.data());
+    return build_overflow(h, rp, perm.data(), L.n_pad);
 }
 
 // ---------------------------------------------------------------------------
@@ -977,19 +1070,30 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
 
     // BFS renumbering on a host thread, overlapping the copies and validation
     OrderJob job;
-    if (L.host_order) {
+    if (L.host_order && !L.device_order) {
         st = job.start(rp, col, nnz, n, L.sigma);
         if (st != PDCA_OK) {
             delete h;
             return st;
         }
     }
+    // the device's BFS order runs on a stream of its own beside the rest of
+    // the copies and the validation (it needs only row_ptr and the columns)
+    SideStream order_side;
     auto fail = [&](pdca_status s) { cudaStreamSynchronize(sm); delete h; return s; };
     auto cp = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, sm) : cudaSuccess;
     };
-    if (cp(s_rp, rp, 8 * ((size_t)n + 1)) != cudaSuccess || cp(s_col, col, 4 * (size_t)nnz) != cudaSuccess ||
-        cp(s_w, w, 4 * (size_t)nnz) != cudaSuccess || cp(s_mask, fid_mask, (size_t)n) != cudaSuccess ||
+    if (cp(s_rp, rp, 8 * ((size_t)n + 1)) != cudaSuccess || cp(s_col, col, 4 * (size_t)nnz) != cudaSuccess)
+        return fail(PDCA_ERR_CUDA);
+    if (L.device_order) {
+        if (order_side.open() != cudaSuccess || cudaEventRecord(order_side.in, sm) != cudaSuccess ||
+            cudaStreamWaitEvent(order_side.s, order_side.in, 0) != cudaSuccess ||
+            device_order_launch(h, order_side.s) != cudaSuccess ||
+            cudaEventRecord(order_side.out, order_side.s) != cudaSuccess)
+            return fail(PDCA_ERR_CUDA);
+    }
+    if (cp(s_w, w, 4 * (size_t)nnz) != cudaSuccess || cp(s_mask, fid_mask, (size_t)n) != cudaSuccess ||
         cp(s_lab, labels, 4 * (size_t)n) != cudaSuccess ||
         cudaMemsetAsync(s_status, 0, 16, sm) != cudaSuccess)
         return fail(PDCA_ERR_CUDA);
@@ -1009,7 +1113,8 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
         if (st != PDCA_OK) return fail(st);
     }
     if (L.host_order) {
-        st = host_renumber(h, rp, job);
+        if (L.device_order && cudaStreamWaitEvent(sm, order_side.out, 0) != cudaSuccess) return fail(PDCA_ERR_CUDA);
+        st = L.device_order ? device_renumber(h, rp) : host_renumber(h, rp, job);
         if (st != PDCA_OK) return fail(st);
     } else {
         if (launch_window_sort(n, L.n_pad, L.sigma, s_rp, h->perm, h->iperm, sm) != cudaSuccess)
@@ -1019,11 +1124,12 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
             if (cudaMemcpyAsync(perm_h.data(), h->perm, 4 * perm_h.size(), cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
                 cudaStreamSynchronize(sm) != cudaSuccess)
                 return fail(PDCA_ERR_CUDA);
-            st = build_overflow(h, rp, perm_h.data());
+            st = build_overflow(h, rp, perm_h.data(), L.n_pad);
             if (st != PDCA_OK) return fail(st);
         }
     }
-    if (cp(h->slice_off, L.slice_off.data(), 8 * L.slice_off.size()) != cudaSuccess) return fail(PDCA_ERR_CUDA);
+    if (!h->slice_off_on_device && cp(h->slice_off, L.slice_off.data(), 8 * L.slice_off.size()) != cudaSuccess)
+        return fail(PDCA_ERR_CUDA);
     cudaError_t pe;
     if (h->tiled)
         pe = launch_pack_tiled(L.n_pad, s_rp, s_col, s_w, s_deg, s_isd, s_mask, s_lab, h->perm, h->iperm, h->slice_off,
@@ -1037,6 +1143,38 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
                          const_cast<__nv_bfloat16 *>(h->ov.wb), s_status, sm);
     if (pe != cudaSuccess) return fail(PDCA_ERR_CUDA);
     const bool c16 = !h->tiled && prm.columns == PDCA_COLUMNS_AUTO;
+    // The power method (Sec. 3.1) runs on the operator as packed (entries in
+    // CSR order, int32 columns), whatever the entry order and column format
+    // chosen after it, so that every layout gets the same estimate.  Where
+    // the entry order or the compression rewrite the arrays, it reads a copy
+    // of them on a stream of its own while they run.
+    const bool power = prm.precond == PDCA_RICHARDSON && prm.lambda_max <= 0;
+    SideStream side;
+    if (power) {
+        if (!L.power_copy || h->tiled) {
+            st = power_launch(h, h->view(), h->tiles(), sm);
+            if (st != PDCA_OK) return fail(st);
+        } else {
+            int32_t *pc = reinterpret_cast<int32_t *>(W + L.o_scol);
+            float *pw = reinterpret_cast<float *>(W + L.o_sw);
+            uint32_t *pi = reinterpret_cast<uint32_t *>(W + L.o_sinfo);
+            SellView A = h->view();
+            A.col = pc;
+            A.col16 = nullptr;
+            A.slice_fmt = nullptr;
+            A.w = pw;
+            A.wb = nullptr;
+            A.rowinfo = pi;
+            if (cp(pc, h->sell_col, 4 * (size_t)L.sell_entries) != cudaSuccess ||
+                cp(pw, h->sell_w, 4 * (size_t)L.sell_entries) != cudaSuccess ||
+                cp(pi, h->rowinfo, 4 * (size_t)L.n_pad) != cudaSuccess || side.open() != cudaSuccess ||
+                cudaEventRecord(side.in, sm) != cudaSuccess || cudaStreamWaitEvent(side.s, side.in, 0) != cudaSuccess)
+                return fail(PDCA_ERR_CUDA);
+            st = power_launch(h, A, nullptr, side.s);
+            if (st != PDCA_OK) return fail(st);
+            if (cudaEventRecord(side.out, side.s) != cudaSuccess) return fail(PDCA_ERR_CUDA);
+        }
+    }
     if (prm.entry_order == PDCA_ENTRIES_SPREAD &&
         launch_spread(L.n_pad, h->slice_off, h->rowinfo, h->tiled ? 0xFFFFFFu : kLenMask, c16 ? s_cls : nullptr,
                       h->tiled ? nullptr : h->sell_col,
@@ -1053,7 +1191,8 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
         if (prm.lambda_max > 0) {
             h->lambda_used = prm.lambda_max;
         } else {
-            st = power_method(h);
+            if (side.s && cudaStreamWaitEvent(sm, side.out, 0) != cudaSuccess) return fail(PDCA_ERR_CUDA);
+            st = power_read(h, sm);
             if (st != PDCA_OK) return fail(st);
         }
         st = feasible(prm, omega, h->lambda_used, h->dmax);
@@ -1395,6 +1534,50 @@ pdca_status pdca_layout(pdca_problem *h, int64_t *sell_entries, int64_t *n_slice
     if (halo_rows) *halo_rows = h->tiled ? h->halo_rows : 0;
     if (max_halo) *max_halo = h->tiled ? h->tv.max_halo : 0;
     return PDCA_OK;
+}
+
+pdca_status pdca_locality_order(const int64_t *row_ptr, const int32_t *col, int32_t n, int32_t sort_window,
+                                int32_t device, int32_t *order, void *stream) {
+    if (!row_ptr || !order || n < 1 || (device != 0 && device != 1)) return PDCA_ERR_INVALID_ARG;
+    const int32_t sigma = sort_window == 0 ? kBfsBlock : sort_window;
+    if (sigma < 32 || sigma > kBfsBlock || (sigma & (sigma - 1)) != 0) return PDCA_ERR_INVALID_ARG;
+    std::vector<int64_t> keep;
+    const int64_t *rp = nullptr;
+    pdca_status st = host_row_ptr(row_ptr, n, keep, &rp);
+    if (st != PDCA_OK) return st;
+    if (rp[n] > 0 && !col) return PDCA_ERR_INVALID_ARG;
+    if (device == 0) {
+        if (is_device_ptr(row_ptr) || is_device_ptr(col) || is_device_ptr(order)) return PDCA_ERR_INVALID_ARG;
+        locality_order(n, rp, col, kBfsBlock, kBfsChunk, sigma, order);
+        return PDCA_OK;
+    }
+    if (!is_device_ptr(row_ptr) || (rp[n] > 0 && !is_device_ptr(col)) || !is_device_ptr(order))
+        return PDCA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *scratch = nullptr;
+    const size_t nn = (size_t)n;
+    if (cudaMalloc(&scratch, 16 * nn + 16) != cudaSuccess) {
+        cudaGetLastError();
+        return PDCA_ERR_OOM;
+    }
+    char *b = static_cast<char *>(scratch);
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(b);
+    int32_t *queue = reinterpret_cast<int32_t *>(b + 8 * nn);
+    int32_t *tmp = reinterpret_cast<int32_t *>(b + 12 * nn);
+    uint32_t *err = reinterpret_cast<uint32_t *>(b + 16 * nn);
+    uint32_t err_h = 0;
+    st = PDCA_OK;
+    if (cudaMemsetAsync(err, 0, 4, s) != cudaSuccess ||
+        launch_bfs_blocks(n, kBfsBlock, kBfsChunk, row_ptr, col, queue, key, tmp, err, s) != cudaSuccess ||
+        cudaMemcpyAsync(&err_h, err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        st = PDCA_ERR_CUDA;
+    else if (err_h)
+        st = PDCA_ERR_CUDA;
+    else if (launch_order_sort(n, sigma, row_ptr, tmp, order, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        st = PDCA_ERR_CUDA;
+    cudaFree(scratch);
+    return st;
 }
 
 pdca_status pdca_profile_enable(pdca_problem *h, int32_t on) {

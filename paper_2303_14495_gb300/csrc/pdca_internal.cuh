@@ -284,6 +284,24 @@ cudaError_t launch_validate(int32_t n, int32_t K, const int64_t *row_ptr, const 
                             double *deg, double *isd, uint32_t *status, cudaStream_t st);
 cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const int64_t *row_ptr,
                                int32_t *perm, int32_t *iperm, cudaStream_t st);
+// From a node order already in perm[0, n) (position -> node): perm's padding
+// rows set to -1, iperm, and slice_off (n_slices + 1) from the slice widths
+// (longest row capped at split, rounded up to kVec).  count: n_slices int32
+// scratch; scan_tmp: order_layout_scan_words(n_slices) int64 scratch.
+cudaError_t launch_order_layout(int32_t n, int32_t n_pad, int32_t split, const int64_t *row_ptr, int32_t *perm,
+                                int32_t *iperm, int32_t *count, int64_t *scan_tmp, int64_t *slice_off,
+                                cudaStream_t st);
+int64_t order_layout_scan_words(int32_t n_slices);
+// BFS-block order of the nodes (order[p] = node at position p), chunks of
+// `chunk` nodes (<= 65536) renumbered by one block each.  queue: n int32,
+// key: n uint64 scratch; err: set nonzero if the order could not be formed
+// (never expected).  Then the degree sort inside windows of sigma (a power
+// of two <= 1024) positions, from order into out.
+cudaError_t launch_bfs_blocks(int32_t n, int32_t block, int32_t chunk, const int64_t *row_ptr, const int32_t *col,
+                              int32_t *queue, unsigned long long *key, int32_t *order, uint32_t *err,
+                              cudaStream_t st);
+cudaError_t launch_order_sort(int32_t n, int32_t sigma, const int64_t *row_ptr, const int32_t *order, int32_t *out,
+                              cudaStream_t st);
 // self == nullptr: L_s weights w_ij / sqrt(d_i d_j); else L weights w_ij and
 // self[r] = d_i (0 on padding rows).  dsq (nullable): sqrt(d_i) per row.
 // rowcls (nullable): entries are written in bands (previous, next, own

@@ -11,6 +11,7 @@
 //   compress_kernel     16-bit columns for the slices that allow them;
 //   init_u_kernel       u^0 (prior on labelled rows, centre elsewhere).
 #include "pdca_internal.cuh"
+#include "scan.cuh"
 
 #include <cuda_bf16.h>
 #include <math.h>
@@ -18,56 +19,89 @@
 namespace pdca {
 namespace {
 
-__global__ void validate_kernel(int32_t n, int32_t K, const int64_t *__restrict__ row_ptr,
-                                const int32_t *__restrict__ col, const float *__restrict__ w,
-                                const uint8_t *__restrict__ mask, const int32_t *__restrict__ labels,
-                                double *__restrict__ deg, double *__restrict__ isd,
-                                uint32_t *__restrict__ status) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// kValLanes lanes per row: each lane checks one entry at a time (range, no
+// self loop, strictly increasing columns, a finite non-negative weight, and
+// w_ji stored with the same value, by binary search in row j); the row's
+// first lane adds the weights into d_i in CSR order (FP64).  One atomic per
+// warp for the flags and for the largest degree.
+constexpr int kValLanes = 8;
+
+__global__ void __launch_bounds__(256)
+validate_kernel(int32_t n, int32_t K, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                const float *__restrict__ w, const uint8_t *__restrict__ mask, const int32_t *__restrict__ labels,
+                double *__restrict__ deg, double *__restrict__ isd, uint32_t *__restrict__ status) {
+    constexpr unsigned kAll = 0xffffffffu;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((t & ~31ll) >= (int64_t)n * kValLanes) return;   // whole warps past the last row
+    const int32_t i = (int32_t)(t / kValLanes);
+    const int sub = (int)(t % kValLanes);
+    const int g0 = (threadIdx.x & 31) & ~(kValLanes - 1);
+    const bool live = i < n;
     uint32_t bad = 0;
     double d = 0.0;
-    int32_t prev = -1;
-    const int64_t e0 = row_ptr[i], e1 = row_ptr[i + 1];
-    for (int64_t e = e0; e < e1; ++e) {
-        const int32_t j = col[e];
-        const float wv = w[e];
-        if (j < 0 || j >= n) {
-            bad |= kBadGraph;
-            continue;
-        }
-        if (j == i || j <= prev) bad |= kBadGraph;
-        prev = j > prev ? j : prev;
-        if (!(isfinite(wv) && wv >= 0.0f)) bad |= kBadGraph;
-        d += (double)wv;
-        // w_ji must be stored with the same value: binary search in row j
-        int64_t lo = row_ptr[j], hi = row_ptr[j + 1] - 1;
-        bool ok = false;
-        while (lo <= hi) {
-            const int64_t mid = lo + ((hi - lo) >> 1);
-            const int32_t cm = col[mid];
-            if (cm == i) {
-                ok = (w[mid] == wv);
-                break;
+    int64_t e0 = 0, e1 = 0;
+    if (live) {
+        e0 = row_ptr[i];
+        e1 = row_ptr[i + 1];
+    }
+    const int32_t chunks = live ? (int32_t)((e1 - e0 + kValLanes - 1) / kValLanes) : 0;
+    const int32_t cmax = __reduce_max_sync(kAll, chunks);
+    for (int32_t c = 0; c < cmax; ++c) {
+        const int64_t e = e0 + (int64_t)c * kValLanes + sub;
+        float wv = 0.0f;
+        if (e < e1) {
+            const int32_t j = col[e];
+            wv = w[e];
+            if (j < 0 || j >= n) {
+                bad |= kBadGraph;
+            } else {
+                if (j == i || (e > e0 && j <= col[e - 1])) bad |= kBadGraph;
+                if (!(isfinite(wv) && wv >= 0.0f)) bad |= kBadGraph;
+                int64_t lo = row_ptr[j], hi = row_ptr[j + 1] - 1;
+                bool ok = false;
+                while (lo <= hi) {
+                    const int64_t mid = lo + ((hi - lo) >> 1);
+                    const int32_t cm = col[mid];
+                    if (cm == i) {
+                        ok = (w[mid] == wv);
+                        break;
+                    }
+                    if (cm < i) lo = mid + 1;
+                    else hi = mid - 1;
+                }
+                if (!ok) bad |= kNotSymmetric;
             }
-            if (cm < i) lo = mid + 1;
-            else hi = mid - 1;
         }
-        if (!ok) bad |= kNotSymmetric;
+#pragma unroll
+        for (int k = 0; k < kValLanes; ++k) {
+            const float wk = __shfl_sync(kAll, wv, g0 + k);
+            if (sub == 0 && e0 + (int64_t)c * kValLanes + k < e1) d += (double)wk;
+        }
     }
-    if (!(d > 0.0)) bad |= kIsolated;
-    const uint8_t m = mask[i];
-    if (m > 1) bad |= kBadGraph;
-    if (m == 1) {
-        const int32_t l = labels[i];
-        const int32_t hiK = K == 1 ? 2 : K;
-        if (l < 0 || l >= hiK) bad |= kBadGraph;
+    unsigned long long dbits = 0;
+    if (live && sub == 0) {
+        if (!(d > 0.0)) bad |= kIsolated;
+        const uint8_t m = mask[i];
+        if (m > 1) bad |= kBadGraph;
+        if (m == 1) {
+            const int32_t l = labels[i];
+            const int32_t hiK = K == 1 ? 2 : K;
+            if (l < 0 || l >= hiK) bad |= kBadGraph;
+        }
+        deg[i] = d;
+        isd[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+        // non-negative doubles order like their bit patterns
+        dbits = (unsigned long long)__double_as_longlong(d);
     }
-    deg[i] = d;
-    isd[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
-    if (bad) atomicOr(status, bad);
-    // non-negative doubles order like their bit patterns
-    atomicMax(reinterpret_cast<unsigned long long *>(status + 2), (unsigned long long)__double_as_longlong(d));
+    bad = __reduce_or_sync(kAll, bad);
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_xor_sync(kAll, dbits, o);
+        dbits = x > dbits ? x : dbits;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicOr(status, bad);
+        atomicMax(reinterpret_cast<unsigned long long *>(status + 2), dbits);
+    }
 }
 
 // One block per window of `sigma` rows: bitonic sort of keys
@@ -116,6 +150,37 @@ __global__ void window_sort_kernel(int32_t n, int32_t n_pad, int32_t sigma,
             iperm[old] = (int32_t)r;
         }
     }
+}
+
+// Renumbering from a node order (position -> node, in perm[0, n)): padding
+// rows of perm set to -1, iperm the inverse.
+__global__ void order_perm_kernel(int32_t n, int32_t n_pad, int32_t *__restrict__ perm,
+                                  int32_t *__restrict__ iperm) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_pad) return;
+    if (r >= n) {
+        perm[r] = -1;
+        return;
+    }
+    iperm[perm[r]] = r;
+}
+
+// Entries of every slice: 32 x (its longest row, capped at the split
+// length, rounded up to kVec).  One warp per slice, lane = row.
+__global__ void slice_count_kernel(int32_t n, int32_t n_slices, int32_t split, const int64_t *__restrict__ row_ptr,
+                                   const int32_t *__restrict__ perm, int32_t *__restrict__ count) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t s = t >> 5;
+    if (s >= n_slices) return;   // warp-uniform
+    const int64_t r = t;
+    int32_t d = 0;
+    if (r < n) {
+        const int32_t v = perm[r];
+        const int64_t dv = row_ptr[v + 1] - row_ptr[v];
+        d = dv < split ? (int32_t)dv : split;
+    }
+    const int32_t wmax = __reduce_max_sync(0xffffffffu, d);
+    if ((threadIdx.x & 31) == 0) count[s] = (wmax + kVec - 1) / kVec * kVec * kSliceRows;
 }
 
 // One thread per row.  With rowcls, a row's entries are ordered in three
@@ -335,18 +400,14 @@ __global__ void pack_tiled_kernel(int32_t n_pad, const int64_t *__restrict__ row
 constexpr int kSpreadLook = 64;
 constexpr int kSpreadLanes = 8;   // S
 
-__global__ void spread_kernel(int32_t n_slices, const int64_t *__restrict__ slice_off,
-                              const uint32_t *__restrict__ rowinfo, uint32_t len_mask,
-                              const uint32_t *__restrict__ rowcls,
-                              int32_t *__restrict__ sell_col,
-                              uint16_t *__restrict__ lcol, const int64_t *__restrict__ halo_off,
-                              const int32_t *__restrict__ halo_idx, float *__restrict__ sell_w,
-                              __nv_bfloat16 *__restrict__ sell_wb) {
-    constexpr int S = kSpreadLanes, groups = kSliceRows / kSpreadLanes;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)n_slices * groups) return;
-    const int64_t s = t / groups;
-    const int32_t lane0 = (int32_t)(t % groups) * S;
+// Quarter lane0 / S of slice s, entries in global memory.
+__device__ void spread_quarter(int64_t s, int32_t lane0, const int64_t *__restrict__ slice_off,
+                               const uint32_t *__restrict__ rowinfo, uint32_t len_mask,
+                               const uint32_t *__restrict__ rowcls, int32_t *__restrict__ sell_col,
+                               uint16_t *__restrict__ lcol, const int64_t *__restrict__ halo_off,
+                               const int32_t *__restrict__ halo_idx, float *__restrict__ sell_w,
+                               __nv_bfloat16 *__restrict__ sell_wb) {
+    constexpr int S = kSpreadLanes;
     const int64_t base = slice_off[s];
     const int64_t h0 = lcol ? halo_off[(s * kSliceRows) / kTileRows] : 0;
     int32_t len[S], np[S], nb[S];
@@ -414,6 +475,134 @@ __global__ void spread_kernel(int32_t n_slices, const int64_t *__restrict__ slic
     }
 }
 
+__global__ void spread_kernel(int32_t n_slices, const int64_t *__restrict__ slice_off,
+                              const uint32_t *__restrict__ rowinfo, uint32_t len_mask,
+                              const uint32_t *__restrict__ rowcls,
+                              int32_t *__restrict__ sell_col,
+                              uint16_t *__restrict__ lcol, const int64_t *__restrict__ halo_off,
+                              const int32_t *__restrict__ halo_idx, float *__restrict__ sell_w,
+                              __nv_bfloat16 *__restrict__ sell_wb) {
+    constexpr int groups = kSliceRows / kSpreadLanes;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_slices * groups) return;
+    spread_quarter(t / groups, (int32_t)(t % groups) * kSpreadLanes, slice_off, rowinfo, len_mask, rowcls,
+                   sell_col, lcol, halo_off, halo_idx, sell_w, sell_wb);
+}
+
+// The same choices with the slice staged in shared memory (global columns,
+// slices up to kSpreadSmemW entries wide; wider ones take spread_quarter):
+// one warp per slice, the four quarters side by side.  At position p the
+// rows of a quarter take their turns in lane order as above; for the row
+// whose turn it is, the 8 lanes of its quarter examine 8 consecutive
+// candidates at once and the first acceptable one (lowest position) wins,
+// which is the candidate the sequential scan would stop at.  Lane q*8 + k
+// holds the group of slot k of quarter q.
+constexpr int kSpreadSmemW = 32;
+constexpr int kSpreadWarps = 4;
+
+__device__ __forceinline__ int32_t spread_loc(int32_t lane, int32_t j) {
+    return kSliceRows * kVec * (j / kVec) + kVec * lane + (j % kVec);
+}
+
+__global__ void __launch_bounds__(32 * kSpreadWarps)
+spread_warp_kernel(int32_t n_slices, const int64_t *__restrict__ slice_off, const uint32_t *__restrict__ rowinfo,
+                   uint32_t len_mask, const uint32_t *__restrict__ rowcls, int32_t *__restrict__ sell_col,
+                   float *__restrict__ sell_w, __nv_bfloat16 *__restrict__ sell_wb) {
+    constexpr int S = kSpreadLanes;
+    constexpr int E = kSliceRows * kSpreadSmemW;
+    constexpr unsigned kAll = 0xffffffffu;
+    __shared__ int32_t s_col[kSpreadWarps][E];
+    __shared__ float s_w[kSpreadWarps][E];
+    __shared__ __nv_bfloat16 s_wb[kSpreadWarps][E];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * kSpreadWarps + warp;
+    if (s >= n_slices) return;   // warp-uniform; the kernel has no block barrier
+    const int64_t base = slice_off[s];
+    const int64_t cnt = slice_off[s + 1] - base;
+    if (cnt > E) {
+        if (lane < kSliceRows / S)
+            spread_quarter(s, lane * S, slice_off, rowinfo, len_mask, rowcls, sell_col, nullptr, nullptr, nullptr,
+                           sell_w, sell_wb);
+        return;
+    }
+    int32_t *cs = s_col[warp];
+    float *ws = s_w[warp];
+    __nv_bfloat16 *bs = s_wb[warp];
+    for (int32_t i = lane; i < (int32_t)cnt; i += 32) {
+        cs[i] = sell_col[base + i];
+        ws[i] = sell_w[base + i];
+        if (sell_wb) bs[i] = sell_wb[base + i];
+    }
+    const int64_t r = s * kSliceRows + lane;
+    const int32_t my_len = (int32_t)((rowinfo[r] >> 8) & len_mask);
+    const uint32_t cls = rowcls ? rowcls[r] : 0u;
+    const int32_t my_np = (int32_t)(cls & 0xFFu), my_nb = my_np + (int32_t)((cls >> 8) & 0xFFu);
+    const int q = lane / S, sub = lane % S;
+    const int32_t maxlen = __reduce_max_sync(kAll, my_len);
+    int32_t grp_slot = 0;
+    bool moved = false;
+    __syncwarp();
+    for (int32_t p = 0; p < maxlen; ++p) {
+        uint32_t used = 0;   // the same in the 8 lanes of a quarter
+        for (int l = 0; l < S; ++l) {
+            const int R = q * S + l;
+            const int32_t len = __shfl_sync(kAll, my_len, R);
+            const int32_t np = __shfl_sync(kAll, my_np, R);
+            const int32_t nb = __shfl_sync(kAll, my_nb, R);
+            const bool active = p < len;
+            // the entry stays inside its band (previous, next, own chunk)
+            const int32_t band_end = p < np ? np : (p < nb ? nb : len);
+            const int32_t lim = min(band_end, p + kSpreadLook);
+            int32_t pick = -1, pslot = 0, pgrp = 0;
+            bool pending = active;
+            for (int32_t j0 = p; __any_sync(kAll, pending); j0 += S) {
+                const int32_t j = j0 + sub;
+                const bool valid = pending && j < lim;
+                const int32_t c = valid ? cs[spread_loc(R, j)] : 0;
+                const int32_t slot = c % S, grp = c / S;
+                const int32_t g_at = __shfl_sync(kAll, grp_slot, q * S + slot);
+                const bool ok = valid && (!((used >> slot) & 1u) || g_at == grp);
+                const uint32_t bits = (__ballot_sync(kAll, ok) >> (q * S)) & ((1u << S) - 1u);
+                const int f = bits ? __ffs(bits) - 1 : 0;
+                const int32_t fslot = __shfl_sync(kAll, slot, q * S + f);
+                const int32_t fgrp = __shfl_sync(kAll, grp, q * S + f);
+                if (pending && bits) {
+                    pick = j0 + f;
+                    pslot = fslot;
+                    pgrp = fgrp;
+                }
+                if (pending && (bits || j0 + S >= lim)) pending = false;
+            }
+            if (active && pick >= 0) {
+                if (!((used >> pslot) & 1u)) {
+                    used |= 1u << pslot;
+                    if (sub == pslot) grp_slot = pgrp;
+                }
+                if (pick != p) {
+                    moved = true;
+                    if (sub == 0) {
+                        const int32_t a = spread_loc(R, p), b = spread_loc(R, pick);
+                        const int32_t xc = cs[a]; cs[a] = cs[b]; cs[b] = xc;
+                        const float xw = ws[a]; ws[a] = ws[b]; ws[b] = xw;
+                        if (sell_wb) {
+                            const __nv_bfloat16 xb = bs[a];
+                            bs[a] = bs[b];
+                            bs[b] = xb;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (!__any_sync(kAll, moved)) return;
+    for (int32_t i = lane; i < (int32_t)cnt; i += 32) {
+        sell_col[base + i] = cs[i];
+        sell_w[base + i] = ws[i];
+        if (sell_wb) sell_wb[base + i] = bs[i];
+    }
+}
+
 // Row tags of a problem that shares another problem's operator: the row
 // lengths come from the base's rowinfo, the tags from the new fidelity data
 // (original node order, checked like the validation kernel does).
@@ -459,9 +648,26 @@ cudaError_t launch_validate(int32_t n, int32_t K, const int64_t *row_ptr, const 
                             const float *w, const uint8_t *mask, const int32_t *labels, double *deg, double *isd,
                             uint32_t *status, cudaStream_t st) {
     count_launches(1);
-    validate_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, K, row_ptr, col, w, mask, labels, deg, isd, status);
+    const int64_t threads = (int64_t)n * kValLanes;
+    validate_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(n, K, row_ptr, col, w, mask, labels, deg, isd,
+                                                                        status);
     return cudaGetLastError();
 }
+
+cudaError_t launch_order_layout(int32_t n, int32_t n_pad, int32_t split, const int64_t *row_ptr, int32_t *perm,
+                                int32_t *iperm, int32_t *count, int64_t *scan_tmp, int64_t *slice_off,
+                                cudaStream_t st) {
+    const int32_t n_slices = n_pad / kSliceRows;
+    count_launches(2);
+    order_perm_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n, n_pad, perm, iperm);
+    slice_count_kernel<<<(unsigned)(((int64_t)n_slices * 32 + 255) / 256), 256, 0, st>>>(n, n_slices, split, row_ptr,
+                                                                                         perm, count);
+    const int64_t nb = (n_slices + kScanBlock - 1) / kScanBlock;
+    exclusive_scan(n_slices, count, slice_off, scan_tmp, scan_tmp + nb, st);
+    return cudaGetLastError();
+}
+
+int64_t order_layout_scan_words(int32_t n_slices) { return (n_slices + kScanBlock - 1) / kScanBlock + 1; }
 
 cudaError_t launch_window_sort(int32_t n, int32_t n_pad, int32_t sigma, const int64_t *row_ptr,
                                int32_t *perm, int32_t *iperm, cudaStream_t st) {
@@ -523,6 +729,11 @@ cudaError_t launch_spread(int32_t n_pad, const int64_t *slice_off, const uint32_
     const int64_t threads = (int64_t)n_slices * (kSliceRows / kSpreadLanes);
     if (threads == 0) return cudaSuccess;
     count_launches(1);
+    if (!lcol) {
+        spread_warp_kernel<<<(unsigned)((n_slices + kSpreadWarps - 1) / kSpreadWarps), 32 * kSpreadWarps, 0, st>>>(
+            n_slices, slice_off, rowinfo, len_mask, rowcls, sell_col, sell_w, sell_wb);
+        return cudaGetLastError();
+    }
     spread_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n_slices, slice_off, rowinfo, len_mask, rowcls,
                                                                      sell_col, lcol, halo_off, halo_idx, sell_w,
                                                                      sell_wb);

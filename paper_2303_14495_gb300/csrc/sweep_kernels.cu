@@ -201,6 +201,9 @@ energy_finalize_kernel(const double *__restrict__ partials, int n_parts, double 
                        int has_prev, RedOut *out, double *trace_F, double *trace_r) {
     __shared__ double sm[256][6];
     double t[6] = {0, 0, 0, 0, 0, 0};
+    // unrolled so that the loads of several partials are in flight at once
+    // (the additions keep their order)
+#pragma unroll 8
     for (int i = threadIdx.x; i < n_parts; i += 256)
 #pragma unroll
         for (int s = 0; s < 6; ++s) t[s] += partials[(size_t)i * kRedSlots + s];
@@ -232,6 +235,7 @@ template <int NT>
 __device__ __forceinline__ void power_reduce(const double *partials, int n_parts, double *scale, double *lambda) {
     __shared__ double sm[NT][3];
     double t[3] = {0, 0, 0};
+#pragma unroll 8
     for (int i = threadIdx.x; i < n_parts; i += NT)
 #pragma unroll
         for (int s = 0; s < 3; ++s) t[s] += __ldcg(partials + (size_t)i * kRedSlots + s);

@@ -121,3 +121,74 @@ def test_disconnected_and_tiny(driver):
     order = run(driver, 5, rp, col, 4, 4, 2)
     assert np.array_equal(np.sort(order), np.arange(5))
     assert np.all(order[:4] < 4) and order[4] == 4
+
+
+def bfs_blocks_reference(n, rp, col, block, chunk, window):
+    """The BFS-block rule restated node by node: inside each chunk, a search
+    starts at the lowest node not yet placed, pops nodes in FIFO order and
+    places each popped node, queueing its free in-chunk neighbours in column
+    order, until the block of `block` nodes is full; nodes still queued then
+    become free again.  A search that runs dry is followed by the next one in
+    the same block.  Then a stable sort by degree (descending) inside every
+    window of `window` positions."""
+    order = np.empty(n, np.int64)
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        m = c1 - c0
+        state = [0] * m
+        pos, seed = c0, 0
+        while pos < c1:
+            cnt = 0
+            while cnt < block and pos < c1:
+                while state[seed] == 2:
+                    seed += 1
+                queue, head = [seed], 0
+                state[seed] = 1
+                while head < len(queue) and cnt < block:
+                    v = queue[head]
+                    head += 1
+                    state[v] = 2
+                    order[pos] = v + c0
+                    pos += 1
+                    cnt += 1
+                    for j in col[rp[v + c0]:rp[v + c0 + 1]]:
+                        lj = int(j) - c0
+                        if 0 <= lj < m and state[lj] == 0:
+                            state[lj] = 1
+                            queue.append(lj)
+                for v in queue[head:]:
+                    state[v] = 0
+    deg = np.diff(rp)
+    for s in range(0, n, window):
+        w = order[s:s + window]
+        order[s:s + window] = w[np.argsort(-deg[w], kind="stable")]
+    return order.astype(np.int32)
+
+
+def random_csr(n, avg, seed, local=0):
+    """Symmetric random graph, strictly increasing columns; local > 0 draws
+    neighbours within +-local ids (long thin components), else anywhere."""
+    rng = np.random.default_rng(seed)
+    m = n * avg // 2
+    a = rng.integers(0, n, m)
+    b = (a + rng.integers(1, local + 1, m)) % n if local else rng.integers(0, n, m)
+    keep = a != b
+    e = np.unique(np.concatenate([np.stack([a[keep], b[keep]], 1), np.stack([b[keep], a[keep]], 1)]), axis=0)
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, e[:, 0] + 1, 1)
+    return np.cumsum(rp), e[:, 1].astype(np.int32)
+
+
+@pytest.mark.parametrize("n,avg,local,block,chunk,window", [
+    (3000, 6, 0, 64, 512, 32), (2500, 4, 3, 32, 1024, 16), (700, 10, 0, 128, 256, 128),
+    (2000, 3, 0, 16, 128, 8), (1, 0, 0, 8, 8, 4)])
+def test_locality_order_matches_rule(driver, n, avg, local, block, chunk, window):
+    """The exact order of the host implementation against the rule written
+    out node by node (several chunks, ragged last chunk, many small
+    components, long thin ones)."""
+    if n == 1:
+        rp, col = np.zeros(2, np.int64), np.zeros(0, np.int32)
+    else:
+        rp, col = random_csr(n, avg, seed=n + avg, local=local)
+    got = run(driver, n, rp, col, block, chunk, window)
+    np.testing.assert_array_equal(got, bfs_blocks_reference(n, rp, col, block, chunk, window))
