@@ -183,3 +183,97 @@ def image_graph_rows_crop(img: np.ndarray, p: int, r: int, k: int, sigma: float,
         gy, gx = cc // Wc + y0, cc % Wc + x0
         out[i] = ((gy * W + gx).astype(np.int32), w[rp[ic]:rp[ic + 1]].copy())
     return out
+
+
+# ---------------------------------------------------------------------------
+# FP64 definition and the properties any FP32 builder must satisfy
+# ---------------------------------------------------------------------------
+def window_d2_f64(img: np.ndarray, p: int, r: int):
+    """(D, offs): D[i, m] = the patch distance of pixel i to its window partner
+    at offset offs[m], in FP64 (the FP32 pixel values are exact in FP64, the
+    differences and squares nearly so); +inf where the partner is outside."""
+    img = np.ascontiguousarray(img, np.float64)
+    H, W, C = img.shape
+    P = np.pad(img, ((p, p), (p, p), (0, 0)), mode="edge")
+    offs = [(dy, dx) for dy in range(-r, r + 1) for dx in range(-r, r + 1) if (dy, dx) != (0, 0)]
+    Hp, Wp = P.shape[:2]
+    cols = []
+    for dy, dx in offs:
+        acc = np.zeros((H, W), np.float64)
+        for oy in range(-p, p + 1):
+            for ox in range(-p, p + 1):
+                A = P[p + oy:p + oy + H, p + ox:p + ox + W, :]
+                yb = np.clip(np.arange(H) + p + oy + dy, 0, Hp - 1)
+                xb = np.clip(np.arange(W) + p + ox + dx, 0, Wp - 1)
+                Bv = P[yb[:, None], xb[None, :], :]
+                acc += ((A - Bv) ** 2).sum(axis=2)
+        ys, xs = np.arange(H)[:, None] + dy, np.arange(W)[None, :] + dx
+        bad = (ys < 0) | (ys >= H) | (xs < 0) | (xs >= W)
+        cols.append(np.where(bad, np.inf, acc).ravel())
+    return np.stack(cols, axis=1), offs
+
+
+def check_against_f64(row_ptr, col, w, img: np.ndarray, p: int, r: int, k: int, sigma: float) -> dict:
+    """Check a window k-NN patch graph built in FP32 against the FP64
+    definition, where FP32 rounding cannot decide otherwise.
+
+    An FP32 sum of m = (2p+1)^2 C non-negative rounded squares of rounded
+    differences is within beta d2 of the exact sum, beta = (m + 4) 2^-24.  With
+    d_k and d_{k+1} the k-th and (k+1)-th smallest exact distances of pixel i:
+      * a partner closer than d_{k+1} (1 - 2 beta) is kept by i (fewer than
+        k + 1 partners lie below d_{k+1}, and they all round below the rest);
+      * a kept partner lies no farther than d_k + 2 beta d_{k+1}.
+    The graph must hold every edge (i, j) that i or j must keep, and only
+    edges that i or j may keep; weights exp(-d2 / sigma^2) within the FP32
+    error of d2 plus a few ulps.  Returns the share of pixels whose kept set
+    the FP64 distances decide alone (d_{k+1} - d_k > 4 beta d_{k+1})."""
+    img = np.ascontiguousarray(img, np.float32)
+    H, W, C = img.shape
+    n = H * W
+    D, offs = window_d2_f64(img, p, r)
+    m_terms = (2 * p + 1) ** 2 * C
+    beta = (m_terms + 4) * 2.0 ** -24
+    Ds = np.sort(D, axis=1)
+    dk = Ds[:, k - 1]
+    dk1 = Ds[:, k] if Ds.shape[1] > k else np.full(n, np.inf)
+    must_t = np.where(np.isfinite(dk1), dk1 * (1 - 2 * beta), np.inf)
+    may_t = np.where(np.isfinite(dk1), dk + 2 * beta * dk1, np.inf)
+    # partner index of every (pixel, offset)
+    ii = np.arange(n)
+    yy, xx = ii // W, ii % W
+    J = np.stack([(yy + dy) * W + (xx + dx) for dy, dx in offs], axis=1)
+    valid = np.isfinite(D)
+    Jc = np.where(valid, J, 0)
+    must = valid & ((D < must_t[:, None]) | (D < must_t[Jc]))
+    may = valid & ((D <= may_t[:, None]) | (D <= may_t[Jc]))
+    # the graph's edges as (pixel, offset) flags
+    row_ptr = np.asarray(row_ptr, np.int64)
+    col = np.asarray(col, np.int64)
+    rows = np.repeat(ii, np.diff(row_ptr))
+    dy = col // W - rows // W
+    dx = col % W - rows % W
+    if np.any((np.abs(dy) > r) | (np.abs(dx) > r) | (col == rows)):
+        raise AssertionError("an edge outside the window")
+    lut = {o: t for t, o in enumerate(offs)}
+    side = 2 * r + 1
+    table = np.full(side * side, -1, np.int64)
+    for (a, b), t in lut.items():
+        table[(a + r) * side + (b + r)] = t
+    oi = table[(dy + r) * side + (dx + r)]
+    have = np.zeros_like(valid)
+    have[rows, oi] = True
+    if np.any(must & ~have):
+        bad = np.argwhere(must & ~have)[:5]
+        raise AssertionError(f"edges that must be kept are missing: {[(int(a), int(J[a, b])) for a, b in bad]}")
+    if np.any(have & ~may):
+        bad = np.argwhere(have & ~may)[:5]
+        raise AssertionError(f"edges that no FP32 rounding can keep: {[(int(a), int(J[a, b])) for a, b in bad]}")
+    d = D[rows, oi]
+    ref = np.exp(-d / float(sigma) ** 2)
+    tol = ref * (beta * d / float(sigma) ** 2 + 4 * 2.0 ** -23)
+    err = np.abs(np.asarray(w, np.float64) - ref)
+    if np.any(err > tol):
+        t = int(np.argmax(err - tol))
+        raise AssertionError(f"weight {float(w[t])} against {float(ref[t])} at entry {t}")
+    decided = np.isfinite(dk1) & (dk1 - dk > 4 * beta * dk1)
+    return {"decided": float(np.mean(decided)), "edges": int(col.size)}

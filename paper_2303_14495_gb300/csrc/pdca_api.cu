@@ -51,8 +51,7 @@ struct Layout {
     size_t o_ovrp, o_ovcol, o_ovw, o_ovwb, o_ovidx, o_ovacc;   // overflow CSR and its pre-pass sums
     size_t o_mr, o_me[2];              // mixed precision: r (FP32) and the two corrections (16-bit)
     size_t o_srp, o_scol, o_sw, o_sdeg, o_sisd, o_smask, o_slab, o_scls, o_sscan = 0, o_skey = 0, o_sbfs = 0,
-        o_sinfo = 0, o_status;
-    bool power_copy = false;           // the create-time power method runs on a copy, beside the entry order
+        o_status;
     size_t persistent = 0, total = 0;
 };
 
@@ -354,15 +353,8 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     L.persistent = o;
     // create-time staging of the CSR input
     L.o_srp = take(8 * (nn + 1));
-    // the power method overlapping the entry order and the column
-    // compression reads a copy of the packed columns, weights and row words
-    // here (the CSR staging is dead by then)
-    L.power_copy = prm.precond == PDCA_RICHARDSON && prm.lambda_max <= 0 && prm.tiling != PDCA_TILING_ON &&
-                   (prm.entry_order == PDCA_ENTRIES_SPREAD || prm.columns == PDCA_COLUMNS_AUTO);
-    const size_t stage = L.power_copy ? std::max<size_t>((size_t)L.nnz, P) : (size_t)L.nnz;
-    L.o_scol = take(4 * stage);
-    L.o_sw = take(4 * stage);
-    L.o_sinfo = take(L.power_copy ? 4 * np : 0);
+    L.o_scol = take(4 * (size_t)L.nnz);
+    L.o_sw = take(4 * (size_t)L.nnz);
     L.o_sdeg = take(8 * nn);
     L.o_sisd = take(8 * nn);
     L.o_smask = take(nn);
@@ -1143,38 +1135,6 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
                          const_cast<__nv_bfloat16 *>(h->ov.wb), s_status, sm);
     if (pe != cudaSuccess) return fail(PDCA_ERR_CUDA);
     const bool c16 = !h->tiled && prm.columns == PDCA_COLUMNS_AUTO;
-    // The power method (Sec. 3.1) runs on the operator as packed (entries in
-    // CSR order, int32 columns), whatever the entry order and column format
-    // chosen after it, so that every layout gets the same estimate.  Where
-    // the entry order or the compression rewrite the arrays, it reads a copy
-    // of them on a stream of its own while they run.
-    const bool power = prm.precond == PDCA_RICHARDSON && prm.lambda_max <= 0;
-    SideStream side;
-    if (power) {
-        if (!L.power_copy || h->tiled) {
-            st = power_launch(h, h->view(), h->tiles(), sm);
-            if (st != PDCA_OK) return fail(st);
-        } else {
-            int32_t *pc = reinterpret_cast<int32_t *>(W + L.o_scol);
-            float *pw = reinterpret_cast<float *>(W + L.o_sw);
-            uint32_t *pi = reinterpret_cast<uint32_t *>(W + L.o_sinfo);
-            SellView A = h->view();
-            A.col = pc;
-            A.col16 = nullptr;
-            A.slice_fmt = nullptr;
-            A.w = pw;
-            A.wb = nullptr;
-            A.rowinfo = pi;
-            if (cp(pc, h->sell_col, 4 * (size_t)L.sell_entries) != cudaSuccess ||
-                cp(pw, h->sell_w, 4 * (size_t)L.sell_entries) != cudaSuccess ||
-                cp(pi, h->rowinfo, 4 * (size_t)L.n_pad) != cudaSuccess || side.open() != cudaSuccess ||
-                cudaEventRecord(side.in, sm) != cudaSuccess || cudaStreamWaitEvent(side.s, side.in, 0) != cudaSuccess)
-                return fail(PDCA_ERR_CUDA);
-            st = power_launch(h, A, nullptr, side.s);
-            if (st != PDCA_OK) return fail(st);
-            if (cudaEventRecord(side.out, side.s) != cudaSuccess) return fail(PDCA_ERR_CUDA);
-        }
-    }
     if (prm.entry_order == PDCA_ENTRIES_SPREAD &&
         launch_spread(L.n_pad, h->slice_off, h->rowinfo, h->tiled ? 0xFFFFFFu : kLenMask, c16 ? s_cls : nullptr,
                       h->tiled ? nullptr : h->sell_col,
@@ -1191,8 +1151,7 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
         if (prm.lambda_max > 0) {
             h->lambda_used = prm.lambda_max;
         } else {
-            if (side.s && cudaStreamWaitEvent(sm, side.out, 0) != cudaSuccess) return fail(PDCA_ERR_CUDA);
-            st = power_read(h, sm);
+            st = power_method(h);
             if (st != PDCA_OK) return fail(st);
         }
         st = feasible(prm, omega, h->lambda_used, h->dmax);

@@ -489,120 +489,6 @@ __global__ void spread_kernel(int32_t n_slices, const int64_t *__restrict__ slic
                    sell_col, lcol, halo_off, halo_idx, sell_w, sell_wb);
 }
 
-// The same choices with the slice staged in shared memory (global columns,
-// slices up to kSpreadSmemW entries wide; wider ones take spread_quarter):
-// one warp per slice, the four quarters side by side.  At position p the
-// rows of a quarter take their turns in lane order as above; for the row
-// whose turn it is, the 8 lanes of its quarter examine 8 consecutive
-// candidates at once and the first acceptable one (lowest position) wins,
-// which is the candidate the sequential scan would stop at.  Lane q*8 + k
-// holds the group of slot k of quarter q.
-constexpr int kSpreadSmemW = 32;
-constexpr int kSpreadWarps = 4;
-
-__device__ __forceinline__ int32_t spread_loc(int32_t lane, int32_t j) {
-    return kSliceRows * kVec * (j / kVec) + kVec * lane + (j % kVec);
-}
-
-__global__ void __launch_bounds__(32 * kSpreadWarps)
-spread_warp_kernel(int32_t n_slices, const int64_t *__restrict__ slice_off, const uint32_t *__restrict__ rowinfo,
-                   uint32_t len_mask, const uint32_t *__restrict__ rowcls, int32_t *__restrict__ sell_col,
-                   float *__restrict__ sell_w, __nv_bfloat16 *__restrict__ sell_wb) {
-    constexpr int S = kSpreadLanes;
-    constexpr int E = kSliceRows * kSpreadSmemW;
-    constexpr unsigned kAll = 0xffffffffu;
-    __shared__ int32_t s_col[kSpreadWarps][E];
-    __shared__ float s_w[kSpreadWarps][E];
-    __shared__ __nv_bfloat16 s_wb[kSpreadWarps][E];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t s = (int64_t)blockIdx.x * kSpreadWarps + warp;
-    if (s >= n_slices) return;   // warp-uniform; the kernel has no block barrier
-    const int64_t base = slice_off[s];
-    const int64_t cnt = slice_off[s + 1] - base;
-    if (cnt > E) {
-        if (lane < kSliceRows / S)
-            spread_quarter(s, lane * S, slice_off, rowinfo, len_mask, rowcls, sell_col, nullptr, nullptr, nullptr,
-                           sell_w, sell_wb);
-        return;
-    }
-    int32_t *cs = s_col[warp];
-    float *ws = s_w[warp];
-    __nv_bfloat16 *bs = s_wb[warp];
-    for (int32_t i = lane; i < (int32_t)cnt; i += 32) {
-        cs[i] = sell_col[base + i];
-        ws[i] = sell_w[base + i];
-        if (sell_wb) bs[i] = sell_wb[base + i];
-    }
-    const int64_t r = s * kSliceRows + lane;
-    const int32_t my_len = (int32_t)((rowinfo[r] >> 8) & len_mask);
-    const uint32_t cls = rowcls ? rowcls[r] : 0u;
-    const int32_t my_np = (int32_t)(cls & 0xFFu), my_nb = my_np + (int32_t)((cls >> 8) & 0xFFu);
-    const int q = lane / S, sub = lane % S;
-    const int32_t maxlen = __reduce_max_sync(kAll, my_len);
-    int32_t grp_slot = 0;
-    bool moved = false;
-    __syncwarp();
-    for (int32_t p = 0; p < maxlen; ++p) {
-        uint32_t used = 0;   // the same in the 8 lanes of a quarter
-        for (int l = 0; l < S; ++l) {
-            const int R = q * S + l;
-            const int32_t len = __shfl_sync(kAll, my_len, R);
-            const int32_t np = __shfl_sync(kAll, my_np, R);
-            const int32_t nb = __shfl_sync(kAll, my_nb, R);
-            const bool active = p < len;
-            // the entry stays inside its band (previous, next, own chunk)
-            const int32_t band_end = p < np ? np : (p < nb ? nb : len);
-            const int32_t lim = min(band_end, p + kSpreadLook);
-            int32_t pick = -1, pslot = 0, pgrp = 0;
-            bool pending = active;
-            for (int32_t j0 = p; __any_sync(kAll, pending); j0 += S) {
-                const int32_t j = j0 + sub;
-                const bool valid = pending && j < lim;
-                const int32_t c = valid ? cs[spread_loc(R, j)] : 0;
-                const int32_t slot = c % S, grp = c / S;
-                const int32_t g_at = __shfl_sync(kAll, grp_slot, q * S + slot);
-                const bool ok = valid && (!((used >> slot) & 1u) || g_at == grp);
-                const uint32_t bits = (__ballot_sync(kAll, ok) >> (q * S)) & ((1u << S) - 1u);
-                const int f = bits ? __ffs(bits) - 1 : 0;
-                const int32_t fslot = __shfl_sync(kAll, slot, q * S + f);
-                const int32_t fgrp = __shfl_sync(kAll, grp, q * S + f);
-                if (pending && bits) {
-                    pick = j0 + f;
-                    pslot = fslot;
-                    pgrp = fgrp;
-                }
-                if (pending && (bits || j0 + S >= lim)) pending = false;
-            }
-            if (active && pick >= 0) {
-                if (!((used >> pslot) & 1u)) {
-                    used |= 1u << pslot;
-                    if (sub == pslot) grp_slot = pgrp;
-                }
-                if (pick != p) {
-                    moved = true;
-                    if (sub == 0) {
-                        const int32_t a = spread_loc(R, p), b = spread_loc(R, pick);
-                        const int32_t xc = cs[a]; cs[a] = cs[b]; cs[b] = xc;
-                        const float xw = ws[a]; ws[a] = ws[b]; ws[b] = xw;
-                        if (sell_wb) {
-                            const __nv_bfloat16 xb = bs[a];
-                            bs[a] = bs[b];
-                            bs[b] = xb;
-                        }
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    }
-    if (!__any_sync(kAll, moved)) return;
-    for (int32_t i = lane; i < (int32_t)cnt; i += 32) {
-        sell_col[base + i] = cs[i];
-        sell_w[base + i] = ws[i];
-        if (sell_wb) sell_wb[base + i] = bs[i];
-    }
-}
-
 // Row tags of a problem that shares another problem's operator: the row
 // lengths come from the base's rowinfo, the tags from the new fidelity data
 // (original node order, checked like the validation kernel does).
@@ -729,11 +615,6 @@ cudaError_t launch_spread(int32_t n_pad, const int64_t *slice_off, const uint32_
     const int64_t threads = (int64_t)n_slices * (kSliceRows / kSpreadLanes);
     if (threads == 0) return cudaSuccess;
     count_launches(1);
-    if (!lcol) {
-        spread_warp_kernel<<<(unsigned)((n_slices + kSpreadWarps - 1) / kSpreadWarps), 32 * kSpreadWarps, 0, st>>>(
-            n_slices, slice_off, rowinfo, len_mask, rowcls, sell_col, sell_w, sell_wb);
-        return cudaGetLastError();
-    }
     spread_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n_slices, slice_off, rowinfo, len_mask, rowcls,
                                                                      sell_col, lcol, halo_off, halo_idx, sell_w,
                                                                      sell_wb);

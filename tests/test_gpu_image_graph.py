@@ -5,7 +5,11 @@ to 1e-6 relative (the oracle takes exp in FP64 of the same FP32 distance and
 rounds to float32; the kernel evaluates it in FP32 with a correction for the
 rounding of the exponent, a few float32 ulps from the oracle).  The kept
 neighbours are decided by FP32 distances computed in the same order on both
-sides, so ties (constant patches) must break identically.
+sides, so ties (constant patches) must break identically.  Independently of
+that shared order, the GPU graphs also meet the FP64 definition wherever
+FP32 rounding cannot decide otherwise (check_against_f64: edges that must be
+kept are present, only edges that may be kept appear, weights within the
+FP32 error of the distance).
 """
 
 import time
@@ -67,6 +71,21 @@ def test_workload_images(B, kind):
         img, _ = voronoi_image(128, 16, 4, 0.15, rng)
         r = 7
     assert_same_graph(gpu_graph(B, img, 1, r, 10, 0.5), IG.image_graph(img, 1, r, 10, 0.5))
+
+
+@pytest.mark.parametrize("kind,shape,p,r,k", [("random", (48, 40, 3), 1, 4, 10), ("random", (33, 31, 1), 2, 5, 12),
+                                              ("ellipses", (96, 96, 3), 1, 5, 10), ("voronoi", (96, 96, 3), 1, 7, 10)])
+def test_fp64_definition(B, kind, shape, p, r, k):
+    rng = np.random.default_rng(SEED_BASE + 7 + shape[0])
+    if kind == "random":
+        img = rng.uniform(size=shape).astype(np.float32)
+    elif kind == "ellipses":
+        img, _ = ellipse_image(shape[0], 6, 0.1, rng)
+    else:
+        img, _ = voronoi_image(shape[0], 16, 4, 0.15, rng)
+    st = IG.check_against_f64(*gpu_graph(B, img, p, r, k, 0.5), img, p, r, k, 0.5)
+    print(f"{kind} {shape}: {st['decided']:.3f} of the rows decided by FP64 distances alone")
+    assert st["decided"] > 0.5, st
 
 
 def test_voronoi2048_spot_rows(B):

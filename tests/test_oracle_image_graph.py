@@ -89,3 +89,47 @@ def test_crop_rows_equal_full():
     for i in rows:
         np.testing.assert_array_equal(got[i][0], col[rp[i]:rp[i + 1]])
         np.testing.assert_array_equal(got[i][1], w[rp[i]:rp[i + 1]])
+
+
+@pytest.mark.parametrize("shape,p,r,k", [((17, 23, 3), 1, 2, 6), ((30, 26, 3), 1, 4, 10), ((12, 40, 1), 2, 3, 8)])
+def test_fp32_definition_within_fp64_bounds(shape, p, r, k):
+    """The FP32 definition (patch sums in a fixed order) satisfies the FP64
+    definition's bounds: an independent check of the builder's rounding, with
+    most rows decided by the FP64 distances alone."""
+    rng = np.random.default_rng(sum(shape) + k)
+    img = rng.uniform(size=shape).astype(np.float32)
+    rp, col, w = IG.image_graph(img, p, r, k, 0.5)
+    st = IG.check_against_f64(rp, col, w, img, p, r, k, 0.5)
+    assert st["decided"] > 0.9, st
+
+
+def test_fp64_check_catches_planted_mistakes():
+    """A dropped edge, an edge to a far partner and a wrong weight each fail."""
+    rng = np.random.default_rng(5)
+    img = rng.uniform(size=(20, 20, 3)).astype(np.float32)
+    rp, col, w = IG.image_graph(img, 1, 3, 6, 0.5)
+    IG.check_against_f64(rp, col, w, img, 1, 3, 6, 0.5)
+    # drop the nearest partner of pixel 50
+    D, offs = IG.window_d2_f64(img, 1, 3)
+    y, x = divmod(50, 20)
+    dy, dx = offs[int(np.argmin(D[50]))]
+    j = (y + dy) * 20 + (x + dx)
+    keep = np.ones(col.size, bool)
+    keep[rp[50] + int(np.searchsorted(col[rp[50]:rp[51]], j))] = False
+    keep[rp[j] + int(np.searchsorted(col[rp[j]:rp[j + 1]], 50))] = False
+    rows = np.repeat(np.arange(400), np.diff(rp))[keep]
+    rp2 = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=400))])
+    with pytest.raises(AssertionError, match="must be kept"):
+        IG.check_against_f64(rp2, col[keep], w[keep], img, 1, 3, 6, 0.5)
+    # a wrong weight
+    w2 = w.copy()
+    w2[7] *= 1.001
+    with pytest.raises(AssertionError, match="weight"):
+        IG.check_against_f64(rp, col, w2, img, 1, 3, 6, 0.5)
+    # the farthest partner of pixel 50 replacing its nearest (both directions)
+    far = offs[int(np.argmax(np.where(np.isfinite(D[50]), D[50], -1)))]
+    jf = (y + far[0]) * 20 + (x + far[1])
+    col3 = col.copy()
+    col3[rp[50] + int(np.searchsorted(col[rp[50]:rp[51]], j))] = jf
+    with pytest.raises(AssertionError):
+        IG.check_against_f64(rp, col3, w, img, 1, 3, 6, 0.5)
