@@ -10,15 +10,20 @@
 // sliced-ELL operator the sweeps use, with every block kept orthogonal to q
 // (A maps that complement to itself).  The block holds the m = 4 lowest
 // eigenpairs of the complement.  Every iteration:
-//   R = A X - X Theta;  W = R orthonormalised against X (twice) and itself;
-//   P (the previous search direction) orthonormalised against X and W;
-//   Rayleigh-Ritz on S = [X W P]: the m smallest eigenpairs of S^T A S;
-//   X <- S C, P <- [W P] C_{W,P}, with A X, A P updated by the same
-//   coefficients (one SpMM per iteration, for A W).
+//   R = A X - X Theta, deflated against q;
+//   Rayleigh-Ritz on S = [X R P] (P the previous search direction) from the
+//   Gram blocks G = S^T S and H = S^T A S, all formed in one batch: with
+//   D = diag(G)^-1/2 and D G D = L L^T, the m smallest eigenpairs of
+//   L^-1 D H D L^-T give the coefficients C (without P when D G D is not
+//   numerically positive definite);
+//   X <- S C, P <- [R P] C_{R,P}, with A X, A P updated by the same
+//   coefficients (one SpMM per iteration, for A R).
+// Every 10 iterations X and P are deflated again and X re-orthonormalised.
 // Device work: the SpMM, 4x4 Gram blocks U^T V (FP64 accumulation, fixed
-// block order, so results are deterministic) and linear combinations of
-// n x 4 blocks.  Host work: the small dense symmetric eigenproblems (cyclic
-// Jacobi rotations) and Cholesky factors, in FP64.
+// block order, the block partials added on the device, so results are
+// deterministic) and linear combinations of n x 4 blocks.  Host work: the
+// small dense symmetric eigenproblems (cyclic Jacobi rotations) and Cholesky
+// factors, in FP64; two waits for the device per iteration.
 #include "device_common.cuh"
 
 #include <math.h>
@@ -35,7 +40,7 @@ using namespace dev;
 constexpr int kM = 4;                       // block size
 constexpr int kGramBlocks = 2 * kSmCount;   // fixed grid of the Gram kernel
 constexpr int kGramSlots = 16;              // Gram products per launch slot
-constexpr int kMaxGrams = 8;                // Gram launches per synchronisation
+constexpr int kMaxGrams = 16;               // Gram launches per synchronisation
 
 // Y = L X for n_pad x 4 FP32 blocks (renumbered rows; padding rows stay 0).
 // (FP32 weights, which every problem keeps whatever its precision.)
@@ -63,9 +68,19 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-// partial[block][4 i + j] = sum over this block's rows of U[r][i] V[r][j]
+// The Gram products queued before a wait, launched together: product s of
+// the table in blockIdx.y.
+struct GramTable {
+    const float *u[kMaxGrams];
+    const float *v[kMaxGrams];
+};
+
+// partial[s][block][4 i + j] = sum over this block's rows of U_s[r][i] V_s[r][j]
 __global__ void __launch_bounds__(256)
-gram4_kernel(int32_t rows, const float *__restrict__ u, const float *__restrict__ v, double *__restrict__ partial) {
+gram4_kernel(int32_t rows, const __grid_constant__ GramTable t, double *__restrict__ partial_all) {
+    const float *__restrict__ u = t.u[blockIdx.y];
+    const float *__restrict__ v = t.v[blockIdx.y];
+    double *__restrict__ partial = partial_all + (size_t)blockIdx.y * kGramBlocks * kGramSlots;
     double acc[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] = 0.0;
@@ -94,6 +109,16 @@ gram4_kernel(int32_t rows, const float *__restrict__ u, const float *__restrict_
     }
 }
 
+// sums[s][q] = the kGramBlocks block partials of Gram slot s added in block
+// order (one thread per entry, the order of a plain loop)
+__global__ void __launch_bounds__(kGramSlots)
+gram_sum_kernel(const double *__restrict__ partial, double *__restrict__ sums) {
+    const double *p = partial + (size_t)blockIdx.x * kGramBlocks * kGramSlots + threadIdx.x;
+    double t = 0.0;
+    for (int b = 0; b < kGramBlocks; ++b) t += p[(size_t)b * kGramSlots];
+    sums[(size_t)blockIdx.x * kGramSlots + threadIdx.x] = t;
+}
+
 struct Coef3 {
     float c[3][16];   // row-major 4 x 4 blocks
 };
@@ -117,6 +142,38 @@ combine4_kernel(int32_t rows, float *__restrict__ out, const float *__restrict__
             for (int j = 0; j < 4; ++j) o[j] = fmaf(x[i], cf.c[b][4 * i + j], o[j]);
     }
     reinterpret_cast<float4 *>(out)[r] = make_float4(o[0], o[1], o[2], o[3]);
+}
+
+// Up to four combinations of up to four blocks each in one launch (output o
+// in blockIdx.y).
+struct Coef4 {
+    float c[4][16];   // row-major 4 x 4 blocks
+};
+
+struct CombTable {
+    float *out[4];
+    const float *u[4][4];
+    Coef4 cf[4];
+};
+
+__global__ void __launch_bounds__(256)
+combine4_multi_kernel(int32_t rows, const __grid_constant__ CombTable t) {
+    const int32_t r = blockIdx.x * 256 + threadIdx.x;
+    if (r >= rows) return;
+    const int o_ix = blockIdx.y;
+    float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const float *src = t.u[o_ix][b];
+        if (!src) continue;
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(src) + r);
+        const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) o[j] = fmaf(x[i], t.cf[o_ix].c[b][4 * i + j], o[j]);
+    }
+    reinterpret_cast<float4 *>(t.out[o_ix])[r] = make_float4(o[0], o[1], o[2], o[3]);
 }
 
 // Start block: column j of row r is a fixed function of the caller's node
@@ -294,6 +351,97 @@ bool ortho_coeffs(const double *g, double *cmat) {
     return true;
 }
 
+// Rayleigh-Ritz on the basis S = [X R P] (nb blocks of 4 columns) from the
+// Gram blocks G = S^T S and H = S^T A S: with D = diag(G)^-1/2, a Cholesky
+// factorisation L L^T of D G D that leaves out, in column order, every
+// column of norm below 1e-12 (a zero residual column of a converged Ritz
+// vector) or whose pivot falls below 1e-8 (a direction already in the span
+// of the earlier ones), the m smallest eigenpairs (y, theta) of L^-1 D H D L^-T on the kept
+// columns give the coefficients D L^-T y of the new X in S (0 for the left
+// out columns).  False when fewer than m columns are kept.
+bool ritz_coeffs(const std::vector<std::vector<double>> &g, const int (&gs)[3][3], const int (&hs)[3][3], int nb,
+                 std::vector<double> &cb, std::vector<double> &theta) {
+    const int ns = 4 * nb;
+    std::vector<double> G((size_t)ns * ns), H((size_t)ns * ns);
+    for (int bi = 0; bi < nb; ++bi)
+        for (int bj = bi; bj < nb; ++bj) {
+            const std::vector<double> &gg = g[gs[bi][bj]], &hh = g[hs[bi][bj]];
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    const double x = bi == bj ? 0.5 * (gg[4 * i + j] + gg[4 * j + i]) : gg[4 * i + j];
+                    const double y = bi == bj ? 0.5 * (hh[4 * i + j] + hh[4 * j + i]) : hh[4 * i + j];
+                    G[(size_t)(4 * bi + i) * ns + 4 * bj + j] = G[(size_t)(4 * bj + j) * ns + 4 * bi + i] = x;
+                    H[(size_t)(4 * bi + i) * ns + 4 * bj + j] = H[(size_t)(4 * bj + j) * ns + 4 * bi + i] = y;
+                }
+        }
+    std::vector<double> d(ns, 0.0);
+    for (int k = 0; k < ns; ++k) {
+        const double gk = G[(size_t)k * ns + k];
+        if (gk > 1e-24 && std::isfinite(gk)) d[k] = 1.0 / sqrt(gk);   // X columns have unit norm
+    }
+    // Cholesky of D G D over the kept columns (act), in column order
+    std::vector<int> act;
+    std::vector<double> L;   // row-major over kept columns, grown as kept
+    for (int k = 0; k < ns; ++k) {
+        if (d[k] == 0.0) continue;
+        const int na = (int)act.size();
+        std::vector<double> row(na + 1, 0.0);
+        double t = 1.0;   // the scaled diagonal
+        for (int m = 0; m < na; ++m) {
+            double u = G[(size_t)k * ns + act[m]] * d[k] * d[act[m]];
+            for (int p2 = 0; p2 < m; ++p2) u -= row[p2] * L[(size_t)m * ns + p2];
+            row[m] = u / L[(size_t)m * ns + m];
+            t -= row[m] * row[m];
+        }
+        if (!(t > 1e-8)) continue;
+        row[na] = sqrt(t);
+        L.resize((size_t)(na + 1) * ns, 0.0);
+        for (int m = 0; m <= na; ++m) L[(size_t)na * ns + m] = row[m];
+        act.push_back(k);
+    }
+    const int na = (int)act.size();
+    if (na < kM) return false;
+    // Li = L^-1 (lower), by forward substitution column by column
+    std::vector<double> Li((size_t)na * na, 0.0);
+    for (int j = 0; j < na; ++j) {
+        Li[(size_t)j * na + j] = 1.0 / L[(size_t)j * ns + j];
+        for (int i = j + 1; i < na; ++i) {
+            double u = 0.0;
+            for (int k = j; k < i; ++k) u += L[(size_t)i * ns + k] * Li[(size_t)k * na + j];
+            Li[(size_t)i * na + j] = -u / L[(size_t)i * ns + i];
+        }
+    }
+    // M = Li (D H D)_act Li^T
+    std::vector<double> Hs((size_t)na * na), T1((size_t)na * na, 0.0), M((size_t)na * na, 0.0);
+    for (int i = 0; i < na; ++i)
+        for (int j = 0; j < na; ++j)
+            Hs[(size_t)i * na + j] = H[(size_t)act[i] * ns + act[j]] * d[act[i]] * d[act[j]];
+    for (int i = 0; i < na; ++i)
+        for (int j = 0; j < na; ++j) {
+            double u = 0.0;
+            for (int k = 0; k <= i; ++k) u += Li[(size_t)i * na + k] * Hs[(size_t)k * na + j];
+            T1[(size_t)i * na + j] = u;
+        }
+    for (int i = 0; i < na; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double u = 0.0;
+            for (int k = 0; k <= j; ++k) u += T1[(size_t)i * na + k] * Li[(size_t)j * na + k];
+            M[(size_t)i * na + j] = M[(size_t)j * na + i] = u;
+        }
+    std::vector<double> w, v;
+    jacobi_eigen(na, M, w, v);
+    // coefficients D Li^T y for the m smallest, on the kept columns
+    cb.assign((size_t)ns * kM, 0.0);
+    for (int i = 0; i < na; ++i)
+        for (int j = 0; j < kM; ++j) {
+            double u = 0.0;
+            for (int k = i; k < na; ++k) u += Li[(size_t)k * na + i] * v[(size_t)k * na + j];
+            cb[(size_t)act[i] * kM + j] = d[act[i]] * u;
+        }
+    for (int j = 0; j < kM; ++j) theta[j] = w[j];
+    return true;
+}
+
 struct Ctx {
     SellView A;
     OverflowView O;
@@ -301,7 +449,9 @@ struct Ctx {
     int32_t n, n_pad;
     bool un;
     double *partial;          // kMaxGrams x kGramBlocks x 16 (device)
-    std::vector<double> host; // the same on the host
+    double *sums;             // kMaxGrams x 16 (device)
+    GramTable table{};        // the products queued since the last wait
+    std::vector<double> host; // the sums on the host
     int pending = 0;
     bool overflow = false;
 };
@@ -317,29 +467,36 @@ cudaError_t spmm(Ctx &c, const float *x, float *y) {
     return cudaGetLastError();
 }
 
-// queue U^T V; returns its slot
+// queue U^T V (launched at the next wait); returns its slot
 int gram(Ctx &c, const float *u, const float *v) {
-    if (c.pending >= kMaxGrams) {   // never expected: every step queues at most 6
+    if (c.pending >= kMaxGrams) {   // never expected: every step queues at most 12
         c.overflow = true;
         return 0;
     }
     const int slot = c.pending++;
-    count_launches(1);
-    gram4_kernel<<<kGramBlocks, 256, 0, c.st>>>(c.n_pad, u, v, c.partial + (size_t)slot * kGramBlocks * kGramSlots);
+    c.table.u[slot] = u;
+    c.table.v[slot] = v;
     return slot;
 }
 
 // wait for the queued Grams; g[slot] = 4 x 4 result (row-major)
 cudaError_t gram_wait(Ctx &c, std::vector<std::vector<double>> &g) {
     if (c.overflow) return cudaErrorInvalidValue;
-    const size_t cnt = (size_t)c.pending * kGramBlocks * kGramSlots;
-    cudaError_t e = cudaMemcpyAsync(c.host.data(), c.partial, cnt * sizeof(double), cudaMemcpyDeviceToHost, c.st);
+    if (c.pending == 0) {
+        g.clear();
+        return cudaSuccess;
+    }
+    count_launches(2);
+    gram4_kernel<<<dim3(kGramBlocks, c.pending), 256, 0, c.st>>>(c.n_pad, c.table, c.partial);
+    gram_sum_kernel<<<c.pending, kGramSlots, 0, c.st>>>(c.partial, c.sums);
+    cudaError_t e = cudaGetLastError();
+    const size_t cnt = (size_t)c.pending * kGramSlots;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.host.data(), c.sums, cnt * sizeof(double), cudaMemcpyDeviceToHost, c.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
     if (e != cudaSuccess) return e;
     g.assign(c.pending, std::vector<double>(16, 0.0));
     for (int s = 0; s < c.pending; ++s)
-        for (int b = 0; b < kGramBlocks; ++b)
-            for (int q = 0; q < 16; ++q) g[s][q] += c.host[((size_t)s * kGramBlocks + b) * kGramSlots + q];
+        for (int q = 0; q < 16; ++q) g[s][q] = c.host[(size_t)s * kGramSlots + q];
     c.pending = 0;
     return cudaSuccess;
 }
@@ -352,6 +509,28 @@ cudaError_t combine(Ctx &c, float *out, const float *u0, const double *c0, const
         for (int q = 0; q < 16; ++q) cf.c[b][q] = cs[b] ? (float)cs[b][q] : 0.0f;
     count_launches(1);
     combine4_kernel<<<(c.n_pad + 255) / 256, 256, 0, c.st>>>(c.n_pad, out, u0, u1, u2, cf);
+    return cudaGetLastError();
+}
+
+// The four updates of an iteration (new X, A X, P, A P) in one launch; each
+// entry: output, up to three inputs and their coefficient blocks.
+struct CombSpec {
+    float *out;
+    const float *u[4];
+    const double *c[4];
+};
+
+cudaError_t combine_four(Ctx &c, const CombSpec (&sp)[4]) {
+    CombTable t{};
+    for (int o = 0; o < 4; ++o) {
+        t.out[o] = sp[o].out;
+        for (int b = 0; b < 4; ++b) {
+            t.u[o][b] = sp[o].u[b];
+            for (int q = 0; q < 16; ++q) t.cf[o].c[b][q] = sp[o].c[b] ? (float)sp[o].c[b][q] : 0.0f;
+        }
+    }
+    count_launches(1);
+    combine4_multi_kernel<<<dim3((c.n_pad + 255) / 256, 4), 256, 0, c.st>>>(c.n_pad, t);
     return cudaGetLastError();
 }
 
@@ -369,7 +548,7 @@ constexpr int kBufs = 13;
 
 size_t spectral_workspace_bytes(int32_t n_pad) {
     const size_t blk = ((size_t)n_pad * kM * sizeof(float) + 255) / 256 * 256;
-    return kBufs * blk + (size_t)kMaxGrams * kGramBlocks * kGramSlots * sizeof(double) + 3 * 256 * 4;
+    return kBufs * blk + (size_t)kMaxGrams * (kGramBlocks + 1) * kGramSlots * sizeof(double) + 3 * 256 * 4;
 }
 
 pdca_status spectral_eigvec(const SellView &A, const OverflowView &O, bool un, const float *q, const int32_t *perm, int32_t n,
@@ -388,8 +567,9 @@ pdca_status spectral_eigvec(const SellView &A, const OverflowView &O, bool un, c
     c.n_pad = n_pad;
     c.un = un;
     c.partial = reinterpret_cast<double *>(W + kBufs * blk);
-    c.host.assign((size_t)kMaxGrams * kGramBlocks * kGramSlots, 0.0);
-    float *bmax = reinterpret_cast<float *>(W + kBufs * blk + (size_t)kMaxGrams * kGramBlocks * kGramSlots * 8);
+    c.sums = c.partial + (size_t)kMaxGrams * kGramBlocks * kGramSlots;
+    c.host.assign((size_t)kMaxGrams * kGramSlots, 0.0);
+    float *bmax = reinterpret_cast<float *>(W + kBufs * blk + (size_t)kMaxGrams * (kGramBlocks + 1) * kGramSlots * 8);
     int32_t *bidx = reinterpret_cast<int32_t *>(bmax + 256);
     int32_t *brow = bidx + 256;
     float *X = buf[0], *AX = buf[1], *Wb = buf[2], *AW = buf[3], *P = buf[4], *AP = buf[5];
@@ -450,101 +630,11 @@ pdca_status spectral_eigvec(const SellView &A, const OverflowView &O, bool un, c
             std::swap(AX, T[1]);
             theta = w;
         }
-        // residual block R = AX - X diag(theta) (into W), and its column norms
-        double mth[16] = {0};
-        for (int i = 0; i < 4; ++i) mth[5 * i] = -theta[i];
-        SP_TRY(combine(c, Wb, AX, kIdentity, X, mth));
-        SP_TRY(deflate(Wb, T[0]));
-        gram(c, Wb, Wb);
-        gram(c, X, Wb);
-        SP_TRY(gram_wait(c, g));
-        const double r0 = sqrt(std::max(0.0, g[0][0]));
-        if (r0 <= tol) {
-            converged = true;
-            break;
-        }
-        if (it == max_iters) break;
-        // W <- W - X (X^T W), twice, then orthonormal
-        double cxw[16];
-        for (int q = 0; q < 16; ++q) cxw[q] = -g[1][q];
-        SP_TRY(combine(c, T[0], Wb, kIdentity, X, cxw));
-        std::swap(Wb, T[0]);
-        gram(c, X, Wb);
-        SP_TRY(gram_wait(c, g));
-        for (int q = 0; q < 16; ++q) cxw[q] = -g[0][q];
-        SP_TRY(combine(c, T[0], Wb, kIdentity, X, cxw));
-        std::swap(Wb, T[0]);
-        gram(c, Wb, Wb);
-        SP_TRY(gram_wait(c, g));
-        double rw[16];
-        if (!ortho_coeffs(g[0].data(), rw)) break;   // the residual block lost rank: as converged as FP32 allows
-        SP_TRY(combine(c, T[0], Wb, rw));
-        std::swap(Wb, T[0]);
-        SP_TRY(spmm(c, Wb, AW));
-        // P <- P - X (X^T P) - W (W^T P), orthonormal; A P follows
-        if (hasP) {
-            gram(c, X, P);
-            gram(c, Wb, P);
-            SP_TRY(gram_wait(c, g));
-            double cx[16], cw[16];
-            for (int q = 0; q < 16; ++q) {
-                cx[q] = -g[0][q];
-                cw[q] = -g[1][q];
-            }
-            SP_TRY(combine(c, T[0], P, kIdentity, X, cx, Wb, cw));
-            SP_TRY(combine(c, T[1], AP, kIdentity, AX, cx, AW, cw));
-            std::swap(P, T[0]);
-            std::swap(AP, T[1]);
-            gram(c, P, P);
-            SP_TRY(gram_wait(c, g));
-            double rp[16];
-            if (ortho_coeffs(g[0].data(), rp)) {
-                SP_TRY(combine(c, T[0], P, rp));
-                SP_TRY(combine(c, T[1], AP, rp));
-                std::swap(P, T[0]);
-                std::swap(AP, T[1]);
-            } else {
-                hasP = false;   // restart without the previous direction
-            }
-        }
-        // Rayleigh-Ritz on S = [X W P]
-        const int nb = hasP ? 3 : 2, ns = 4 * nb;
-        const float *S[3] = {X, Wb, P}, *AS[3] = {AX, AW, AP};
-        int slot[3][3];
-        for (int i = 0; i < nb; ++i)
-            for (int j = i; j < nb; ++j) slot[i][j] = gram(c, S[i], AS[j]);
-        SP_TRY(gram_wait(c, g));
-        std::vector<double> a((size_t)ns * ns), w, v;
-        for (int bi = 0; bi < nb; ++bi)
-            for (int bj = bi; bj < nb; ++bj) {
-                const std::vector<double> &G = g[slot[bi][bj]];   // S_bi^T A S_bj
-                for (int i = 0; i < 4; ++i)
-                    for (int j = 0; j < 4; ++j) {
-                        const double x = bi == bj ? 0.5 * (G[4 * i + j] + G[4 * j + i]) : G[4 * i + j];
-                        a[(size_t)(4 * bi + i) * ns + 4 * bj + j] = x;
-                        a[(size_t)(4 * bj + j) * ns + 4 * bi + i] = x;
-                    }
-            }
-        jacobi_eigen(ns, a, w, v);
-        double cb[3][16];
-        for (int b = 0; b < nb; ++b)
-            for (int i = 0; i < 4; ++i)
-                for (int j = 0; j < 4; ++j) cb[b][4 * i + j] = v[(size_t)(4 * b + i) * ns + j];
-        for (int j = 0; j < 4; ++j) theta[j] = w[j];
-        // new X, A X, P, A P
-        SP_TRY(combine(c, T[0], X, cb[0], Wb, cb[1], hasP ? P : nullptr, hasP ? cb[2] : nullptr));
-        SP_TRY(combine(c, T[1], AX, cb[0], AW, cb[1], hasP ? AP : nullptr, hasP ? cb[2] : nullptr));
-        SP_TRY(combine(c, T[2], Wb, cb[1], hasP ? P : nullptr, hasP ? cb[2] : nullptr));
-        SP_TRY(combine(c, T[3], AW, cb[1], hasP ? AP : nullptr, hasP ? cb[2] : nullptr));
-        std::swap(X, T[0]);
-        std::swap(AX, T[1]);
-        std::swap(P, T[2]);
-        std::swap(AP, T[3]);
-        hasP = true;
-        // keep X orthogonal to q and orthonormal against FP32 drift every 10
-        // iterations (A q = 0, so A X needs no deflation)
+        // keep X, P orthogonal to q and X orthonormal against FP32 drift every
+        // 10 iterations (A q = 0, so A X and A P need no deflation)
         if (it % 10 == 9) {
             SP_TRY(deflate(X, T[0]));
+            if (hasP) SP_TRY(deflate(P, T[0]));
             gram(c, X, X);
             SP_TRY(gram_wait(c, g));
             double rx[16];
@@ -554,6 +644,51 @@ pdca_status spectral_eigvec(const SellView &A, const OverflowView &O, bool un, c
             std::swap(X, T[0]);
             std::swap(AX, T[1]);
         }
+        // residual block R = AX - X diag(theta) (into W) and A R
+        double mth[16] = {0};
+        for (int i = 0; i < 4; ++i) mth[5 * i] = -theta[i];
+        SP_TRY(combine(c, Wb, AX, kIdentity, X, mth));
+        SP_TRY(deflate(Wb, T[0]));
+        SP_TRY(spmm(c, Wb, AW));
+        // every Gram block of S = [X R P] and S^T A S in one batch
+        const int nb = hasP ? 3 : 2;
+        const float *S[3] = {X, Wb, P}, *AS[3] = {AX, AW, AP};
+        int gs[3][3], hs[3][3];
+        for (int i = 0; i < nb; ++i)
+            for (int j = i; j < nb; ++j) {
+                gs[i][j] = gram(c, S[i], S[j]);
+                hs[i][j] = gram(c, S[i], AS[j]);
+            }
+        SP_TRY(gram_wait(c, g));
+        const double r0 = sqrt(std::max(0.0, g[gs[1][1]][0]));
+        if (r0 <= tol) {
+            converged = true;
+            break;
+        }
+        if (it == max_iters) break;
+        std::vector<double> cb;   // (4 nb) x 4 coefficients of the new X
+        int nbu = nb;
+        for (; nbu >= 2; --nbu) {   // with P, else without it when [X R P] is numerically dependent
+            if (ritz_coeffs(g, gs, hs, nbu, cb, theta)) break;
+        }
+        if (nbu < 2) break;   // R lies in span X numerically: as converged as FP32 allows
+        double cx[3][16] = {{0}};
+        for (int bb = 0; bb < nbu; ++bb)
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) cx[bb][4 * i + j] = cb[(size_t)(4 * bb + i) * 4 + j];
+        const bool useP = nbu == 3;
+        // new X, A X, P, A P
+        const CombSpec sp[4] = {
+            {T[0], {X, Wb, useP ? P : nullptr, nullptr}, {cx[0], cx[1], useP ? cx[2] : nullptr, nullptr}},
+            {T[1], {AX, AW, useP ? AP : nullptr, nullptr}, {cx[0], cx[1], useP ? cx[2] : nullptr, nullptr}},
+            {T[2], {Wb, useP ? P : nullptr, nullptr, nullptr}, {cx[1], useP ? cx[2] : nullptr, nullptr, nullptr}},
+            {T[3], {AW, useP ? AP : nullptr, nullptr, nullptr}, {cx[1], useP ? cx[2] : nullptr, nullptr, nullptr}}};
+        SP_TRY(combine_four(c, sp));
+        std::swap(X, T[0]);
+        std::swap(AX, T[1]);
+        std::swap(P, T[2]);
+        std::swap(AP, T[3]);
+        hasP = true;
     }
     if (!std::isfinite(theta[0])) return PDCA_ERR_NONFINITE;
     if (lambda2) *lambda2 = theta[0];
