@@ -10,6 +10,10 @@
 #include <thread>
 #include <vector>
 
+namespace pdca {
+int host_workers();   // threads host_parallel_for uses (reorder.cpp)
+}  // namespace pdca
+
 using namespace pdca;
 
 namespace {
@@ -293,7 +297,12 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     if (prm.reorder == PDCA_REORDER_BFS) {
         // the widths depend on the renumbering (computed at create); size for the bound
         L.host_order = true;
-        L.device_order = prm.tiling != PDCA_TILING_ON;   // the tiles' halos are built on the host
+        // One device block renumbers a chunk and one host thread does too;
+        // the device form pays off once the chunks outnumber the host's
+        // threads by more than twice (both give the same order).  The tiles'
+        // halo lists are built on the host.
+        const int64_t chunks = ((int64_t)n + kBfsChunk - 1) / kBfsChunk;
+        L.device_order = prm.tiling != PDCA_TILING_ON && chunks > 2 * (int64_t)host_workers();
         L.sigma = sigma_req && sigma_req <= kBfsBlock ? sigma_req : kBfsBlock;
         L.sell_entries = 0;
         L.sell_cap = sell_bound(rp, n, L.sigma, max_deg);
@@ -766,7 +775,7 @@ pdca_status host_renumber(pdca_problem *h, const int64_t *rp, OrderJob &job) {
     // PDCA_TILING_ON (on every workload measured on GB300 the plain kernels
     // were faster than the shared-memory tiles, so AUTO uses the plain ones):
     // the tiles' halo lists on the host
-    {
+    if (h->prm.tiling == PDCA_TILING_ON) {
         std::vector<int64_t> hoff;
         std::vector<int32_t> hidx;
         int32_t mx = 0;

@@ -97,6 +97,8 @@ void chunk_blocks(int64_t c0, int64_t c1, const int64_t *rp, const int32_t *col,
 
 void host_parallel_for(int64_t count, const std::function<void(int64_t)> &f) { parallel_for(count, f); }
 
+int host_workers() { return worker_count(); }
+
 void locality_order(int32_t n, const int64_t *rp, const int32_t *col, int32_t block, int32_t chunk,
                     int32_t sort_window, int32_t *order) {
     const int64_t nchunks = ((int64_t)n + chunk - 1) / chunk;
