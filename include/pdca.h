@@ -26,11 +26,15 @@
  *  - Every function returns a pdca_status; no C++ exception crosses it.
  *  - Pointers documented "host or device" may be either: the library asks
  *    the CUDA runtime which kind it is and copies accordingly.
- *  - The library allocates no device memory.  All device state lives in the
- *    caller's workspace (size from pdca_workspace_size), which the handle
- *    borrows until pdca_destroy; the caller frees it afterwards.
- *  - All device work of a handle runs on the stream given to pdca_create.
- *    Calls that return host values synchronise that stream.  Errors of
+ *  - The library allocates no device memory (one exception: the device form
+ *    of the inspection call pdca_locality_order).  All device state lives
+ *    in the caller's workspace (size from pdca_workspace_size), which the
+ *    handle borrows until pdca_destroy; the caller frees it afterwards.
+ *  - All device work of a handle runs on the stream given to pdca_create,
+ *    except that pdca_create may run its renumbering on a stream of its own:
+ *    ordered after the work the given stream holds when the call starts, and
+ *    finished, with the stream released, before the call returns.  Calls
+ *    that return host values synchronise that stream.  Errors of
  *    asynchronous kernels surface at the next synchronising call.
  *  - One handle must not be used from two host threads at once; separate
  *    handles on separate streams are independent.
