@@ -56,7 +56,7 @@ struct Layout {
     size_t o_mr, o_me[2];              // mixed precision: r (FP32) and the two corrections (16-bit)
     size_t o_srp, o_scol, o_sw, o_sdeg, o_sisd, o_smask, o_slab, o_scls, o_sscan = 0, o_skey = 0, o_sbfs = 0,
         o_status;
-    size_t persistent = 0, total = 0;
+    size_t total = 0;
 };
 
 // Upper bound of the padded entries for any renumbering that sorts rows by
@@ -266,6 +266,36 @@ int32_t split_length(const pdca_params &p, int64_t nnz, int64_t max_deg) {
     return kSplitMax;
 }
 
+// The first regions of a problem's workspace: the create-time copies of the
+// caller's CSR and fidelity data and the status words, at offsets that
+// depend on n and nnz only, so that the copies can start before the host has
+// checked the row offsets and worked out the layout.
+struct StageHead {
+    size_t o_srp, o_scol, o_sw, o_smask, o_slab, o_status, end;
+};
+
+StageHead stage_head(int32_t n, int64_t nnz) {
+    StageHead S;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + std::max<size_t>(bytes, 1)); return at; };
+    S.o_srp = take(8 * ((size_t)n + 1));
+    S.o_scol = take(4 * (size_t)nnz);
+    S.o_sw = take(4 * (size_t)nnz);
+    S.o_smask = take((size_t)n);
+    S.o_slab = take(4 * (size_t)n);
+    S.o_status = take(16);
+    S.end = o;
+    return S;
+}
+
+// The device renumbering pays off once the 65536-node chunks (serial work for
+// one device block, or for one host thread) outnumber the host's threads by
+// more than twice; the tiles' halo lists are built on the host.
+bool use_device_order(const pdca_params &prm, int32_t n) {
+    const int64_t chunks = ((int64_t)n + kBfsChunk - 1) / kBfsChunk;
+    return prm.reorder == PDCA_REORDER_BFS && prm.tiling != PDCA_TILING_ON && chunks > 2 * (int64_t)host_workers();
+}
+
 pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_params &prm, int64_t max_deg,
                            Layout &L) {
     const int32_t sigma_req = prm.sort_window;
@@ -297,12 +327,7 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     if (prm.reorder == PDCA_REORDER_BFS) {
         // the widths depend on the renumbering (computed at create); size for the bound
         L.host_order = true;
-        // One device block renumbers a chunk and one host thread does too;
-        // the device form pays off once the chunks outnumber the host's
-        // threads by more than twice (both give the same order).  The tiles'
-        // halo lists are built on the host.
-        const int64_t chunks = ((int64_t)n + kBfsChunk - 1) / kBfsChunk;
-        L.device_order = prm.tiling != PDCA_TILING_ON && chunks > 2 * (int64_t)host_workers();
+        L.device_order = use_device_order(prm, n);   // both forms give the same order
         L.sigma = sigma_req && sigma_req <= kBfsBlock ? sigma_req : kBfsBlock;
         L.sell_entries = 0;
         L.sell_cap = sell_bound(rp, n, L.sigma, max_deg);
@@ -327,7 +352,14 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
 
     const size_t P = (size_t)L.sell_cap, np = (size_t)L.n_pad, nn = (size_t)n;
     const size_t parts = (size_t)std::max(1, energy_blocks(L.n_slices)) * kRedSlots;
-    size_t o = 0;
+    const StageHead S = stage_head(n, L.nnz);
+    L.o_srp = S.o_srp;
+    L.o_scol = S.o_scol;
+    L.o_sw = S.o_sw;
+    L.o_smask = S.o_smask;
+    L.o_slab = S.o_slab;
+    L.o_status = S.o_status;
+    size_t o = S.end;
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + std::max<size_t>(bytes, 1)); return at; };
     const bool mixed = prm.precision != PDCA_FP32;
     L.o_col = take(4 * P);
@@ -359,20 +391,13 @@ pdca_status compute_layout(const int64_t *rp, int32_t n, int32_t K, const pdca_p
     L.o_mr = take(mixed ? 4 * np * (size_t)K : 0);
     L.o_me[0] = take(half_rows);
     L.o_me[1] = take(half_rows);
-    L.persistent = o;
-    // create-time staging of the CSR input
-    L.o_srp = take(8 * (nn + 1));
-    L.o_scol = take(4 * (size_t)L.nnz);
-    L.o_sw = take(4 * (size_t)L.nnz);
+    // the rest of the create-time staging
     L.o_sdeg = take(8 * nn);
     L.o_sisd = take(8 * nn);
-    L.o_smask = take(nn);
-    L.o_slab = take(4 * nn);
     L.o_scls = take(4 * np);
     L.o_sscan = take(L.host_order ? 8 * (size_t)order_layout_scan_words(L.n_slices) : 0);
     L.o_skey = take(L.device_order ? 8 * nn : 0);
     L.o_sbfs = take(L.device_order ? 16 : 0);
-    L.o_status = take(16);
     L.total = o;
     return PDCA_OK;
 }
@@ -1010,19 +1035,58 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
         st = feasible(prm, omega, prm.lambda_max, 1.0);
         if (st != PDCA_OK) return st;
     }
+    // With the row offsets in host memory, the copies of the CSR and
+    // fidelity data start first, to fixed workspace offsets, and the host's
+    // checks and layout work overlap them (the device renumbering waits for
+    // the columns only).  Every return after this point first waits for the
+    // copies, which read the caller's buffers.
+    cudaStream_t sm0 = static_cast<cudaStream_t>(stream);
+    SideStream order_side;
+    bool early = false, order_ready = false;
+    if (!is_device_ptr(row_ptr)) {
+        const int64_t nnz0 = row_ptr[n];
+        const StageHead S = stage_head(n, std::max<int64_t>(nnz0, 0));
+        if (row_ptr[0] == 0 && nnz0 >= 0 && nnz0 < ((int64_t)1 << 40) && (nnz0 == 0 || (col && w)) &&
+            ws_bytes >= S.end) {
+            char *W0 = static_cast<char *>(workspace);
+            auto cp0 = [&](size_t at, const void *src, size_t bytes) {
+                return bytes ? cudaMemcpyAsync(W0 + at, src, bytes, cudaMemcpyDefault, sm0) : cudaSuccess;
+            };
+            early = true;
+            cudaError_t e = cp0(S.o_srp, row_ptr, 8 * ((size_t)n + 1));
+            if (e == cudaSuccess) e = cp0(S.o_scol, col, 4 * (size_t)nnz0);
+            if (e == cudaSuccess && use_device_order(prm, n)) {
+                e = order_side.open();
+                if (e == cudaSuccess) e = cudaEventRecord(order_side.in, sm0);
+                order_ready = e == cudaSuccess;
+            }
+            if (e == cudaSuccess) e = cp0(S.o_sw, w, 4 * (size_t)nnz0);
+            if (e == cudaSuccess) e = cp0(S.o_smask, fid_mask, (size_t)n);
+            if (e == cudaSuccess) e = cp0(S.o_slab, labels, 4 * (size_t)n);
+            if (e == cudaSuccess) e = cudaMemsetAsync(W0 + S.o_status, 0, 16, sm0);
+            if (e != cudaSuccess) {
+                cudaStreamSynchronize(sm0);
+                return PDCA_ERR_CUDA;
+            }
+        }
+    }
+    auto early_fail = [&](pdca_status s2) {
+        if (early) cudaStreamSynchronize(sm0);
+        return s2;
+    };
     std::vector<int64_t> keep;
     const int64_t *rp = nullptr;
     int64_t max_deg = 0;
     st = host_row_ptr(row_ptr, n, keep, &rp, &max_deg);
-    if (st != PDCA_OK) return st;
+    if (st != PDCA_OK) return early_fail(st);
     const int64_t nnz = rp[n];
-    if (nnz > 0 && (!col || !w)) return PDCA_ERR_INVALID_ARG;
+    if (nnz > 0 && (!col || !w)) return early_fail(PDCA_ERR_INVALID_ARG);
 
     pdca_problem *h = new (std::nothrow) pdca_problem();
-    if (!h) return PDCA_ERR_INVALID_ARG;
+    if (!h) return early_fail(PDCA_ERR_INVALID_ARG);
     st = compute_layout(rp, n, k, prm, max_deg, h->L);
-    if (st != PDCA_OK) { delete h; return st; }
-    if (ws_bytes < h->L.total) { delete h; return PDCA_ERR_OOM; }
+    if (st != PDCA_OK) { delete h; return early_fail(st); }
+    if (ws_bytes < h->L.total) { delete h; return early_fail(PDCA_ERR_OOM); }
     h->prm = prm;
     h->omega = omega;
     h->stream = static_cast<cudaStream_t>(stream);
@@ -1080,23 +1144,25 @@ pdca_status pdca_create(const int64_t *row_ptr, const int32_t *col, const float 
     }
     // the device's BFS order runs on a stream of its own beside the rest of
     // the copies and the validation (it needs only row_ptr and the columns)
-    SideStream order_side;
     auto fail = [&](pdca_status s) { cudaStreamSynchronize(sm); delete h; return s; };
     auto cp = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, sm) : cudaSuccess;
     };
-    if (cp(s_rp, rp, 8 * ((size_t)n + 1)) != cudaSuccess || cp(s_col, col, 4 * (size_t)nnz) != cudaSuccess)
+    if (!early &&
+        (cp(s_rp, rp, 8 * ((size_t)n + 1)) != cudaSuccess || cp(s_col, col, 4 * (size_t)nnz) != cudaSuccess))
         return fail(PDCA_ERR_CUDA);
     if (L.device_order) {
-        if (order_side.open() != cudaSuccess || cudaEventRecord(order_side.in, sm) != cudaSuccess ||
-            cudaStreamWaitEvent(order_side.s, order_side.in, 0) != cudaSuccess ||
+        if (!order_ready &&
+            (order_side.open() != cudaSuccess || cudaEventRecord(order_side.in, sm) != cudaSuccess))
+            return fail(PDCA_ERR_CUDA);
+        if (cudaStreamWaitEvent(order_side.s, order_side.in, 0) != cudaSuccess ||
             device_order_launch(h, order_side.s) != cudaSuccess ||
             cudaEventRecord(order_side.out, order_side.s) != cudaSuccess)
             return fail(PDCA_ERR_CUDA);
     }
-    if (cp(s_w, w, 4 * (size_t)nnz) != cudaSuccess || cp(s_mask, fid_mask, (size_t)n) != cudaSuccess ||
-        cp(s_lab, labels, 4 * (size_t)n) != cudaSuccess ||
-        cudaMemsetAsync(s_status, 0, 16, sm) != cudaSuccess)
+    if (!early && (cp(s_w, w, 4 * (size_t)nnz) != cudaSuccess || cp(s_mask, fid_mask, (size_t)n) != cudaSuccess ||
+                   cp(s_lab, labels, 4 * (size_t)n) != cudaSuccess ||
+                   cudaMemsetAsync(s_status, 0, 16, sm) != cudaSuccess))
         return fail(PDCA_ERR_CUDA);
     if (launch_validate(n, k, s_rp, s_col, s_w, s_mask, s_lab, s_deg, s_isd, s_status, sm) != cudaSuccess)
         return fail(PDCA_ERR_CUDA);
