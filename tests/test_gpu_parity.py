@@ -563,6 +563,37 @@ def test_graph_errors(B):
     assert _err_create(B, rp, col, w, K=1, mask=m, lab=lab) == "PDCA_ERR_BAD_GRAPH"
 
 
+def test_create_row_offset_errors(B):
+    """pdca_create from host buffers starts its copies before it checks the
+    row offsets: bad offsets still come back as errors (after the copies
+    have drained), a workspace too small as OOM, and the next create on the
+    same stream and workspace works."""
+    import torch
+    rp, col, w = complete(6)
+    n = 6
+    prm = B.make_params()
+    mask, lab = np.zeros(n, np.uint8), np.zeros(n, np.int32)
+    size = B.pdca_workspace_size(rp, n, 1, prm)
+    ws = torch.empty(size, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    bad = rp.copy()
+    bad[3] = bad[4] + 1                                     # decreasing offsets
+    st, _ = B.pdca_create(bad, col, w, n, 1, mask, lab, prm, ws, ws.numel(), s)
+    assert B.STATUS_NAMES[st] == "PDCA_ERR_INVALID_ARG"
+    bad0 = rp.copy()
+    bad0[0] = 1                                             # not starting at 0
+    st, _ = B.pdca_create(bad0, col, w, n, 1, mask, lab, prm, ws, ws.numel(), s)
+    assert B.STATUS_NAMES[st] == "PDCA_ERR_INVALID_ARG"
+    st, _ = B.pdca_create(rp, col, w, n, 1, mask, lab, prm, ws, 64, s)
+    assert B.STATUS_NAMES[st] == "PDCA_ERR_OOM"
+    st, h = B.pdca_create(rp, col, w, n, 1, mask, lab, prm, ws, ws.numel(), s)
+    assert st == 0
+    assert B.pdca_solve(h, 2, 3) == 0
+    st, F, _ = B.pdca_energy(h)
+    assert st == 0 and np.isfinite(F)
+    B.pdca_destroy(h)
+
+
 def test_profile_and_launch_counter(B):
     wl = make_workload("moons2k")
     g = B.Problem(wl.row_ptr, wl.col, wl.w, 1, wl.fid_mask, wl.fid_labels,
