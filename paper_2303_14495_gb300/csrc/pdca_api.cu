@@ -734,8 +734,8 @@ cudaError_t device_order_launch(pdca_problem *h, cudaStream_t st) {
 
 // The renumbering (perm, iperm, slice offsets) from that order, on the
 // handle's stream (which must follow the order's work): degree sort, perm,
-// iperm and offsets on the device; the offsets, and the order where rows
-// overflow, come back to the host.
+// iperm and offsets on the device; the entry total, and the order where
+// rows overflow, come back to the host.
 pdca_status device_renumber(pdca_problem *h, const int64_t *rp) {
     Layout &L = h->L;
     const int32_t n = L.n;
@@ -750,12 +750,12 @@ pdca_status device_renumber(pdca_problem *h, const int64_t *rp) {
     if (err_h) return PDCA_ERR_CUDA;   // the order is not a permutation; never expected
     PDCA_TRY(launch_order_sort(n, L.sigma, d_rp, h->iperm, h->perm, st));
     PDCA_TRY(launch_order_layout(n, L.n_pad, L.split, d_rp, h->perm, h->iperm, count, tmp, h->slice_off, st));
-    L.slice_off.resize((size_t)L.n_slices + 1);
-    PDCA_TRY(cudaMemcpyAsync(L.slice_off.data(), h->slice_off, 8 * L.slice_off.size(), cudaMemcpyDeviceToHost, st));
+    int64_t entries = 0;   // the offsets stay on the device; their total comes back
+    PDCA_TRY(cudaMemcpyAsync(&entries, h->slice_off + L.n_slices, 8, cudaMemcpyDeviceToHost, st));
     std::vector<int32_t> perm_h(L.n_ov > 0 ? (size_t)n : 0);
     if (L.n_ov > 0) PDCA_TRY(cudaMemcpyAsync(perm_h.data(), h->perm, 4 * (size_t)n, cudaMemcpyDeviceToHost, st));
     PDCA_TRY(cudaStreamSynchronize(st));
-    L.sell_entries = L.slice_off.back();
+    L.sell_entries = entries;
     if (L.sell_entries > L.sell_cap) return PDCA_ERR_CUDA;   // the bound is a theorem; never expected
     h->slice_off_on_device = true;
     return build_overflow(h, rp, perm_h.data(), L.n_ov > 0 ? n : 0);
