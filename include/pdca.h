@@ -65,7 +65,7 @@ typedef enum {
     PDCA_ERR_NONFINITE = 5,      /* NaN/Inf in the iterate                             */
     PDCA_ERR_OOM = 6,            /* workspace smaller than pdca_workspace_size         */
     PDCA_ERR_CUDA = 7,           /* a CUDA runtime call failed                         */
-    PDCA_ERR_TIMEOUT = 8,        /* a bounded device-side wait ran out                 */
+    PDCA_ERR_TIMEOUT = 8,        /* reserved: no call waits on the device (no spin)   */
     PDCA_ERR_BAD_GRAPH = 9,      /* column out of range, self loop, columns not
                                     strictly increasing, weight < 0 or not finite,
                                     mask not 0/1, or prior label out of range           */

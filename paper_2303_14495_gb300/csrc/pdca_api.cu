@@ -988,7 +988,7 @@ const char *pdca_status_string(pdca_status s) {
     case PDCA_ERR_NONFINITE: return "non-finite value in the iterate";
     case PDCA_ERR_OOM: return "workspace too small";
     case PDCA_ERR_CUDA: return "CUDA runtime error";
-    case PDCA_ERR_TIMEOUT: return "bounded device wait ran out";
+    case PDCA_ERR_TIMEOUT: return "reserved (no call waits on the device)";
     case PDCA_ERR_BAD_GRAPH: return "malformed graph or fidelity input";
     case PDCA_ERR_TOO_LARGE: return "graph larger than the fixed scratch of pdca_energy_static";
     case PDCA_ERR_NOT_CONVERGED: return "iteration limit reached before the tolerance";
