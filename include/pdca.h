@@ -261,6 +261,21 @@ pdca_status pdca_workspace_size_like(const pdca_problem *base, int32_t k, const 
 pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t *fid_mask, const int32_t *labels,
                              const pdca_params *p, void *workspace, size_t ws_bytes, pdca_problem **out);
 
+/* pdca_create_like without waiting for the stream, for serving loops that
+ * admit requests while earlier problems run.  The fidelity arrays are copied
+ * and checked on the stream: they must stay unchanged until the stream has
+ * passed the copies (device memory, or page-locked host memory; pageable host
+ * memory is accepted but may make the copy wait).  The check's outcome (a
+ * mask value above 1 or a label out of range, BAD_GRAPH in
+ * pdca_create_like) is not returned here: the bad rows start and stay
+ * unlabelled, and pdca_labels returns BAD_GRAPH, pdca_labels_async writes a
+ * nonzero status word.  When base holds no lambda estimate and the problem
+ * uses Richardson with lambda_max = 0, the power method runs and the call
+ * waits for it.  Errors: as pdca_create_like, less BAD_GRAPH. */
+pdca_status pdca_create_like_async(const pdca_problem *base, int32_t k, const uint8_t *fid_mask,
+                                   const int32_t *labels, const pdca_params *p, void *workspace, size_t ws_bytes,
+                                   pdca_problem **out);
+
 /* Replace the iterate: u (n x K row-major float32, host or device), or NULL
  * to restore u^0.  Clears the record of the last outer step. */
 pdca_status pdca_set_u(pdca_problem *h, const float *u);
@@ -313,8 +328,22 @@ pdca_status pdca_locality_order(const int64_t *row_ptr, const int32_t *col, int3
 pdca_status pdca_get_u(pdca_problem *h, float *u_out);
 
 /* Labels of the current iterate into labels_out (n int32, host or device):
- * K = 1: 1 if u_i >= 0 else 0;  K >= 2: argmax_k u_ik, lowest k on ties. */
+ * K = 1: 1 if u_i >= 0 else 0;  K >= 2: argmax_k u_ik, lowest k on ties.
+ * Synchronises.  Errors: INVALID_ARG, CUDA, BAD_GRAPH (a problem made by
+ * pdca_create_like_async whose fidelity arrays failed the check; the labels
+ * are written all the same). */
 pdca_status pdca_labels(pdca_problem *h, int32_t *labels_out);
+
+/* pdca_labels enqueued on the handle's stream without waiting: labels_out
+ * (n int32, device or page-locked host memory) holds the labels once the
+ * stream has passed the call; pageable host memory makes the call wait.
+ * fid_status_out: NULL, or one uint32 (device or host) receiving 0 when the
+ * fidelity arrays were valid and nonzero when pdca_create_like_async found a
+ * bad mask value or label (written on the stream for a problem made by
+ * pdca_create_like_async, at once otherwise).  The labels are staged in the
+ * handle's spare iterate buffer, so a later step on the same stream is
+ * ordered after the copy.  Errors: INVALID_ARG, CUDA. */
+pdca_status pdca_labels_async(pdca_problem *h, int32_t *labels_out, uint32_t *fid_status_out);
 
 /* The lambda_max in use by the Richardson preconditioner (the power-method
  * estimate raised by 0.1% and capped at 2, or the value given), and the raw
@@ -502,6 +531,14 @@ void pdca_batch_destroy(pdca_batch *b);
 /* Release the handle's host-side state (the workspace stays the caller's).
  * Synchronises the handle's stream first.  NULL is ignored. */
 void pdca_destroy(pdca_problem *h);
+
+/* pdca_destroy without waiting for the stream (it still waits when the
+ * handle holds captured solve graphs).  Work already enqueued for the
+ * handle keeps running and reads the workspace, so the caller reuses the
+ * workspace only in the stream's order: on the same stream (a stream-ordered
+ * allocator such as PyTorch's caching allocator on that stream), or after an
+ * event recorded on the stream has completed.  NULL is ignored. */
+void pdca_release(pdca_problem *h);
 
 /* Static description of a status code. */
 const char *pdca_status_string(pdca_status s);

@@ -51,6 +51,7 @@ EXPORTS = [
     "pdca_spectral_workspace_size", "pdca_spectral_init",
     "pdca_image_graph_workspace_size", "pdca_image_graph",
     "pdca_point_graph_workspace_size", "pdca_point_graph", "pdca_graph_enable", "pdca_locality_order",
+    "pdca_create_like_async", "pdca_labels_async", "pdca_release",
 ]
 
 
@@ -116,6 +117,9 @@ def lib():
                 "pdca_batch_destroy": (None, [vp]),
                 "pdca_workspace_size_like": (C.c_int, [vp, i32, P, C.POINTER(C.c_size_t)]),
                 "pdca_create_like": (C.c_int, [vp, i32, vp, vp, P, vp, C.c_size_t, C.POINTER(vp)]),
+                "pdca_create_like_async": (C.c_int, [vp, i32, vp, vp, P, vp, C.c_size_t, C.POINTER(vp)]),
+                "pdca_labels_async": (C.c_int, [vp, vp, vp]),
+                "pdca_release": (None, [vp]),
                 "pdca_spectral_workspace_size": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
                 "pdca_spectral_init": (C.c_int, [vp, vp, C.c_size_t, i32, dbl, C.POINTER(dbl), vp,
                                                  C.POINTER(i32)]),
@@ -318,8 +322,13 @@ class Problem:
         self.h = h
 
     @classmethod
-    def like(cls, base: "Problem", K, fid_mask, fid_labels, params: pdca_params):
-        """A problem on base's graph (shared, read-only operator); see pdca_create_like."""
+    def like(cls, base: "Problem", K, fid_mask, fid_labels, params: pdca_params, wait: bool = True):
+        """A problem on base's graph (shared, read-only operator); see pdca_create_like.
+
+        wait=False calls pdca_create_like_async: nothing waits for the stream,
+        the fidelity arrays must stay unchanged until the stream has copied
+        them (pass device tensors or pinned host tensors), and a failed
+        fidelity check shows in ``labels`` / ``labels_async``."""
         import torch
         self = cls.__new__(cls)
         self.torch = torch
@@ -333,8 +342,9 @@ class Problem:
         self.ws_bytes = int(out.value)
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
         h = C.c_void_p()
-        _check(lib().pdca_create_like(base.h, self.K, _ptr(fid_mask), _ptr(fid_labels), C.byref(params),
-                                      _ptr(self.workspace), self.ws_bytes, C.byref(h)), "pdca_create_like")
+        name = "pdca_create_like" if wait else "pdca_create_like_async"
+        _check(getattr(lib(), name)(base.h, self.K, _ptr(fid_mask), _ptr(fid_labels), C.byref(params),
+                                    _ptr(self.workspace), self.ws_bytes, C.byref(h)), name)
         self.h = h
         return self
 
@@ -342,6 +352,15 @@ class Problem:
         if getattr(self, "h", None):
             pdca_destroy(self.h)
             self.h = None
+
+    def release(self):
+        """pdca_release: drop the handle without waiting for the stream.  The
+        workspace tensor is returned to PyTorch's caching allocator, which
+        reuses it only in the order of the stream it was allocated on."""
+        if getattr(self, "h", None):
+            lib().pdca_release(self.h)
+            self.h = None
+        self.workspace = None
 
     def __del__(self):
         try:
@@ -380,6 +399,14 @@ class Problem:
         if out is None:
             out = np.empty(self.n, np.int32)
         _check(pdca_labels(self.h, out), "pdca_labels")
+        return out
+
+    def labels_async(self, out, status=None):
+        """pdca_labels_async: enqueue the labels into ``out`` (a device or
+        pinned host int32 tensor of n) and the fidelity-check word into
+        ``status`` (one int32 or uint32 element, or None); both are valid once
+        the stream has passed the call."""
+        _check(lib().pdca_labels_async(self.h, _ptr(out), _ptr(status)), "pdca_labels_async")
         return out
 
     def spectral_init(self, max_iters: int = 500, tol: float = 1e-5, strict: bool = True):

@@ -441,6 +441,7 @@ struct pdca_problem {
     bool prof = false;
     bool tiled = false;
     bool slice_off_on_device = false;   // slice_off computed by the device renumbering
+    uint32_t *fid_status = nullptr;     // fidelity check left on the device (pdca_create_like_async)
     TileView tv{};
     int64_t halo_rows = 0;
     bool mixed = false, bf16u = false;
@@ -1259,8 +1260,15 @@ pdca_status pdca_workspace_size_like(const pdca_problem *base, int32_t k, const 
     return PDCA_OK;
 }
 
-pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t *fid_mask, const int32_t *labels,
-                             const pdca_params *p, void *workspace, size_t ws_bytes, pdca_problem **out) {
+}  // extern "C"
+
+namespace {
+
+// pdca_create_like and pdca_create_like_async: `wait` reads the fidelity
+// check back before returning; without it the check's word stays on the
+// device for pdca_labels / pdca_labels_async to report.
+pdca_status create_like(const pdca_problem *base, int32_t k, const uint8_t *fid_mask, const int32_t *labels,
+                        const pdca_params *p, void *workspace, size_t ws_bytes, pdca_problem **out, bool wait) {
     if (!out) return PDCA_ERR_INVALID_ARG;
     *out = nullptr;
     if (!base || k < 1 || k > PDCA_MAX_K || !fid_mask || !labels || !workspace) return PDCA_ERR_INVALID_ARG;
@@ -1347,6 +1355,11 @@ pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t 
     h->cur = 0;
     h->prev = 1;
     h->has_prev = false;
+    if (!wait) {
+        h->fid_status = s_status;
+        *out = h;
+        return PDCA_OK;
+    }
     uint32_t status = 0;
     if (cudaMemcpyAsync(&status, s_status, 4, cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
         cudaStreamSynchronize(sm) != cudaSuccess)
@@ -1354,6 +1367,21 @@ pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t 
     if (status) return fail(PDCA_ERR_BAD_GRAPH);
     *out = h;
     return PDCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t *fid_mask, const int32_t *labels,
+                             const pdca_params *p, void *workspace, size_t ws_bytes, pdca_problem **out) {
+    return create_like(base, k, fid_mask, labels, p, workspace, ws_bytes, out, true);
+}
+
+pdca_status pdca_create_like_async(const pdca_problem *base, int32_t k, const uint8_t *fid_mask,
+                                   const int32_t *labels, const pdca_params *p, void *workspace, size_t ws_bytes,
+                                   pdca_problem **out) {
+    return create_like(base, k, fid_mask, labels, p, workspace, ws_bytes, out, false);
 }
 
 pdca_status pdca_set_u(pdca_problem *h, const float *u) {
@@ -1535,15 +1563,39 @@ pdca_status pdca_get_u(pdca_problem *h, float *u_out) {
 pdca_status pdca_labels(pdca_problem *h, int32_t *labels_out) {
     if (!h || !labels_out) return PDCA_ERR_INVALID_ARG;
     const Layout &L = h->L;
+    uint32_t fid = 0;
     if (is_device_ptr(labels_out)) {
         PDCA_TRY(launch_labels(L.K, L.n, h->U[h->cur], h->perm, labels_out, h->stream));
-        PDCA_TRY(cudaStreamSynchronize(h->stream));
-        return PDCA_OK;
+    } else {
+        int32_t *stage = reinterpret_cast<int32_t *>(h->U[h->spare()]);
+        PDCA_TRY(launch_labels(L.K, L.n, h->U[h->cur], h->perm, stage, h->stream));
+        PDCA_TRY(cudaMemcpyAsync(labels_out, stage, sizeof(int32_t) * (size_t)L.n, cudaMemcpyDeviceToHost,
+                                 h->stream));
     }
-    int32_t *stage = reinterpret_cast<int32_t *>(h->U[h->spare()]);
-    PDCA_TRY(launch_labels(L.K, L.n, h->U[h->cur], h->perm, stage, h->stream));
-    PDCA_TRY(cudaMemcpyAsync(labels_out, stage, sizeof(int32_t) * (size_t)L.n, cudaMemcpyDeviceToHost, h->stream));
+    if (h->fid_status) PDCA_TRY(cudaMemcpyAsync(&fid, h->fid_status, 4, cudaMemcpyDeviceToHost, h->stream));
     PDCA_TRY(cudaStreamSynchronize(h->stream));
+    return fid ? PDCA_ERR_BAD_GRAPH : PDCA_OK;
+}
+
+pdca_status pdca_labels_async(pdca_problem *h, int32_t *labels_out, uint32_t *fid_status_out) {
+    if (!h || !labels_out) return PDCA_ERR_INVALID_ARG;
+    const Layout &L = h->L;
+    if (is_device_ptr(labels_out)) {
+        PDCA_TRY(launch_labels(L.K, L.n, h->U[h->cur], h->perm, labels_out, h->stream));
+    } else {
+        int32_t *stage = reinterpret_cast<int32_t *>(h->U[h->spare()]);
+        PDCA_TRY(launch_labels(L.K, L.n, h->U[h->cur], h->perm, stage, h->stream));
+        PDCA_TRY(cudaMemcpyAsync(labels_out, stage, sizeof(int32_t) * (size_t)L.n, cudaMemcpyDeviceToHost,
+                                 h->stream));
+    }
+    if (!fid_status_out) return PDCA_OK;
+    if (h->fid_status) {
+        PDCA_TRY(cudaMemcpyAsync(fid_status_out, h->fid_status, 4, cudaMemcpyDefault, h->stream));
+    } else if (is_device_ptr(fid_status_out)) {
+        PDCA_TRY(cudaMemsetAsync(fid_status_out, 0, 4, h->stream));
+    } else {
+        *fid_status_out = 0;   // checked when the problem was created
+    }
     return PDCA_OK;
 }
 
@@ -1763,6 +1815,14 @@ void pdca_destroy(pdca_problem *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    h->drop_graphs();
+    delete h;
+}
+
+void pdca_release(pdca_problem *h) {
+    if (!h) return;
+    if (!h->graphs.empty()) cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);   // a pending event is freed once it completes
     h->drop_graphs();
     delete h;
 }

@@ -11,7 +11,9 @@ problems by a few passes in shared launches (pdca_batch_step); finished
 problems are polled, their labels read, their memory released, and waiting
 requests take the freed slots while the others keep running.  The graph and
 the iterate of a problem stay resident on the device from admission to
-completion.
+completion.  The loop is pipelined: admission, the labels read and the
+release are enqueued without waiting for the stream, and the host waits only
+for the tick before the newest, so host work overlaps the device's.
 
 ``serve_sequential`` is the comparison: one problem at a time (FP32 by
 default), pdca_solve per request in arrival order, on the same prepared
@@ -65,50 +67,102 @@ def prepare(pool, precision: int, stream):
 
 def serve_batched(bases, requests, precision: int = B.PDCA_MIXED_BF16W_FP16U, mem_budget: int = 64 << 30,
                   max_slots: int = 64, passes_per_tick: int = 4, keep_results: bool = False,
-                  time_scale: float = 1.0):
+                  time_scale: float = 1.0, pipelined: bool = True):
     """Continuous batching on prepared operators (``bases`` of the matching
-    precision family).  Returns (Stats, {rid: (labels, u)} if keep_results)."""
+    precision family).  Returns (Stats, {rid: (labels, u)} if keep_results).
+
+    pipelined=True keeps the stream busy while the host works: requests are
+    admitted with pdca_create_like_async (fidelity arrays staged in pinned
+    host memory), a finished problem's labels are enqueued with
+    pdca_labels_async into pinned memory, and the host waits only for the
+    tick before the one it has just enqueued, so that the device runs tick t
+    while the host retires tick t - 1 and admits for tick t + 1.  A finished
+    problem is released (pdca_release) once its labels have arrived; its
+    workspace returns to PyTorch's allocator on the serving stream.
+    pipelined=False waits for the stream at every admission and every
+    finished problem (pdca_create_like, pdca_labels, pdca_destroy)."""
+    import collections
     import torch
     stream = bases[0].stream
     batch = B.Batch(max_problems=max_slots, stream=stream)
     pending = sorted(requests, key=lambda r: r.arrival)
+    nxt = 0                           # next pending request
     active = {}                       # handle value -> (request, problem, ws bytes)
+    inflight = collections.deque()    # (event after a tick, [(request, problem, ws, labels, status)])
     used = peak = busy_admits = 0
     lat: Dict[int, float] = {}
     results = {}
     t0 = time.perf_counter()
+
+    def retire(entries):
+        nonlocal used
+        now = time.perf_counter() - t0
+        for req, prob, ws, lab, st in entries:
+            if st is not None and int(st[0]) != 0:
+                raise B.PdcaError(B.PDCA_ERR_BAD_GRAPH, f"pdca_create_like_async (request {req.rid})")
+            lat[req.rid] = now - req.arrival * time_scale
+            if keep_results:
+                results[req.rid] = (np.array(lab, dtype=np.int32), prob.get_u())
+            if pipelined:
+                prob.release()
+            else:
+                prob.close()
+            used -= ws
+
     with torch.cuda.stream(stream):
-        while pending or active:
+        while nxt < len(pending) or active or inflight:
             now = time.perf_counter() - t0
-            while pending and pending[0].arrival * time_scale <= now and len(active) < max_slots:
-                req = pending[0]
+            while nxt < len(pending) and pending[nxt].arrival * time_scale <= now and len(active) < max_slots:
+                req = pending[nxt]
                 base = bases[req.template]
                 prm = _params(req, precision)
                 ws = B.workspace_size_like(base, req.K, prm)
-                if used + ws > mem_budget and active:
+                if used + ws > mem_budget and (active or inflight):
                     break
-                prob = B.Problem.like(base, req.K, req.fid_mask, req.fid_labels, prm)
+                if pipelined:
+                    mask = torch.from_numpy(np.ascontiguousarray(req.fid_mask)).pin_memory()
+                    labs = torch.from_numpy(np.ascontiguousarray(req.fid_labels)).pin_memory()
+                    prob = B.Problem.like(base, req.K, mask, labs, prm, wait=False)
+                else:
+                    prob = B.Problem.like(base, req.K, req.fid_mask, req.fid_labels, prm)
                 batch.add(prob, req.outer, req.inner)
                 busy_admits += 1 if active else 0
                 active[prob.h.value] = (req, prob, ws)
                 used += ws
                 peak = max(peak, used)
-                pending.pop(0)
-            if not active:
-                wait = pending[0].arrival * time_scale - (time.perf_counter() - t0)
+                nxt += 1
+            if active:
+                batch.step(passes_per_tick)
+                done = []
+                for prob in batch.poll():
+                    req, p, ws = active.pop(prob.h.value)
+                    if pipelined:
+                        lab = torch.empty(prob.n, dtype=torch.int32, pin_memory=True)
+                        st = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+                        prob.labels_async(lab, st)
+                        done.append((req, prob, ws, lab, st))
+                    else:
+                        done.append((req, prob, ws, prob.labels(), None))   # synchronises the stream
+                    del p
+                if not pipelined:
+                    retire(done)
+                    continue
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                inflight.append((ev, done))
+                while len(inflight) > 1:      # the device keeps the newest tick
+                    ev_old, entries = inflight.popleft()
+                    ev_old.synchronize()
+                    retire(entries)
+                continue
+            while inflight:                   # nothing resident: drain
+                ev_old, entries = inflight.popleft()
+                ev_old.synchronize()
+                retire(entries)
+            if nxt < len(pending) and not active:
+                wait = pending[nxt].arrival * time_scale - (time.perf_counter() - t0)
                 if wait > 0:
                     time.sleep(wait)
-                continue
-            batch.step(passes_per_tick)
-            for prob in batch.poll():
-                req, p, ws = active.pop(prob.h.value)
-                lab = prob.labels()               # synchronises the serving stream
-                lat[req.rid] = time.perf_counter() - t0 - req.arrival * time_scale
-                if keep_results:
-                    results[req.rid] = (lab, prob.get_u())
-                prob.close()
-                del prob, p
-                used -= ws
     makespan = time.perf_counter() - t0
     batch.close()
     return Stats(lat, makespan, peak, busy_admits), results

@@ -104,3 +104,73 @@ def test_create_like_equals_fresh_create(setup):
             B.Problem.like(base, 4, wl.fid_mask, bad, B.make_params(precision=prec))
         with pytest.raises(B.PdcaError, match="INVALID_ARG"):
             B.Problem.like(base, 4, wl.fid_mask, lab % 4, B.make_params(precision=1 - prec))
+
+
+def test_pipelined_equals_waiting_loop(setup):
+    """The pipelined loop (asynchronous admission, labels and release) gives
+    every request bit for bit the result of the loop that waits for the
+    stream at each admission and each finished problem."""
+    from paper_2303_14495_gb300 import serving
+    B, pool, reqs, bases = setup
+    sub = reqs[:12]
+    st_p, piped = serving.serve_batched(bases["mixed"], sub, max_slots=5, passes_per_tick=2, keep_results=True)
+    st_w, waited = serving.serve_batched(bases["mixed"], sub, max_slots=5, passes_per_tick=2, keep_results=True,
+                                         pipelined=False)
+    assert st_p.summary()["requests"] == st_w.summary()["requests"] == len(sub)
+    for r in sub:
+        np.testing.assert_array_equal(piped[r.rid][1], waited[r.rid][1])
+        np.testing.assert_array_equal(piped[r.rid][0], waited[r.rid][0])
+
+
+def test_create_like_async_and_labels_async(setup):
+    """pdca_create_like_async on pinned fidelity arrays iterates exactly like
+    pdca_create_like; pdca_labels_async into pinned host and device memory
+    equals pdca_labels; a bad label is reported by the status word and by
+    pdca_labels instead of by the create call; released problems leave the
+    stream usable."""
+    import torch
+    from gen import make_workload
+    B, pool, reqs, bases = setup
+    wl = make_workload("voronoi2048", size=128)
+    rng = np.random.default_rng(5)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        base = B.Problem(wl.row_ptr, wl.col, wl.w, 1, np.zeros(wl.n, np.uint8), np.zeros(wl.n, np.int32),
+                         B.make_params(precond=2, eps=1.0, c=502.0, eta=500.0), stream=stream)
+        prm = B.make_params(precond=2, eps=1.0, c=502.0, eta=500.0)
+        for K in (1, 3, 6):
+            lab = rng.integers(0, max(K, 2), size=wl.n).astype(np.int32)
+            mask_p = torch.from_numpy(wl.fid_mask.copy()).pin_memory()
+            lab_p = torch.from_numpy(lab).pin_memory()
+            ref = B.Problem.like(base, K, wl.fid_mask, lab, prm)
+            asy = B.Problem.like(base, K, mask_p, lab_p, prm, wait=False)
+            ref.solve(2, 4)
+            asy.solve(2, 4)
+            out_h = torch.full((wl.n,), -1, dtype=torch.int32, pin_memory=True)
+            out_d = torch.full((wl.n,), -1, dtype=torch.int32, device="cuda")
+            st_h = torch.full((1,), 7, dtype=torch.int32, pin_memory=True)
+            st_d = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+            asy.labels_async(out_h, st_h)
+            asy.labels_async(out_d, st_d)
+            stream.synchronize()
+            np.testing.assert_array_equal(asy.get_u(), ref.get_u())
+            np.testing.assert_array_equal(out_h.numpy(), ref.labels())
+            np.testing.assert_array_equal(out_d.cpu().numpy(), ref.labels())
+            assert int(st_h[0]) == 0 and int(st_d.cpu()[0]) == 0
+            st_r = torch.full((1,), 7, dtype=torch.int32, pin_memory=True)
+            ref.labels_async(out_h, st_r)      # made by pdca_create_like: the word is written at once
+            assert int(st_r[0]) == 0
+            asy.release()
+            ref.close()
+        bad = lab.copy()
+        bad[np.flatnonzero(wl.fid_mask)[0]] = 99
+        bad_p = torch.from_numpy(bad).pin_memory()
+        asy = B.Problem.like(base, 6, mask_p, bad_p, prm, wait=False)
+        st_h = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+        asy.labels_async(torch.empty(wl.n, dtype=torch.int32, pin_memory=True), st_h)
+        stream.synchronize()
+        assert int(st_h[0]) != 0
+        with pytest.raises(B.PdcaError, match="BAD_GRAPH"):
+            asy.labels()
+        asy.release()
+        stream.synchronize()
