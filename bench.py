@@ -400,6 +400,32 @@ def run_serving(args, local):
     }
 
 
+def power_spmv_timing(wl, prm_kw, dev, hbm, extra=400, reps=2):
+    """Time per iteration of the power method's SpMV (run inside pdca_create):
+    creates with 1 and 1 + extra iterations, each timed on the host around a
+    synchronised create, best of ``reps``; the difference is ``extra`` SpMV
+    launches with their scale and finalize work.  Bytes per iteration
+    E (4 + 4) + N (2 4) (int32 column, weight; x read and y written)."""
+    import torch
+    from paper_2303_14495_gb300 import binding as B
+    best = {}
+    for it in (1, 1 + extra) * reps:
+        prm = B.params_from_workload(wl.params, power_iters=it, **prm_kw)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        g = B.Problem(wl.row_ptr, wl.col, wl.w, wl.K, wl.fid_mask, wl.fid_labels, prm, device=dev)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t
+        g.close()
+        best[it] = min(best.get(it, float("inf")), dt)
+    us = (best[1 + extra] - best[1]) / extra * 1e6
+    nbytes = 8 * wl.nnz + 8 * wl.n
+    gbs = nbytes / (us * 1e-6) / 1e9
+    return {"kernel": "power_spmv_kernel", "us_per_iteration": us, "bytes_per_iteration": nbytes,
+            "achieved": gbs, "unit": "GB/s", "peak": hbm, "frac": gbs / hbm,
+            "how": f"create with {1 + extra} minus create with 1 power iteration, best of {reps}, / {extra}"}
+
+
 def run_ours(args, wl, world, rank, local):
     import torch
     from paper_2303_14495_gb300 import binding as B
@@ -613,6 +639,14 @@ def run_ours(args, wl, world, rank, local):
             cpu["voronoi2048_ms_per_sweep"]["allcores"] = 1e3 * dt2 / 2
         cpu["small_configs"] = small_configs(args, dev)
 
+    power = None
+    if rank == 0 and not precision and not lay["tiled"]:
+        try:
+            power = power_spmv_timing(wl, dict(sort_window=args.sort_window, **LAYOUT_PARAMS[args.layout]), dev,
+                                      hbm)
+        except Exception as exc:   # a side measurement: report why it is missing
+            power = {"error": f"{type(exc).__name__}: {exc}"}
+
     serve = None
     if rank == 0 and not args.no_serving:
         serve = run_serving(args, local)
@@ -651,6 +685,8 @@ def run_ours(args, wl, world, rank, local):
     }
     if e2e:
         line["e2e"] = e2e
+    if power:
+        line["power_method"] = power
     if mixed:
         line["mixed_precision"] = mixed
     if tuned_layout is not None:
