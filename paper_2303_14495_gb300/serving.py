@@ -102,7 +102,8 @@ def serve_batched(bases, requests, precision: int = B.PDCA_MIXED_BF16W_FP16U, me
                 raise B.PdcaError(B.PDCA_ERR_BAD_GRAPH, f"pdca_create_like_async (request {req.rid})")
             lat[req.rid] = now - req.arrival * time_scale
             if keep_results:
-                results[req.rid] = (np.array(lab, dtype=np.int32), prob.get_u())
+                host = lab.numpy() if hasattr(lab, "numpy") else lab    # pinned tensor or numpy array
+                results[req.rid] = (np.array(host, dtype=np.int32), prob.get_u())
             if pipelined:
                 prob.release()
             else:
