@@ -117,3 +117,23 @@ def test_no_oracle_in_product():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "pdca_oracle" not in text, f
+
+
+def test_async_entry_points_reject_before_device_work(B):
+    """The asynchronous admission, labels and release calls check their
+    arguments before any device work (NULL handles; NULL out pointer)."""
+    lib = B.lib()
+    h = C.c_void_p()
+    mask = np.zeros(8, np.uint8)
+    lab = np.zeros(8, np.int32)
+    ws = C.create_string_buffer(1 << 12)
+    p = B.make_params()
+    assert lib.pdca_create_like_async(None, 2, mask.ctypes.data, lab.ctypes.data, C.byref(p), C.addressof(ws),
+                                      1 << 12, C.byref(h)) == 1
+    assert h.value is None
+    assert lib.pdca_create_like_async(None, 2, mask.ctypes.data, lab.ctypes.data, C.byref(p), C.addressof(ws),
+                                      1 << 12, None) == 1
+    out = np.zeros(8, np.int32)
+    st = np.zeros(1, np.uint32)
+    assert lib.pdca_labels_async(None, out.ctypes.data, st.ctypes.data) == 1
+    lib.pdca_release(None)          # ignored, like pdca_destroy(NULL)
