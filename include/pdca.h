@@ -271,7 +271,8 @@ pdca_status pdca_create_like(const pdca_problem *base, int32_t k, const uint8_t 
  * unlabelled, and pdca_labels returns BAD_GRAPH, pdca_labels_async writes a
  * nonzero status word.  When base holds no lambda estimate and the problem
  * uses Richardson with lambda_max = 0, the power method runs and the call
- * waits for it.  Errors: as pdca_create_like, less BAD_GRAPH. */
+ * waits for it.  Serving infrastructure; the paper has no counterpart.
+ * Errors: as pdca_create_like, less BAD_GRAPH. */
 pdca_status pdca_create_like_async(const pdca_problem *base, int32_t k, const uint8_t *fid_mask,
                                    const int32_t *labels, const pdca_params *p, void *workspace, size_t ws_bytes,
                                    pdca_problem **out);
@@ -342,7 +343,9 @@ pdca_status pdca_labels(pdca_problem *h, int32_t *labels_out);
  * bad mask value or label (written on the stream for a problem made by
  * pdca_create_like_async, at once otherwise).  The labels are staged in the
  * handle's spare iterate buffer, so a later step on the same stream is
- * ordered after the copy.  Errors: INVALID_ARG, CUDA. */
+ * ordered after the copy.  The labels are those of pdca_labels; the
+ * asynchronous form has no counterpart in the paper.  Errors: INVALID_ARG,
+ * CUDA. */
 pdca_status pdca_labels_async(pdca_problem *h, int32_t *labels_out, uint32_t *fid_status_out);
 
 /* The lambda_max in use by the Richardson preconditioner (the power-method
@@ -537,7 +540,8 @@ void pdca_destroy(pdca_problem *h);
  * handle keeps running and reads the workspace, so the caller reuses the
  * workspace only in the stream's order: on the same stream (a stream-ordered
  * allocator such as PyTorch's caching allocator on that stream), or after an
- * event recorded on the stream has completed.  NULL is ignored. */
+ * event recorded on the stream has completed.  No counterpart in the
+ * paper.  NULL is ignored. */
 void pdca_release(pdca_problem *h);
 
 /* Static description of a status code. */
