@@ -355,11 +355,15 @@ class Problem:
 
     def release(self):
         """pdca_release: drop the handle without waiting for the stream.  The
-        workspace tensor is returned to PyTorch's caching allocator, which
-        reuses it only in the order of the stream it was allocated on."""
+        workspace tensor goes back to PyTorch's caching allocator marked as
+        used by the problem's stream (record_stream), so the allocator hands
+        it out again only after the work enqueued there has finished."""
         if getattr(self, "h", None):
             lib().pdca_release(self.h)
             self.h = None
+        ws = getattr(self, "workspace", None)
+        if ws is not None:
+            ws.record_stream(self.stream)
         self.workspace = None
 
     def __del__(self):
